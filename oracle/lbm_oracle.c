@@ -1,0 +1,398 @@
+/*
+ * lbm_oracle.c -- plain FP64 reference of the D3Q19 BGK collide-and-stream
+ * update (test infrastructure only).
+ *
+ * This file is the oracle that the CUDA path is checked against.  Only the
+ * tests, the smoke check and the CPU-baseline leg of the benchmark load it;
+ * the product library never links, calls or includes it, and it shares no
+ * table, header or helper with the CUDA sources.
+ *
+ * What it computes.  Fu & Song (arXiv 2208.05429) merge two collision-
+ * streaming cycles of a D3Q19 lattice (Sec. 3, Alg. 1; Sec. 4.1, Alg. 2;
+ * Sec. 4.2, Alg. 3) and state that the merged solvers reproduce the plain
+ * single-step solver exactly (Sec. 5.1, verification of the four solvers on
+ * the same cavity).  The paper never writes down the lattice, the collision
+ * or the boundary rule; they are the Palabos defaults it builds on.  The
+ * oracle therefore is the plain definition of one time step, written out in
+ * the textbook form the method reaches:
+ *
+ *   lattice    D3Q19, c_0 = 0, six face vectors (w = 1/18), twelve edge
+ *              vectors (w = 1/36), w_0 = 1/3, c_s^2 = 1/3.  Directions 1..9
+ *              are the vectors whose first non-zero component (x, y, z order)
+ *              is -1 -- the half of the neighbours the swap streams to
+ *              (Sec. 3) -- and direction i+9 is the opposite of i.
+ *   collision  BGK with Guo forcing, omega = 1/tau:
+ *                rho = sum f_i,  u = (sum f_i c_i + F/2) / rho
+ *                feq_i = w_i rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u)
+ *                S_i   = w_i (3 (c_i - u) + 9 (c_i.u) c_i) . F
+ *                f*_i  = f_i - omega (f_i - feq_i) + (1 - omega/2) S_i
+ *   streaming  f_i(x + c_i, t+1) = f*_i(x); periodic axes wrap; a link that
+ *              leaves the box across a non-periodic face is a wall link
+ *              (half-way bounce-back):
+ *                f_opp(i)(x, t+1) = f*_i(x) - 6 w_i rho_w (c_i . u_w)
+ *              with u_w the lid velocity when one of the faces crossed is a
+ *              LID face (the lid takes precedence at edges and corners),
+ *              zero otherwise.
+ *
+ * The state at step n is the post-stream population f^n in the canonical
+ * layout f[i][z][y][x] (x fastest).  Everything is double precision and is
+ * evaluated in the order written above, cell by cell, with no blocking or
+ * fusion beyond the one-cell collide-then-scatter of the definition.
+ *
+ * The adjoint (orc_adjoint_step, orc_adjoint_seed) is the hand-derived
+ * discrete adjoint of the step above, with rho_w constant so that the lid
+ * term has no derivative.  It has no counterpart in the paper.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q 19
+
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_LID = 2 };
+enum { FORCE_NONE = 0, FORCE_UNIFORM = 1, FORCE_FIELD = 2 };
+
+/* The D3Q19 velocity set in the half-neighbour order described above. */
+static const int C[Q][3] = {
+    {0, 0, 0},
+    {-1, 0, 0}, {0, -1, 0}, {0, 0, -1}, {-1, -1, 0}, {-1, 1, 0},
+    {-1, 0, -1}, {-1, 0, 1}, {0, -1, -1}, {0, -1, 1},
+    {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, -1, 0},
+    {1, 0, 1}, {1, 0, -1}, {0, 1, 1}, {0, 1, -1},
+};
+
+static const double W[Q] = {
+    1.0 / 3.0,
+    1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 36.0, 1.0 / 36.0,
+    1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
+    1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 36.0, 1.0 / 36.0,
+    1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
+};
+
+static int OPP(int i) { return i == 0 ? 0 : (i <= 9 ? i + 9 : i - 9); }
+
+typedef struct {
+    int64_t nx, ny, nz;
+    double tau;
+    int32_t bc[6];          /* x-, x+, y-, y+, z-, z+ */
+    double u_lid[3];
+    double rho_wall;
+    int32_t force_mode;
+    double force_uniform[3];
+    const double *force_field; /* [3][N] canonical, used when FORCE_FIELD */
+} orc_cfg;
+
+static int64_t ncells(const orc_cfg *g) { return g->nx * g->ny * g->nz; }
+
+static int64_t cell_index(const orc_cfg *g, int64_t x, int64_t y, int64_t z)
+{
+    return (z * g->ny + y) * g->nx + x;
+}
+
+/* Body force acting on one cell. */
+static void cell_force(const orc_cfg *g, int64_t cell, double F[3])
+{
+    const int64_t n = ncells(g);
+    for (int a = 0; a < 3; ++a) {
+        if (g->force_mode == FORCE_UNIFORM)
+            F[a] = g->force_uniform[a];
+        else if (g->force_mode == FORCE_FIELD)
+            F[a] = g->force_field[a * n + cell];
+        else
+            F[a] = 0.0;
+    }
+}
+
+/* Follow the link from cell (x,y,z) along c_i.  Returns 1 and the target
+ * cell when the link stays inside the (periodically wrapped) box, 0 for a
+ * wall link; *lid tells whether a LID face is among the faces crossed. */
+static int link_target(const orc_cfg *g, int64_t x, int64_t y, int64_t z, int i,
+                       int64_t *target, int *lid)
+{
+    int64_t p[3] = {x + C[i][0], y + C[i][1], z + C[i][2]};
+    const int64_t n[3] = {g->nx, g->ny, g->nz};
+    int wall = 0;
+    *lid = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (p[a] < 0 || p[a] >= n[a]) {
+            const int face = 2 * a + (p[a] < 0 ? 0 : 1);
+            if (g->bc[face] == BC_PERIODIC) {
+                p[a] = (p[a] + n[a]) % n[a];
+            } else {
+                wall = 1;
+                if (g->bc[face] == BC_LID) *lid = 1;
+            }
+        }
+    }
+    if (wall) return 0;
+    *target = cell_index(g, p[0], p[1], p[2]);
+    return 1;
+}
+
+/* Moving-wall correction 6 w_i rho_w (c_i . u_w) of a wall link. */
+static double wall_term(const orc_cfg *g, int i, int lid)
+{
+    if (!lid) return 0.0;
+    const double cu = C[i][0] * g->u_lid[0] + C[i][1] * g->u_lid[1] + C[i][2] * g->u_lid[2];
+    return 6.0 * W[i] * g->rho_wall * cu;
+}
+
+/* ------------------------------------------------------------------ */
+/* lattice tables, equilibrium, collision                              */
+/* ------------------------------------------------------------------ */
+
+void orc_lattice(int32_t *c /* [19][3] */, double *w /* [19] */, int32_t *opp /* [19] */)
+{
+    for (int i = 0; i < Q; ++i) {
+        for (int a = 0; a < 3; ++a) c[3 * i + a] = C[i][a];
+        w[i] = W[i];
+        opp[i] = OPP(i);
+    }
+}
+
+void orc_equilibrium(double rho, const double *u, double *feq)
+{
+    const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < Q; ++i) {
+        const double cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
+        feq[i] = W[i] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+    }
+}
+
+void orc_collide_cell(double tau, const double *f, const double *F, double *fstar)
+{
+    double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < Q; ++i) {
+        rho += f[i];
+        for (int a = 0; a < 3; ++a) m[a] += f[i] * C[i][a];
+    }
+    double u[3];
+    for (int a = 0; a < 3; ++a) u[a] = (m[a] + 0.5 * F[a]) / rho;
+    const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+    const double omega = 1.0 / tau;
+    for (int i = 0; i < Q; ++i) {
+        const double cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
+        const double cF = C[i][0] * F[0] + C[i][1] * F[1] + C[i][2] * F[2];
+        const double feq = W[i] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+        const double S = W[i] * (3.0 * (cF - uF) + 9.0 * cu * cF);
+        fstar[i] = f[i] - omega * (f[i] - feq) + (1.0 - 0.5 * omega) * S;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* field operations                                                    */
+/* ------------------------------------------------------------------ */
+
+/* f = feq(rho, u) in every cell; rho == NULL means 1, u == NULL means 0. */
+void orc_init_equilibrium(const orc_cfg *g, const double *rho, const double *u, double *f)
+{
+    const int64_t n = ncells(g);
+    for (int64_t cell = 0; cell < n; ++cell) {
+        const double r = rho ? rho[cell] : 1.0;
+        double uc[3] = {0.0, 0.0, 0.0};
+        if (u)
+            for (int a = 0; a < 3; ++a) uc[a] = u[a * n + cell];
+        double feq[Q];
+        orc_equilibrium(r, uc, feq);
+        for (int i = 0; i < Q; ++i) f[i * n + cell] = feq[i];
+    }
+}
+
+/* One time step, f_in -> f_out (two lattices, f_out fully overwritten). */
+void orc_step(const orc_cfg *g, const double *f_in, double *f_out)
+{
+    const int64_t n = ncells(g);
+#pragma omp parallel for schedule(static)
+    for (int64_t z = 0; z < g->nz; ++z)
+        for (int64_t y = 0; y < g->ny; ++y)
+            for (int64_t x = 0; x < g->nx; ++x) {
+                const int64_t cell = cell_index(g, x, y, z);
+                double f[Q], fs[Q], F[3];
+                for (int i = 0; i < Q; ++i) f[i] = f_in[i * n + cell];
+                cell_force(g, cell, F);
+                orc_collide_cell(g->tau, f, F, fs);
+                for (int i = 0; i < Q; ++i) {
+                    int64_t t;
+                    int lid;
+                    if (link_target(g, x, y, z, i, &t, &lid))
+                        f_out[i * n + t] = fs[i];
+                    else
+                        f_out[OPP(i) * n + cell] = fs[i] - wall_term(g, i, lid);
+                }
+            }
+}
+
+/* f^{t+1} at selected cells only: out[k][19] for the cells xyz[k] = (x,y,z).
+ * Each population is fetched from the cell it streams out of (the cell
+ * x - c_i, or x itself across a wall link), which is collided on the way --
+ * the same rule as orc_step read from the receiving side, so that single
+ * cells of a large lattice can be checked without stepping all of it. */
+void orc_step_cells(const orc_cfg *g, const double *f_in, const int64_t *xyz, int64_t count, double *out)
+{
+    const int64_t n = ncells(g);
+    for (int64_t k = 0; k < count; ++k) {
+        const int64_t x = xyz[3 * k], y = xyz[3 * k + 1], z = xyz[3 * k + 2];
+        for (int i = 0; i < Q; ++i) {
+            int64_t src;
+            int lid;
+            double f[Q], fs[Q], F[3];
+            if (link_target(g, x, y, z, OPP(i), &src, &lid)) {
+                for (int j = 0; j < Q; ++j) f[j] = f_in[j * n + src];
+                cell_force(g, src, F);
+                orc_collide_cell(g->tau, f, F, fs);
+                out[k * Q + i] = fs[i];
+            } else {
+                const int64_t self = cell_index(g, x, y, z);
+                for (int j = 0; j < Q; ++j) f[j] = f_in[j * n + self];
+                cell_force(g, self, F);
+                orc_collide_cell(g->tau, f, F, fs);
+                out[k * Q + i] = fs[OPP(i)] - wall_term(g, OPP(i), lid);
+            }
+        }
+    }
+}
+
+/* nsteps time steps in place on f; tmp is a second lattice of the same size. */
+void orc_run(const orc_cfg *g, double *f, int64_t nsteps, double *tmp)
+{
+    const int64_t n = ncells(g);
+    for (int64_t s = 0; s < nsteps; ++s) {
+        orc_step(g, f, tmp);
+        memcpy(f, tmp, sizeof(double) * (size_t)(Q * n));
+    }
+}
+
+/* rho[N] and u[3][N] of the post-stream state, u including half the force. */
+void orc_moments(const orc_cfg *g, const double *f, double *rho, double *u)
+{
+    const int64_t n = ncells(g);
+    for (int64_t cell = 0; cell < n; ++cell) {
+        double r = 0.0, m[3] = {0.0, 0.0, 0.0}, F[3];
+        for (int i = 0; i < Q; ++i) {
+            r += f[i * n + cell];
+            for (int a = 0; a < 3; ++a) m[a] += f[i * n + cell] * C[i][a];
+        }
+        cell_force(g, cell, F);
+        rho[cell] = r;
+        for (int a = 0; a < 3; ++a) u[a * n + cell] = (m[a] + 0.5 * F[a]) / r;
+    }
+}
+
+/* out = {sum rho, sum_x sum_i f_i c_ix, ...y, ...z, sum 1/2 rho |u|^2},
+ * summed cell by cell in canonical order. */
+void orc_reduce(const orc_cfg *g, const double *f, double *out)
+{
+    const int64_t n = ncells(g);
+    double M = 0.0, P[3] = {0.0, 0.0, 0.0}, KE = 0.0;
+    for (int64_t cell = 0; cell < n; ++cell) {
+        double r = 0.0, m[3] = {0.0, 0.0, 0.0}, F[3];
+        for (int i = 0; i < Q; ++i) {
+            r += f[i * n + cell];
+            for (int a = 0; a < 3; ++a) m[a] += f[i * n + cell] * C[i][a];
+        }
+        cell_force(g, cell, F);
+        double usq = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double ua = (m[a] + 0.5 * F[a]) / r;
+            usq += ua * ua;
+        }
+        M += r;
+        for (int a = 0; a < 3; ++a) P[a] += m[a];
+        KE += 0.5 * r * usq;
+    }
+    out[0] = M;
+    out[1] = P[0];
+    out[2] = P[1];
+    out[3] = P[2];
+    out[4] = KE;
+}
+
+/* ------------------------------------------------------------------ */
+/* discrete adjoint (no counterpart in the paper)                      */
+/* ------------------------------------------------------------------ */
+
+/* Reverse of orc_step: given f_t (the state the forward step started from)
+ * and lam_next = dL/df^{t+1}, write lam_t = dL/df^t and add dL/dF (per cell,
+ * through this step) to gF[3][N]. */
+void orc_adjoint_step(const orc_cfg *g, const double *f_t, const double *lam_next,
+                      double *lam_t, double *gF)
+{
+    const int64_t n = ncells(g);
+    const double omega = 1.0 / g->tau;
+    const double k = 1.0 - 0.5 * omega;
+#pragma omp parallel for schedule(static)
+    for (int64_t z = 0; z < g->nz; ++z)
+        for (int64_t y = 0; y < g->ny; ++y)
+            for (int64_t x = 0; x < g->nx; ++x) {
+                const int64_t cell = cell_index(g, x, y, z);
+                double f[Q], F[3], mu[Q];
+                for (int i = 0; i < Q; ++i) f[i] = f_t[i * n + cell];
+                cell_force(g, cell, F);
+                double rho = 0.0, m[3] = {0.0, 0.0, 0.0}, u[3];
+                for (int i = 0; i < Q; ++i) {
+                    rho += f[i];
+                    for (int a = 0; a < 3; ++a) m[a] += f[i] * C[i][a];
+                }
+                for (int a = 0; a < 3; ++a) u[a] = (m[a] + 0.5 * F[a]) / rho;
+                const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+                /* mu_i = dL/df*_i: transpose of the streaming map */
+                for (int i = 0; i < Q; ++i) {
+                    int64_t t;
+                    int lid;
+                    if (link_target(g, x, y, z, i, &t, &lid))
+                        mu[i] = lam_next[i * n + t];
+                    else
+                        mu[i] = lam_next[OPP(i) * n + cell];
+                }
+                double A = 0.0, B[3] = {0.0, 0.0, 0.0}, S[3] = {0.0, 0.0, 0.0};
+                double G[3] = {0.0, 0.0, 0.0};
+                for (int i = 0; i < Q; ++i) {
+                    const double cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
+                    const double cF = C[i][0] * F[0] + C[i][1] * F[1] + C[i][2] * F[2];
+                    /* d feq_i / d rho */
+                    A += mu[i] * W[i] * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+                    for (int a = 0; a < 3; ++a) {
+                        /* d feq_i / d u_a */
+                        B[a] += mu[i] * W[i] * rho * (3.0 * C[i][a] + 9.0 * cu * C[i][a] - 3.0 * u[a]);
+                        /* d S_i / d u_a */
+                        S[a] += mu[i] * W[i] * (-3.0 * F[a] + 9.0 * cF * C[i][a]);
+                        /* d S_i / d F_a at fixed u */
+                        G[a] += mu[i] * W[i] * (3.0 * (C[i][a] - u[a]) + 9.0 * cu * C[i][a]);
+                    }
+                }
+                double E[3];
+                for (int a = 0; a < 3; ++a) E[a] = omega * B[a] + k * S[a];
+                for (int j = 0; j < Q; ++j) {
+                    double v = (1.0 - omega) * mu[j] + omega * A;
+                    for (int a = 0; a < 3; ++a) v += E[a] * (C[j][a] - u[a]) / rho;
+                    lam_t[j * n + cell] = v;
+                }
+                for (int a = 0; a < 3; ++a) gF[a * n + cell] += k * G[a] + E[a] / (2.0 * rho);
+            }
+}
+
+/* Seed of the reverse sweep for a loss of the output moments (rho, u) of
+ * state f: lam = dL/df, gF += dL/dF through u's half-force term.
+ * dLdrho may be NULL (loss independent of rho). */
+void orc_adjoint_seed(const orc_cfg *g, const double *f, const double *dLdrho,
+                      const double *dLdu, double *lam, double *gF)
+{
+    const int64_t n = ncells(g);
+    for (int64_t cell = 0; cell < n; ++cell) {
+        double r = 0.0, m[3] = {0.0, 0.0, 0.0}, F[3], u[3];
+        for (int i = 0; i < Q; ++i) {
+            r += f[i * n + cell];
+            for (int a = 0; a < 3; ++a) m[a] += f[i * n + cell] * C[i][a];
+        }
+        cell_force(g, cell, F);
+        for (int a = 0; a < 3; ++a) u[a] = (m[a] + 0.5 * F[a]) / r;
+        for (int j = 0; j < Q; ++j) {
+            double v = dLdrho ? dLdrho[cell] : 0.0;
+            for (int a = 0; a < 3; ++a) v += dLdu[a * n + cell] * (C[j][a] - u[a]) / r;
+            lam[j * n + cell] = v;
+        }
+        for (int a = 0; a < 3; ++a) gF[a * n + cell] += dLdu[a * n + cell] / (2.0 * r);
+    }
+}
