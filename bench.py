@@ -1,0 +1,475 @@
+#!/usr/bin/env python3
+"""Throughput of the D3Q19 hot path on GB300: MLUPS and the HBM roofline.
+
+Workload (the benchmark configuration): lid-driven cavity 256^3, D3Q19 BGK,
+tau = 0.55, lid u = (0.05, 0, 0) on the z+ face, half-way bounce-back on the
+other five faces, fluid at rest at t = 0; FP32 storage and arithmetic; the
+two-step merged single-copy schedule.  One benchmark step = one merged sweep
+= two lattice time steps over all 16.8 M cells.  MLUPS counts every cell as a
+fluid node (million lattice-node updates per second).
+
+Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs an
+independent replica on its own GPU (the update shards only through a halo
+exchange that this single-GPU build does not implement): value = the cells
+all ranks updated / the slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle (the plain two-lattice
+definition of the step, OpenMP on the host cores) on a bounded sample of the
+same workload and prints the same line with ``"impl": "reference"``.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D3Q19 MLUPS and % of HBM roofline per precision; adjoint/forward step ratio"
+UNIT = "MLUPS"
+TAU = 0.55
+U_LID = (0.05, 0.0, 0.0)
+FALLBACK_HBM_GBS = 6800.0
+Q = 19
+ELEM = {"f64": 8, "f32": 4, "f32s": 4, "f16s": 2, "bf16s": 2}
+DTYPE_NAME = {"f64": "f64", "f32": "f32", "f32s": "f32", "f16s": "f32 (f16 storage)", "bf16s": "f32 (bf16 storage)"}
+
+
+def workload_name(n: int) -> str:
+    return (f"lid-driven cavity {n}^3, D3Q19 BGK, tau={TAU}, lid u=(0.05,0,0) on z+, half-way bounce-back "
+            f"on the other faces, initial rest state")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000, help="timed merged sweeps (2 time steps each)")
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--size", type=int, default=256)
+    p.add_argument("--storage", default="f32", choices=sorted(ELEM))
+    p.add_argument("--variant", default="merged", choices=["merged", "aa", "two_lattice"])
+    p.add_argument("--tile-y", type=int, default=0)
+    p.add_argument("--no-extras", action="store_true", help="skip the per-variant, adjoint and CPU legs")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle baseline")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_digest() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2208_05429_gb300", "csrc", "*"))):
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(key: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        ent = d.get(key)
+        if ent and ent.get("kernel_digest") == kernel_digest():
+            return float(ent["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[4:]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        max_mhz = max(r[1] for r in rows)
+        loaded = [r for r in rows if r[0] > 0.5 * max_mhz] or rows
+        reasons = set()
+        names = ["active_mask", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names[1:], r[2][1:]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max_mhz,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def sync_all(dist_on):
+    import torch
+    torch.cuda.synchronize()
+    if dist_on:
+        import torch.distributed as dist
+        dist.barrier()
+        torch.cuda.synchronize()
+
+
+# ------------------------------------------------------------------ GPU legs
+
+def make_cavity(n, storage, variant, tile_y=0):
+    from paper_2208_05429_gb300.lbm import CAVITY_BC, Lattice
+    return Lattice((n, n, n), TAU, bc=CAVITY_BC, u_lid=U_LID, storage=storage, variant=variant,
+                   tile=(32 if tile_y else 0, tile_y))
+
+
+def alg_bytes_per_launch(kernel: str, storage: str, cells: int) -> float:
+    """Algorithmic DRAM bytes of one launch: every population read and written
+    once per round trip (a merged sweep is one round trip for two steps)."""
+    return 2.0 * Q * ELEM[storage] * cells
+
+
+def time_variant(n, storage, variant, steps, warmup, dist_on=False, tile_y=0):
+    """(elapsed ms over `steps` calls of step(2), per-kernel records, lattice)."""
+    import torch
+    lat = make_cavity(n, storage, variant, tile_y)
+    lat.init_equilibrium()
+    for _ in range(warmup):
+        lat.step(2)
+    sync_all(dist_on)
+    st = lat.stream
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    lat.profile(True)
+    start.record(st)
+    for _ in range(steps):
+        lat.step(2)
+    end.record(st)
+    end.synchronize()
+    lat.profile(False)
+    sync_all(dist_on)
+    return start.elapsed_time(end), lat.profile_read(), lat
+
+
+def roofline_of(prof, kernel, storage, cells, peak, peak_kind):
+    if kernel not in prof:
+        return None
+    launches, ms = prof[kernel]
+    avg = ms / launches
+    byts = alg_bytes_per_launch(kernel, storage, cells)
+    achieved = byts / (avg * 1e-3) / 1e9
+    traffic = recorded_traffic(f"{kernel}_{storage}_{round(cells ** (1 / 3))}")
+    return {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+            "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+            "alg_bytes_per_launch": byts, "avg_launch_ms": round(avg, 5), "launches": launches}
+
+
+def e2e_leg(n, storage, variant, steps, warmup):
+    """Same metric end to end through the public API with host buffers: the
+    timed region uploads the initial populations from pinned host memory,
+    runs the steps with an FP64 mass/momentum/energy read-back every 100 time
+    steps, and downloads the final density and velocity fields."""
+    import torch
+    lat = make_cavity(n, storage, variant)
+    lat.init_equilibrium()
+    host_f = lat.populations(torch.float32).cpu().pin_memory()
+    dev_f = torch.empty_like(host_f, device=lat.device)
+    host_rho = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
+    host_u = torch.empty((3, n, n, n), dtype=torch.float32).pin_memory()
+    for _ in range(warmup):
+        lat.step(2)
+    torch.cuda.synchronize()
+    st = lat.stream
+    every = 50
+    reads = 0
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st):
+        start.record(st)
+        dev_f.copy_(host_f, non_blocking=True)
+        lat.init_populations(dev_f)
+        for k in range(steps):
+            lat.step(2)
+            if (k + 1) % every == 0:
+                lat.reduce()
+                reads += 1
+        rho, u = lat.moments(torch.float32)
+        host_rho.copy_(rho, non_blocking=True)
+        host_u.copy_(u, non_blocking=True)
+        end.record(st)
+    end.synchronize()
+    ms = start.elapsed_time(end)
+    cells = n ** 3
+    h2d = host_f.numel() * 4
+    d2h = (host_rho.numel() + host_u.numel()) * 4 + reads * 5 * 8
+    return {"value": round(cells * 2 * steps / (ms * 1e3), 1), "unit": UNIT,
+            "h2d_bytes_per_step": round(h2d / steps, 1), "d2h_bytes_per_step": round(d2h / steps, 1),
+            "ms": round(ms, 3),
+            "what": "pinned host populations -> device, steps with an FP64 reduction read every 100 time "
+                    "steps, final rho and u -> pinned host; bytes per step amortised over the run"}
+
+
+def adjoint_leg():
+    """Adjoint/forward time ratio on the differentiable channel workload
+    (128 x 64 x 64, periodic x, walls y and z, tau 0.6, 200 steps,
+    checkpoint every 20, per-cell force, FP32)."""
+    import torch
+    from paper_2208_05429_gb300 import inputs
+    from paper_2208_05429_gb300.lbm import Lattice
+    NX, NY, NZ, T, K = 128, 64, 64, 200, 20
+    F = torch.tensor(inputs.channel_force(NX, NY, NZ), device="cuda")
+    bc = ("periodic", "periodic", "wall", "wall", "wall", "wall")
+    lat = Lattice((NX, NY, NZ), 0.6, bc=bc, storage="f32", variant="merged", force=F)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    st = lat.stream
+    res = {}
+    for rep in range(2):
+        lat.init_equilibrium()
+        ev[0].record(st)
+        lat.step(T)
+        ev[1].record(st)
+        lat.init_equilibrium()
+        ev[2].record(st)
+        lat.adjoint_forward(T, K)
+        ev[3].record(st)
+        _, u = lat.moments(torch.float32)
+        target = torch.tensor(inputs.parabolic_target(NY, NZ), device=u.device, dtype=torch.float32)
+        g = torch.zeros_like(u)
+        g[0, :, :, NX - 1] = 2.0 * (u[0, :, :, NX - 1] - target) / target.numel()
+        ev[4].record(st)
+        lat.adjoint_backward(g)
+        ev[5].record(st)
+        torch.cuda.synchronize()
+        res = {"forward_ms": ev[0].elapsed_time(ev[1]), "checkpointed_forward_ms": ev[2].elapsed_time(ev[3]),
+               "backward_ms": ev[4].elapsed_time(ev[5])}
+    res = {k: round(v, 3) for k, v in res.items()}
+    res["ratio"] = round(res["backward_ms"] / res["forward_ms"], 3)
+    res["workload"] = "channel 128x64x64, 200 steps, checkpoint every 20, FP32; ratio = backward / plain forward"
+    return res
+
+
+# ------------------------------------------------------------------ CPU legs
+
+def oracle_mlups(n, budget_s, pairs=None):
+    """Time the FP64 oracle (two lattices, OpenMP) on an n^3 cavity: runs
+    `pairs` double steps, or as many as fit in budget_s (at least one)."""
+    import numpy as np
+    import oracle
+    cfg = oracle.cavity(n, TAU, u_lid=U_LID)
+    f = oracle.init_equilibrium(cfg)
+    g = np.empty_like(f)
+    oracle.step(cfg, f)  # warm the library and the pages
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle._load().orc_step(__import__("ctypes").byref(cfg._c()), oracle._ptr(f), oracle._ptr(g))
+        oracle._load().orc_step(__import__("ctypes").byref(cfg._c()), oracle._ptr(g), oracle._ptr(f))
+        done += 2
+        el = time.perf_counter() - t0
+        if pairs is not None:
+            if done >= 2 * pairs:
+                break
+        elif el >= budget_s:
+            break
+    return n ** 3 * done / el / 1e6, done, el
+
+
+def omp_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    # pick the largest sample edge whose estimated run fits ~2 minutes
+    total_pairs = args.steps + args.warmup
+    edge = 32
+    for cand in (args.size, 192, 128, 96, 64, 48, 32):
+        if cand > args.size:
+            continue
+        rate, _, _ = oracle_mlups(cand, 0.0, pairs=1)
+        est = 2 * total_pairs * cand ** 3 / (rate * 1e6)
+        if est <= 120.0:
+            edge = cand
+            break
+    oracle_mlups(edge, 0.0, pairs=max(args.warmup, 0) or 1)
+    rate, done, el = oracle_mlups(edge, 0.0, pairs=args.steps)
+    cores = omp_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(rate, 3), "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.size), "sample": f"{edge}^3 cavity of the same setup",
+                   "time_steps_per_step": 2},
+        "cpu_baseline": {"value": round(rate, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{done} time steps of a {edge}^3 cavity (same tau, lid and walls), "
+                                   f"FP64 two-lattice oracle, OpenMP {cores} threads"},
+        "e2e": {"value": round(rate, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ main
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist_on = world > 1
+    if dist_on:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+
+    from paper_2208_05429_gb300 import build
+    if rank == 0 or not dist_on:
+        build.build()
+    if dist_on:
+        import torch.distributed as dist
+        dist.barrier()
+
+    n = args.size
+    cells = n ** 3
+    peak, peak_kind = measured_peaks()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, prof, lat = time_variant(n, args.storage, args.variant, args.steps, args.warmup, dist_on, args.tile_y)
+    clocks = sampler.stop()
+    if dist_on:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # mass check of the timed state: a broken kernel shows up here
+    mass = lat.reduce()[0]
+    ok = abs(mass - cells) / cells < 1e-5
+    del lat
+
+    value = world * cells * 2 * args.steps / (ms * 1e3)
+    dominant = "merged" if args.variant == "merged" else ("aa_odd" if args.variant == "aa" else "two_lattice")
+    roof = roofline_of(prof, dominant, args.storage, cells, peak, peak_kind)
+    launches = sum(v[0] for v in prof.values())
+    if "snapshot" in prof and roof is not None:
+        sn, sms = prof["snapshot"]
+        mn, mms = prof["merged"]
+        roof["snapshot_avg_launch_ms"] = round(sms / sn, 5)
+        roof["step_frac_of_peak_alg"] = round(alg_bytes_per_launch("merged", args.storage, cells) /
+                                              ((sms + mms) / mn * 1e-3) / 1e9 / peak, 4)
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[args.storage], "data": "synthetic",
+        "config": {"workload": workload_name(n), "cells": cells, "time_steps_per_step": 2,
+                   "storage": args.storage, "variant": args.variant,
+                   "l2": "no flush: the populations (%.2f GB) are larger than the 129 MB L2" %
+                         (Q * ELEM[args.storage] * cells / 1e9),
+                   "parallelism": "independent replicas, one per GPU" if dist_on else "single GPU"},
+        "roofline": roof, "gpu_launches": launches, "clocks": clocks, "mass_conserved": bool(ok),
+    }
+
+    if rank == 0 and not args.no_extras:
+        try:
+            line["e2e"] = e2e_leg(n, args.storage, args.variant, min(args.steps, 1000), 3)
+        except Exception as e:  # keep the main line if a secondary leg fails
+            line["e2e"] = {"error": repr(e)}
+        variants = {}
+        for st, var in (("f32", "aa"), ("f32", "two_lattice"), ("f16s", "merged"), ("bf16s", "merged"),
+                        ("f16s", "aa"), ("f64", "merged")):
+            if (st, var) == (args.storage, args.variant):
+                continue
+            k = min(args.steps, 300)
+            vms, vprof, vl = time_variant(n, st, var, k, 5)
+            del vl
+            dk = "merged" if var == "merged" else ("aa_odd" if var == "aa" else "two_lattice")
+            r = roofline_of(vprof, dk, st, cells, peak, peak_kind)
+            variants[f"{var}_{st}"] = {"MLUPS": round(cells * 2 * k / (vms * 1e3), 1),
+                                       "kernel_frac_of_peak": r["frac"] if r else None,
+                                       "kernel": dk}
+        line["variants"] = variants
+        try:
+            line["adjoint"] = adjoint_leg()
+        except Exception as e:
+            line["adjoint"] = {"error": repr(e)}
+        if not dist_on:
+            import oracle
+            oracle.build()
+            rate, done, el = oracle_mlups(n, args.cpu_seconds)
+            line["cpu_baseline"] = {
+                "value": round(rate, 3), "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
+                "sample": f"{done} time steps of the {n}^3 cavity itself, FP64 two-lattice oracle "
+                          f"({el:.1f} s, OpenMP)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist_on:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,247 @@
+/*
+ * lbm.h -- C ABI of the GB300 D3Q19 lattice Boltzmann library.
+ *
+ * The library advances a 3D D3Q19 BGK lattice (Guo body force, periodic or
+ * half-way bounce-back faces, one moving lid) on one GPU, in place, with a
+ * single copy of the populations.  It implements the hot path of Fu & Song,
+ * "Designing a 3D Parallel Memory-Aware Lattice Boltzmann Algorithm on
+ * Manycore Systems" (arXiv 2208.05429): the fused collide-and-stream update
+ * (Sec. 3, Alg. 1) and its merge of two collision-streaming cycles into one
+ * sweep over memory (Sec. 4.1, Alg. 2; Sec. 4.2, Alg. 3), re-designed for the
+ * GPU as an AA-pattern even/odd pair and a tiled kernel that performs both
+ * steps per HBM round trip.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: an lbm_status (0 = success, negative = error).  Nothing
+ *    throws across the ABI; lbm_strerror() gives a static message.
+ *  - Pointers documented as "device" are CUDA device pointers owned by the
+ *    caller (for example torch tensors); the library never frees them and
+ *    only reads/writes them on the handle's stream.  Arguments documented as
+ *    "host" are plain host memory.
+ *  - Canonical field layout (inputs and outputs): x fastest, then y, then z:
+ *      scalar field  a[z][y][x]              (N = nx*ny*nz elements)
+ *      vector field  a[3][z][y][x]           (component-major)
+ *      populations   f[19][z][y][x]          (direction-major, directions
+ *                                             in the order lbm_lattice() reports)
+ *  - Every launch is asynchronous on the stream given at creation.  Only
+ *    lbm_reduce() and lbm_adjoint_* with host outputs synchronise it.
+ *  - A handle is not thread-safe; use one handle per host thread.
+ *  - The populations held by a handle always represent the post-stream state
+ *    f^n after n time steps; the AA parity used internally is hidden.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_handle lbm_handle;
+
+/* Status codes. */
+enum lbm_status {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,        /* invalid argument or configuration            */
+    LBM_ENOMEM = -2,        /* device allocation failed / buffer too small  */
+    LBM_ECUDA = -3,         /* a CUDA runtime call failed                   */
+    LBM_ESTATE = -4,        /* call not valid in the handle's current state */
+    LBM_ENONFINITE = -5,    /* a reduction met a NaN or Inf                 */
+    LBM_ETIMEOUT = -6,      /* a bounded device wait gave up                */
+    LBM_EUNSUPPORTED = -7   /* combination not built in this library        */
+};
+
+/* Face boundary types; faces are ordered x-, x+, y-, y+, z-, z+.  The two
+ * faces of one axis are either both PERIODIC or both non-periodic. */
+enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_LID = 2 };
+
+/* Population storage.  F64 and F32 store f_i; the "S" forms store the
+ * shifted value f_i - w_i (w_i the lattice weight), which keeps the small
+ * deviations from rest at full relative precision.  All forms except F64
+ * compute in FP32 registers; F64 computes in FP64. */
+enum { LBM_STORAGE_F64 = 0, LBM_STORAGE_F32 = 1, LBM_STORAGE_F32S = 2,
+       LBM_STORAGE_F16S = 3, LBM_STORAGE_BF16S = 4 };
+
+/* Update schedule.  All three give bit-identical populations for the same
+ * storage (Sec. 5.1 of the paper verifies its two-step solvers against the
+ * single-step ones the same way).
+ *   TWO_LATTICE  fused collide-and-push into a second lattice (reference
+ *                form of Alg. 1; needs twice the population memory)
+ *   AA           single copy: even step collides in place into the opposite
+ *                slots (the "revert" of Sec. 3), odd step gathers, collides
+ *                and scatters (the "swap_stream" half of Sec. 3)
+ *   MERGED       single copy, two time steps per sweep (Sec. 4): a tiled
+ *                kernel marching z performs the even and the odd step of a
+ *                column in one pass; a pre-pass snapshots the tile shells so
+ *                that tiles never read what a neighbouring tile has already
+ *                overwritten (the role of Stage I of Alg. 3). */
+enum { LBM_VARIANT_TWO_LATTICE = 0, LBM_VARIANT_AA = 1, LBM_VARIANT_MERGED = 2 };
+
+/* Body force (Guo forcing): none, one vector for every cell, or a per-cell
+ * FP32 field [3][z][y][x] set with lbm_set_force(). */
+enum { LBM_FORCE_NONE = 0, LBM_FORCE_UNIFORM = 1, LBM_FORCE_FIELD = 2 };
+
+/* Element type of caller-provided field buffers. */
+enum { LBM_DTYPE_F32 = 0, LBM_DTYPE_F64 = 1 };
+
+typedef struct lbm_config {
+    int64_t nx, ny, nz;       /* cells per axis, each >= 1                     */
+    double tau;               /* BGK relaxation time, > 0.5                    */
+    int32_t face_bc[6];       /* x-, x+, y-, y+, z-, z+ (LBM_BC_*)             */
+    double u_lid[3];          /* velocity of every LID face, |u_lid| < 0.3     */
+    double rho_wall;          /* density in the moving-wall term (default 1)   */
+    int32_t storage;          /* LBM_STORAGE_*                                 */
+    int32_t variant;          /* LBM_VARIANT_*                                 */
+    int32_t force_mode;       /* LBM_FORCE_*                                   */
+    double force_uniform[3];  /* the force of LBM_FORCE_UNIFORM                */
+    int32_t tile_x, tile_y;   /* MERGED tile shape; 0 = library default        */
+} lbm_config;
+
+/* Fill cfg with a 32^3 fully periodic FP32 AA lattice, tau = 0.6. */
+void lbm_config_default(lbm_config *cfg);
+
+/* Check a configuration without allocating.  LBM_EINVAL on: a dimension < 1,
+ * cell count beyond 2^31, tau <= 0.5, a face type out of range, an axis with
+ * one periodic and one non-periodic face, |u_lid| >= 0.3, rho_wall <= 0,
+ * unknown storage/variant/force mode, negative tile sizes or a tile_x that is
+ * not a multiple of 32. */
+int lbm_validate(const lbm_config *cfg);
+
+/* Device bytes a handle of this configuration uses (populations, second
+ * lattice for TWO_LATTICE, tile-shell snapshot for MERGED, reduction
+ * scratch), each region aligned to 256 bytes.  *bytes is a host output. */
+int lbm_required_bytes(const lbm_config *cfg, size_t *bytes);
+
+/* Create a handle that allocates its own device memory (cudaMalloc on the
+ * current device) and launches on `stream` (a cudaStream_t; NULL = legacy
+ * default stream).  Populations start at zero: call lbm_init_equilibrium()
+ * or lbm_init_populations() before stepping.  *out receives the handle. */
+int lbm_create(const lbm_config *cfg, void *stream, lbm_handle **out);
+
+/* Same as lbm_create() but uses `device_buffer` (device, at least
+ * lbm_required_bytes() bytes, 256-byte aligned, owned by the caller and
+ * kept alive until lbm_destroy()).  LBM_ENOMEM if `bytes` is too small. */
+int lbm_create_with_buffer(const lbm_config *cfg, void *stream, void *device_buffer,
+                           size_t bytes, lbm_handle **out);
+
+/* Release the handle (and the memory lbm_create() allocated).  NULL is a
+ * no-op.  Synchronises the handle's stream first. */
+void lbm_destroy(lbm_handle *h);
+
+/* Static message for a status code. */
+const char *lbm_strerror(int status);
+
+/* The library's D3Q19 table: c[19][3] integer velocities and w[19] weights
+ * (host outputs, either may be NULL).  Directions 1..9 are those whose first
+ * non-zero component is -1 (the half of the neighbours the swap algorithm of
+ * Sec. 3 streams to), direction i+9 is the opposite of i, 0 is rest. */
+int lbm_lattice(int32_t *c, double *w);
+
+/* Populations of every cell := equilibrium feq(rho, u) (second-order BGK
+ * equilibrium) and the time counter := 0.  rho: device [z][y][x] or NULL
+ * (rho = 1); u: device [3][z][y][x] or NULL (u = 0); both of element type
+ * `dtype`.  This is the initial state of the cavity of Sec. 5.1. */
+int lbm_init_equilibrium(lbm_handle *h, const void *rho, const void *u, int32_t dtype);
+
+/* Set the per-cell body force used when force_mode == LBM_FORCE_FIELD.
+ * F: device FP32 [3][z][y][x], borrowed: it must stay valid and unchanged
+ * while steps are in flight.  LBM_ESTATE for other force modes. */
+int lbm_set_force(lbm_handle *h, const float *F);
+
+/* Advance n >= 0 time steps (one step = collide then stream, Sec. 3).  With
+ * MERGED, pairs of steps run as one merged sweep (Sec. 4) and an odd
+ * remainder as one AA step.  Asynchronous on the handle's stream. */
+int lbm_step(lbm_handle *h, int64_t n);
+
+/* Time steps taken since the last init (host output). */
+int lbm_time(const lbm_handle *h, int64_t *t);
+
+/* Density and velocity of the current state (the per-cell velocity norm the
+ * paper's verification logs is |u|, Sec. 5.1): rho = sum_i f_i,
+ * u = (sum_i f_i c_i + F/2) / rho.  rho: device [z][y][x] or NULL; u: device
+ * [3][z][y][x] or NULL; element type `dtype`. */
+int lbm_moments(lbm_handle *h, void *rho, void *u, int32_t dtype);
+
+/* Copy out the post-stream populations f^n in canonical layout
+ * f[19][z][y][x] (device, element type `dtype`, directions as lbm_lattice()). */
+int lbm_populations(lbm_handle *h, void *f_out, int32_t dtype);
+
+/* Replace the state with caller populations f_in (device, canonical layout,
+ * element type `dtype`, rounded to the storage format) and reset time to 0. */
+int lbm_init_populations(lbm_handle *h, const void *f_in, int32_t dtype);
+
+/* Global FP64 sums of the current state, written to out[5] (host):
+ *   out[0] = sum rho              (mass)
+ *   out[1..3] = sum_cells sum_i f_i c_i   (momentum, without the half force)
+ *   out[4] = sum 1/2 rho |u|^2    (kinetic energy, u as in lbm_moments)
+ * Deterministic (fixed summation tree).  Synchronises the stream.
+ * LBM_ENONFINITE if any cell has a non-finite density or velocity; out is
+ * still written. */
+int lbm_reduce(lbm_handle *h, double *out);
+
+/* ---------------- per-kernel timing ----------------
+ * Kernel classes launched by lbm_step(). */
+enum { LBM_KERNEL_TWO_LATTICE = 0, LBM_KERNEL_AA_EVEN = 1, LBM_KERNEL_AA_ODD = 2,
+       LBM_KERNEL_SNAPSHOT = 3, LBM_KERNEL_MERGED = 4, LBM_KERNEL_COUNT = 5 };
+
+/* enable = 1: from now on every kernel lbm_step() launches is bracketed by
+ * two CUDA events recorded on the handle's stream (earlier records are
+ * dropped); enable = 0 stops recording and keeps the records.  The events
+ * are created on first use and owned by the handle. */
+int lbm_profile(lbm_handle *h, int32_t enable);
+
+/* Launch count and summed device time (milliseconds, from the events) of
+ * one kernel class (LBM_KERNEL_*) since profiling was last enabled; host
+ * outputs.  Synchronises on the recorded events. */
+int lbm_profile_read(lbm_handle *h, int32_t kernel, int64_t *launches, double *total_ms);
+
+/* ---------------- adjoint (reverse-mode) ----------------
+ * The reverse of one step f^t -> f^{t+1} of this handle's configuration,
+ * derived by hand from the collide and stream rules above (the paper has no
+ * counterpart).  The wall-density rho_wall is a constant, so the lid term
+ * carries no derivative.  Computation in the handle's compute precision,
+ * gradient accumulation in FP64. */
+
+/* lambda_out = (d f^{t+1} / d f^t)^T lambda_in, and dLdF += (d f^{t+1}/dF)^T
+ * lambda_in per cell.  f_t: device canonical populations of the state the
+ * forward step started from; lambda_in / lambda_out: device canonical
+ * populations (distinct buffers); all three of element type `dtype`.
+ * dLdF: device FP64 [3][z][y][x], accumulated (may be NULL). */
+int lbm_adjoint_step(lbm_handle *h, const void *f_t, const void *lambda_in, void *lambda_out,
+                     int32_t dtype, double *dLdF);
+
+/* Seed of the reverse sweep for a loss L(rho, u) of the moments of the
+ * current state: lambda = dL/df (device canonical, `dtype`), and
+ * dLdF += dL/du / (2 rho) (the half-force path of u; FP64, may be NULL).
+ * dLdrho: device [z][y][x] or NULL; dLdu: device [3][z][y][x]; both `dtype`. */
+int lbm_adjoint_seed(lbm_handle *h, const void *dLdrho, const void *dLdu, void *lambda,
+                     int32_t dtype, double *dLdF);
+
+/* Workspace bytes for lbm_adjoint_forward/backward with T steps and a
+ * checkpoint every K steps: ceil(T/K)+1 checkpoints, K recompute states and
+ * two adjoint buffers.  Host output. */
+int lbm_adjoint_workspace_bytes(const lbm_handle *h, int64_t T, int64_t K, size_t *bytes);
+
+/* Run T >= 1 steps forward from the current state (which becomes f^0),
+ * keeping a checkpoint every K >= 1 steps in `work` (device, at least the
+ * bytes above, owned by the caller and left untouched until
+ * lbm_adjoint_backward returns).  Leaves the handle at f^T, bit-identical to
+ * lbm_step(T). */
+int lbm_adjoint_forward(lbm_handle *h, int64_t T, int64_t K, void *work, size_t work_bytes);
+
+/* Reverse sweep of the last lbm_adjoint_forward: seeds with dL/drho, dL/du of
+ * f^T (device, `dtype`, dLdrho may be NULL), recomputes each K-step segment
+ * from its checkpoint and applies lbm_adjoint_step backwards.  Writes
+ * dLdf0 = dL/df^0 (device canonical populations, `dtype`, may be NULL) and
+ * accumulates dLdF += dL/dF (device FP64 [3][z][y][x], may be NULL). */
+int lbm_adjoint_backward(lbm_handle *h, const void *dLdrho, const void *dLdu, int32_t dtype,
+                         void *dLdf0, double *dLdF, void *work, size_t work_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

@@ -1,0 +1,292 @@
+// d3q19.cuh -- device-side lattice, arithmetic, storage codecs and the BGK
+// collision shared by every kernel of the library.
+//
+// The collision (BGK with Guo forcing) is evaluated in the shifted form
+// s_i = f_i - w_i: delta_rho = sum s_i, j = sum s_i c_i, and
+//   feq_i - w_i = w_i (delta_rho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)),
+// which keeps the O(1e-2) deviations from rest at full FP32 precision.  Every
+// arithmetic step uses an explicitly rounded intrinsic (__fadd_rn, __fmaf_rn,
+// ...), so the compiler can neither contract nor reorder it: all kernels that
+// call bgk_collide() produce bit-identical results for the same inputs, which
+// is how TWO_LATTICE, AA and MERGED are made to agree bit for bit.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+#include <utility>
+
+namespace lbm {
+
+constexpr int Q = 19;
+
+// ---------------------------------------------------------------------------
+// D3Q19 velocity set.  Directions 1..9 have -1 as their first non-zero
+// component (the half of the neighbours that the swap scheme streams to,
+// Sec. 3 of the paper) and i+9 is the opposite of i.  Inside that rule the
+// listing is grouped by c_z, which the plane-marching kernel exploits.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int cx(int i)
+{
+    return i == 2 || i == 4 || i == 6 || i == 8 || i == 9 ? -1
+         : i == 11 || i == 13 || i == 15 || i == 17 || i == 18 ? 1 : 0;
+}
+__host__ __device__ constexpr int cy(int i)
+{
+    return i == 3 || i == 5 || i == 7 || i == 8 || i == 18 ? -1
+         : i == 12 || i == 14 || i == 16 || i == 17 || i == 9 ? 1 : 0;
+}
+__host__ __device__ constexpr int cz(int i)
+{
+    return i == 1 || i == 2 || i == 3 || i == 13 || i == 14 ? -1
+         : i == 4 || i == 5 || i == 10 || i == 11 || i == 12 ? 1 : 0;
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i <= 9 ? i + 9 : i - 9); }
+__host__ __device__ constexpr int csq(int i) { return cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i); }
+__host__ __device__ constexpr double wgt(int i)
+{
+    return csq(i) == 0 ? 1.0 / 3.0 : (csq(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = 0..N-1.
+template <class F, int... Is>
+__host__ __device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, Is...>)
+{
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F>
+__host__ __device__ __forceinline__ void static_for(F &&f)
+{
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// ---------------------------------------------------------------------------
+// Explicitly rounded arithmetic (no contraction, no reassociation).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a, b); }
+
+// c_i . (ax, ay, az) as a signed sum of the non-zero components (exact for
+// the unit components of D3Q19, no multiplications).
+template <int I, class R>
+__device__ __forceinline__ R cdot(R ax, R ay, R az)
+{
+    R v = R(0);
+    bool first = true;
+    auto acc = [&](int c, R a) {
+        if (c == 0) return;
+        if (first) { v = c > 0 ? a : -a; first = false; }
+        else v = c > 0 ? radd(v, a) : rsub(v, a);
+    };
+    acc(cx(I), ax);
+    acc(cy(I), ay);
+    acc(cz(I), az);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Storage codecs.  T = stored element, R = compute type.  decode() returns
+// the shifted value s_i = f_i - w_i in R; encode() stores it back.
+// ---------------------------------------------------------------------------
+struct StoreF64 {
+    using T = double; using R = double;
+    static constexpr bool shifted = false;
+    __device__ static R to_r(T v) { return v; }
+    __device__ static T from_r(R v) { return v; }
+};
+struct StoreF32 {
+    using T = float; using R = float;
+    static constexpr bool shifted = false;
+    __device__ static R to_r(T v) { return v; }
+    __device__ static T from_r(R v) { return v; }
+};
+struct StoreF32S {
+    using T = float; using R = float;
+    static constexpr bool shifted = true;
+    __device__ static R to_r(T v) { return v; }
+    __device__ static T from_r(R v) { return v; }
+};
+struct StoreF16S {
+    using T = __half; using R = float;
+    static constexpr bool shifted = true;
+    __device__ static R to_r(T v) { return __half2float(v); }
+    __device__ static T from_r(R v) { return __float2half_rn(v); }
+};
+struct StoreBF16S {
+    using T = __nv_bfloat16; using R = float;
+    static constexpr bool shifted = true;
+    __device__ static R to_r(T v) { return __bfloat162float(v); }
+    __device__ static T from_r(R v) { return __float2bfloat16_rn(v); }
+};
+
+template <class S, int I>
+__device__ __forceinline__ typename S::R decode(typename S::T v)
+{
+    using R = typename S::R;
+    if constexpr (S::shifted) return S::to_r(v);
+    else return rsub(S::to_r(v), R(wgt(I)));
+}
+template <class S, int I>
+__device__ __forceinline__ typename S::T encode(typename S::R s)
+{
+    using R = typename S::R;
+    if constexpr (S::shifted) return S::from_r(s);
+    else return S::from_r(radd(s, R(wgt(I))));
+}
+// The value a later decode() of encode(s) returns (storage rounding).
+template <class S, int I>
+__device__ __forceinline__ typename S::R roundtrip(typename S::R s)
+{
+    return decode<S, I>(encode<S, I>(s));
+}
+
+// ---------------------------------------------------------------------------
+// Moments and collision.
+// ---------------------------------------------------------------------------
+template <class R>
+struct Mom {
+    R drho, rho, ux, uy, uz;
+};
+
+// delta_rho, rho and u = (j + F/2) / rho from shifted populations.
+template <class R, bool FORCE>
+__device__ __forceinline__ Mom<R> moments_of(const R (&s)[Q], R Fx, R Fy, R Fz)
+{
+    R drho = s[0];
+    static_for<Q - 1>([&](auto K) { drho = radd(drho, s[decltype(K)::value + 1]); });
+    R jx = R(0), jy = R(0), jz = R(0);
+    static_for<Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        if constexpr (cx(i) == 1) jx = radd(jx, s[i]);
+        if constexpr (cx(i) == -1) jx = rsub(jx, s[i]);
+        if constexpr (cy(i) == 1) jy = radd(jy, s[i]);
+        if constexpr (cy(i) == -1) jy = rsub(jy, s[i]);
+        if constexpr (cz(i) == 1) jz = radd(jz, s[i]);
+        if constexpr (cz(i) == -1) jz = rsub(jz, s[i]);
+    });
+    Mom<R> m;
+    m.drho = drho;
+    m.rho = radd(R(1), drho);
+    const R inv = rdiv(R(1), m.rho);
+    if constexpr (FORCE) {
+        jx = rfma(R(0.5), Fx, jx);
+        jy = rfma(R(0.5), Fy, jy);
+        jz = rfma(R(0.5), Fz, jz);
+    }
+    m.ux = rmul(jx, inv);
+    m.uy = rmul(jy, inv);
+    m.uz = rmul(jz, inv);
+    return m;
+}
+
+// In-place BGK + Guo collision of one cell's shifted populations.
+// omega = 1/tau, kf = 1 - omega/2.
+template <class R, bool FORCE>
+__device__ __forceinline__ void bgk_collide(R (&s)[Q], R omega, R kf, R Fx, R Fy, R Fz)
+{
+    const Mom<R> m = moments_of<R, FORCE>(s, Fx, Fy, Fz);
+    const R usq = rfma(m.ux, m.ux, rfma(m.uy, m.uy, rmul(m.uz, m.uz)));
+    const R base = rmul(R(-1.5), usq);
+    R uF = R(0);
+    if constexpr (FORCE) uF = rfma(m.ux, Fx, rfma(m.uy, Fy, rmul(m.uz, Fz)));
+    static_for<Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        const R cu = cdot<i, R>(m.ux, m.uy, m.uz);
+        // 3 c.u + 4.5 (c.u)^2 - 1.5 u.u
+        const R P = (i == 0) ? base : rfma(cu, rfma(R(4.5), cu, R(3)), base);
+        // feq_i - w_i
+        const R seq = rmul(R(wgt(i)), rfma(m.rho, P, m.drho));
+        R out = rfma(omega, rsub(seq, s[i]), s[i]);
+        if constexpr (FORCE) {
+            const R cF = cdot<i, R>(Fx, Fy, Fz);
+            // S_i = w_i (3 (c.F - u.F) + 9 (c.u)(c.F))
+            const R S = rmul(R(wgt(i)), rfma(rmul(R(9), cu), cF, rmul(R(3), rsub(cF, uF))));
+            out = rfma(kf, S, out);
+        }
+        s[i] = out;
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Geometry and boundary description passed by value to every kernel.
+// ---------------------------------------------------------------------------
+template <class R>
+struct Geom {
+    int nx, ny, nz;
+    int per[3];          // axis periodic?
+    int lid[6];          // face is a moving lid?  (x-, x+, y-, y+, z-, z+)
+    int64_t nxp;         // padded row pitch (elements)
+    int64_t plane;       // nxp * ny
+    int64_t slot;        // plane * nz: elements per direction
+    R omega, kf;         // 1/tau, 1 - omega/2
+    R L[Q];              // 6 w_k rho_w (c_k . u_lid): added to incoming slot k of a lid link
+    R Fu[3];             // uniform force
+    const float *Ff;     // per-cell force field [3][N] canonical, or nullptr
+};
+
+// Link from (x,y,z) along d: returns true and the wrapped target cell, or
+// false for a wall link (and tells whether a lid face is crossed).
+template <class R>
+__device__ __forceinline__ bool link(const Geom<R> &g, int x, int y, int z, int dx, int dy, int dz,
+                                     int &tx, int &ty, int &tz, bool &lid)
+{
+    bool wall = false;
+    lid = false;
+    tx = x + dx; ty = y + dy; tz = z + dz;
+    if (tx < 0 || tx >= g.nx) {
+        if (g.per[0]) tx = tx < 0 ? tx + g.nx : tx - g.nx;
+        else { wall = true; lid |= g.lid[tx < 0 ? 0 : 1] != 0; }
+    }
+    if (ty < 0 || ty >= g.ny) {
+        if (g.per[1]) ty = ty < 0 ? ty + g.ny : ty - g.ny;
+        else { wall = true; lid |= g.lid[ty < 0 ? 2 : 3] != 0; }
+    }
+    if (tz < 0 || tz >= g.nz) {
+        if (g.per[2]) tz = tz < 0 ? tz + g.nz : tz - g.nz;
+        else { wall = true; lid |= g.lid[tz < 0 ? 4 : 5] != 0; }
+    }
+    return !wall;
+}
+
+template <class R>
+__device__ __forceinline__ int64_t cell_of(const Geom<R> &g, int x, int y, int z)
+{
+    return (int64_t)z * g.plane + (int64_t)y * g.nxp + x;
+}
+
+// True when every neighbour of (x,y,z) is an ordinary, unwrapped cell.
+template <class R>
+__device__ __forceinline__ bool interior(const Geom<R> &g, int x, int y, int z)
+{
+    return x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1;
+}
+
+// Body force of canonical cell index c.
+template <class R, bool FORCE>
+__device__ __forceinline__ void force_at(const Geom<R> &g, int64_t c, int64_t n, R &Fx, R &Fy, R &Fz)
+{
+    if constexpr (FORCE) {
+        if (g.Ff) {
+            Fx = R(g.Ff[c]);
+            Fy = R(g.Ff[n + c]);
+            Fz = R(g.Ff[2 * n + c]);
+        } else {
+            Fx = g.Fu[0]; Fy = g.Fu[1]; Fz = g.Fu[2];
+        }
+    } else {
+        Fx = Fy = Fz = R(0);
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,560 @@
+// kernels.cuh -- CUDA kernels of the D3Q19 update and their host launchers.
+//
+// Population layout in device memory: structure of arrays f[q][z][y][xp],
+// x fastest, rows padded to a pitch nxp (a multiple of 16 elements) so that
+// every row starts on a 32-byte sector; 64-bit element offsets throughout.
+//
+// State convention.  "Natural" parity: slot i of cell x holds f_i(x) of the
+// post-stream state.  "A" parity (after an AA even step): slot opp(i) of x
+// holds the post-collision f*_i(x) -- for a wall link the value that comes
+// back, f*_i + L_opp(i), so the next read needs no boundary arithmetic.
+//
+// Semantics shared by every schedule (TWO_LATTICE, AA, MERGED): each time
+// step collides with bgk_collide(), then every post-stream population is
+// rounded to the storage format once (encode), the lid term of a wall link
+// added before that rounding.  This is what makes the three schedules agree
+// bit for bit.
+#pragma once
+
+#include "d3q19.cuh"
+#include "ops.h"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// host -> device parameter conversion
+// ---------------------------------------------------------------------------
+template <class R>
+inline Geom<R> make_geom(const HostGeom &h, int64_t pitch)
+{
+    Geom<R> g;
+    g.nx = h.nx; g.ny = h.ny; g.nz = h.nz;
+    for (int a = 0; a < 3; ++a) g.per[a] = h.per[a];
+    for (int k = 0; k < 6; ++k) g.lid[k] = h.lid[k];
+    g.nxp = pitch;
+    g.plane = pitch * h.ny;
+    g.slot = g.plane * h.nz;
+    g.omega = R(h.omega);
+    g.kf = R(h.kf);
+    for (int i = 0; i < Q; ++i) g.L[i] = R(h.L[i]);
+    for (int a = 0; a < 3; ++a) g.Fu[a] = R(h.Fu[a]);
+    g.Ff = h.Ff;
+    return g;
+}
+
+template <class R>
+__device__ __forceinline__ int64_t canon(const Geom<R> &g, int x, int y, int z)
+{
+    return ((int64_t)z * g.ny + y) * g.nx + x;
+}
+
+template <class R>
+__device__ __forceinline__ int64_t ncanon(const Geom<R> &g)
+{
+    return (int64_t)g.nx * g.ny * g.nz;
+}
+
+// Natural post-stream value f_i from a stored element of slot I.
+template <class S, int I>
+__device__ __forceinline__ typename S::R natural_value(typename S::T v)
+{
+    using R = typename S::R;
+    if constexpr (S::shifted) return radd(S::to_r(v), R(wgt(I)));
+    else return S::to_r(v);
+}
+
+// Shifted populations of cell (x,y,z) at natural parity.
+template <class S>
+__device__ __forceinline__ void load_natural(const Geom<typename S::R> &g, const typename S::T *__restrict__ f,
+                                             int x, int y, int z, typename S::R (&s)[Q])
+{
+    const int64_t c = cell_of(g, x, y, z);
+    static_for<Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        s[i] = decode<S, i>(f[i * g.slot + c]);
+    });
+}
+
+// Shifted post-stream populations of cell (x,y,z) from a state at A parity:
+// f_k(x) sits in slot opp(k) of x - c_k, or (wall link) in slot k of x.
+template <class S>
+__device__ __forceinline__ void load_aparity(const Geom<typename S::R> &g, const typename S::T *__restrict__ f,
+                                             int x, int y, int z, typename S::R (&s)[Q])
+{
+    const int64_t c = cell_of(g, x, y, z);
+    if (interior(g, x, y, z)) {
+        static_for<Q>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            const int64_t off = (int64_t)cz(k) * g.plane + (int64_t)cy(k) * g.nxp + cx(k);
+            s[k] = decode<S, k>(f[opp(k) * g.slot + c - off]);
+        });
+    } else {
+        static_for<Q>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            int sx, sy, sz;
+            bool lid;
+            if (link(g, x, y, z, -cx(k), -cy(k), -cz(k), sx, sy, sz, lid))
+                s[k] = decode<S, k>(f[opp(k) * g.slot + cell_of(g, sx, sy, sz)]);
+            else
+                s[k] = decode<S, k>(f[k * g.slot + c]);
+        });
+    }
+}
+
+// Store post-collision populations with the streaming rule of a two-lattice
+// push: slot i of x + c_i, or slot opp(i) of x (+ lid term) for a wall link.
+template <class S>
+__device__ __forceinline__ void push_store(const Geom<typename S::R> &g, typename S::T *__restrict__ dst,
+                                           int x, int y, int z, const typename S::R (&s)[Q])
+{
+    const int64_t c = cell_of(g, x, y, z);
+    if (interior(g, x, y, z)) {
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            const int64_t off = (int64_t)cz(i) * g.plane + (int64_t)cy(i) * g.nxp + cx(i);
+            dst[i * g.slot + c + off] = encode<S, i>(s[i]);
+        });
+    } else {
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            int tx, ty, tz;
+            bool lid;
+            if (link(g, x, y, z, cx(i), cy(i), cz(i), tx, ty, tz, lid)) {
+                dst[i * g.slot + cell_of(g, tx, ty, tz)] = encode<S, i>(s[i]);
+            } else {
+                typename S::R v = s[i];
+                if (lid) v = radd(v, g.L[opp(i)]);
+                dst[opp(i) * g.slot + c] = encode<S, opp(i)>(v);
+            }
+        });
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K0: equilibrium initialisation (natural parity)
+// ---------------------------------------------------------------------------
+template <class S>
+__global__ void k_init_eq(Geom<typename S::R> g, typename S::T *__restrict__ f, const void *rho, const void *u,
+                          int dtype)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const int64_t n = ncanon(g), cc = canon(g, x, y, z), c = cell_of(g, x, y, z);
+    double r = 1.0, ux = 0.0, uy = 0.0, uz = 0.0;
+    if (dtype == 1) {
+        const double *rp = (const double *)rho, *up = (const double *)u;
+        if (rp) r = rp[cc];
+        if (up) { ux = up[cc]; uy = up[n + cc]; uz = up[2 * n + cc]; }
+    } else {
+        const float *rp = (const float *)rho, *up = (const float *)u;
+        if (rp) r = rp[cc];
+        if (up) { ux = up[cc]; uy = up[n + cc]; uz = up[2 * n + cc]; }
+    }
+    const double usq = ux * ux + uy * uy + uz * uz;
+    static_for<Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+        const double P = 3.0 * cu + 4.5 * cu * cu - 1.5 * usq;
+        if constexpr (S::shifted) {
+            const double sv = wgt(i) * ((r - 1.0) + r * P);
+            f[i * g.slot + c] = S::from_r((typename S::R)sv);
+        } else {
+            const double fv = wgt(i) * r * (1.0 + P);
+            f[i * g.slot + c] = S::from_r((typename S::R)fv);
+        }
+    });
+}
+
+// ---------------------------------------------------------------------------
+// K1: two-lattice fused collide-and-push (natural -> natural)
+// ---------------------------------------------------------------------------
+template <class S, bool FORCE>
+__global__ void __launch_bounds__(128) k_two_lattice(Geom<typename S::R> g, const typename S::T *__restrict__ src,
+                                                     typename S::T *__restrict__ dst)
+{
+    using R = typename S::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    R s[Q];
+    load_natural<S>(g, src, x, y, z, s);
+    R Fx, Fy, Fz;
+    force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
+    bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
+    push_store<S>(g, dst, x, y, z, s);
+}
+
+// ---------------------------------------------------------------------------
+// K2: AA even step (natural -> A parity), purely local: collide and write
+// f*_i into slot opp(i) of the same cell (the "revert" of Sec. 3).
+// ---------------------------------------------------------------------------
+template <class S, bool FORCE>
+__global__ void __launch_bounds__(128) k_aa_even(Geom<typename S::R> g, typename S::T *__restrict__ f)
+{
+    using R = typename S::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const int64_t c = cell_of(g, x, y, z);
+    R s[Q];
+    load_natural<S>(g, f, x, y, z, s);
+    R Fx, Fy, Fz;
+    force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
+    bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
+    if (interior(g, x, y, z)) {
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            f[opp(i) * g.slot + c] = encode<S, opp(i)>(s[i]);
+        });
+    } else {
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            int tx, ty, tz;
+            bool lid;
+            R v = s[i];
+            if (!link(g, x, y, z, cx(i), cy(i), cz(i), tx, ty, tz, lid) && lid) v = radd(v, g.L[opp(i)]);
+            f[opp(i) * g.slot + c] = encode<S, opp(i)>(v);
+        });
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K3: AA odd step (A parity -> natural): gather the streamed values, collide,
+// scatter to the neighbours (the "swap_stream" of Sec. 3).  Cell x reads
+// (x - c_k, opp(k)) and writes (x + c_i, i); no other cell touches those
+// locations in this sweep, so the update is race-free in place.
+// ---------------------------------------------------------------------------
+template <class S, bool FORCE>
+__global__ void __launch_bounds__(128) k_aa_odd(Geom<typename S::R> g, typename S::T *__restrict__ f)
+{
+    using R = typename S::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    R s[Q];
+    load_aparity<S>(g, f, x, y, z, s);
+    R Fx, Fy, Fz;
+    force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
+    bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
+    push_store<S>(g, f, x, y, z, s);
+}
+
+// ---------------------------------------------------------------------------
+// K5: moments, population export/import, raw parity normalisation
+// ---------------------------------------------------------------------------
+template <class S, bool FORCE, bool APAR>
+__global__ void k_moments(Geom<typename S::R> g, const typename S::T *__restrict__ f, void *rho, void *u, int dtype)
+{
+    using R = typename S::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    R s[Q];
+    if constexpr (APAR) load_aparity<S>(g, f, x, y, z, s);
+    else load_natural<S>(g, f, x, y, z, s);
+    const int64_t n = ncanon(g), cc = canon(g, x, y, z);
+    R Fx, Fy, Fz;
+    force_at<R, FORCE>(g, cc, n, Fx, Fy, Fz);
+    const Mom<R> m = moments_of<R, FORCE>(s, Fx, Fy, Fz);
+    if (dtype == 1) {
+        if (rho) ((double *)rho)[cc] = (double)m.rho;
+        if (u) {
+            double *up = (double *)u;
+            up[cc] = (double)m.ux; up[n + cc] = (double)m.uy; up[2 * n + cc] = (double)m.uz;
+        }
+    } else {
+        if (rho) ((float *)rho)[cc] = (float)m.rho;
+        if (u) {
+            float *up = (float *)u;
+            up[cc] = (float)m.ux; up[n + cc] = (float)m.uy; up[2 * n + cc] = (float)m.uz;
+        }
+    }
+}
+
+template <class S, bool APAR>
+__global__ void k_export(Geom<typename S::R> g, const typename S::T *__restrict__ f, void *out, int dtype)
+{
+    using R = typename S::R;
+    using T = typename S::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const int64_t n = ncanon(g), cc = canon(g, x, y, z), c = cell_of(g, x, y, z);
+    const bool in = interior(g, x, y, z);
+    static_for<Q>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        T v;
+        if constexpr (APAR) {
+            int sx, sy, sz;
+            bool lid;
+            if (in) v = f[opp(k) * g.slot + c - ((int64_t)cz(k) * g.plane + (int64_t)cy(k) * g.nxp + cx(k))];
+            else if (link(g, x, y, z, -cx(k), -cy(k), -cz(k), sx, sy, sz, lid))
+                v = f[opp(k) * g.slot + cell_of(g, sx, sy, sz)];
+            else v = f[k * g.slot + c];
+        } else {
+            v = f[k * g.slot + c];
+        }
+        const R nv = natural_value<S, k>(v);
+        if (dtype == 1) ((double *)out)[k * n + cc] = (double)nv;
+        else ((float *)out)[k * n + cc] = (float)nv;
+    });
+}
+
+template <class S>
+__global__ void k_import(Geom<typename S::R> g, typename S::T *__restrict__ f, const void *in, int dtype)
+{
+    using R = typename S::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const int64_t n = ncanon(g), cc = canon(g, x, y, z), c = cell_of(g, x, y, z);
+    static_for<Q>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        if (dtype == 1) {
+            const double v = ((const double *)in)[k * n + cc];
+            f[k * g.slot + c] = S::from_r((R)(S::shifted ? v - wgt(k) : v));
+        } else {
+            const float v = ((const float *)in)[k * n + cc];
+            f[k * g.slot + c] = S::from_r(S::shifted ? (R)rsub(v, float(wgt(k))) : (R)v);
+        }
+    });
+}
+
+// Raw copy of a state into natural parity (no rounding): from A parity this
+// is the pure gather, element by element; used for exact checkpoints.
+template <class S>
+__global__ void k_raw_natural(Geom<typename S::R> g, const typename S::T *__restrict__ f, typename S::T *__restrict__ out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const int64_t c = cell_of(g, x, y, z);
+    static_for<Q>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        int sx, sy, sz;
+        bool lid;
+        if (link(g, x, y, z, -cx(k), -cy(k), -cz(k), sx, sy, sz, lid))
+            out[k * g.slot + c] = f[opp(k) * g.slot + cell_of(g, sx, sy, sz)];
+        else
+            out[k * g.slot + c] = f[k * g.slot + c];
+    });
+}
+
+// ---------------------------------------------------------------------------
+// K6: deterministic FP64 reductions (mass, momentum, kinetic energy)
+// ---------------------------------------------------------------------------
+constexpr int RED_THREADS = 256;
+constexpr int RED_MAX_BLOCKS = 1024;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <class S, bool FORCE, bool APAR>
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_partial(Geom<typename S::R> g, const typename S::T *__restrict__ f,
+                                                                double *__restrict__ partial, int *__restrict__ flag)
+{
+    using R = typename S::R;
+    const int64_t n = ncanon(g);
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    bool bad = false;
+    for (int64_t cc = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; cc < n; cc += (int64_t)gridDim.x * RED_THREADS) {
+        const int x = (int)(cc % g.nx);
+        const int64_t r = cc / g.nx;
+        const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+        R s[Q];
+        if constexpr (APAR) load_aparity<S>(g, f, x, y, z, s);
+        else load_natural<S>(g, f, x, y, z, s);
+        double dr = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            const double v = (double)s[i];
+            dr += v;
+            if constexpr (cx(i) != 0) jx += cx(i) * v;
+            if constexpr (cy(i) != 0) jy += cy(i) * v;
+            if constexpr (cz(i) != 0) jz += cz(i) * v;
+        });
+        R Fx, Fy, Fz;
+        force_at<R, FORCE>(g, cc, n, Fx, Fy, Fz);
+        const double rho = 1.0 + dr;
+        const double ux = (jx + 0.5 * (double)Fx) / rho, uy = (jy + 0.5 * (double)Fy) / rho,
+                     uz = (jz + 0.5 * (double)Fz) / rho;
+        const double ke = 0.5 * rho * (ux * ux + uy * uy + uz * uz);
+        if (!isfinite(rho) || !isfinite(ke)) bad = true;
+        acc[0] += rho; acc[1] += jx; acc[2] += jy; acc[3] += jz; acc[4] += ke;
+    }
+    if (bad) atomicOr(flag, 1);
+    __shared__ double red[5][RED_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            double v = lane < RED_THREADS / 32 ? red[k][lane] : 0.0;
+            v = warp_sum(v);
+            if (lane == 0) partial[(int64_t)k * gridDim.x + blockIdx.x] = v;
+        }
+    }
+}
+
+static __global__ void __launch_bounds__(RED_THREADS) k_reduce_final(const double *__restrict__ partial, int nblocks,
+                                                              double *__restrict__ out)
+{
+    __shared__ double red[RED_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < 5; ++k) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += RED_THREADS) v += partial[(int64_t)k * nblocks + b];
+        v = warp_sum(v);
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            double t = lane < RED_THREADS / 32 ? red[lane] : 0.0;
+            t = warp_sum(t);
+            if (lane == 0) out[k] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K4: two steps per sweep.  See merged.cuh.
+// ---------------------------------------------------------------------------
+
+// ---------------------------------------------------------------------------
+// K8: adjoint of one step (two buffers) and its seed.
+// ---------------------------------------------------------------------------
+// lam_out(x) = (d f^{t+1}/d f^t)^T lam_in at cell x, gF(x) += (d f^{t+1}/dF(x))^T lam_in.
+// f and lam share the geometry g (pitch g.nxp); gF and the force are canonical.
+template <class S, bool FORCE>
+__global__ void __launch_bounds__(128) k_adjoint(Geom<typename S::R> g, const typename S::T *__restrict__ f,
+                                                 const typename S::R *__restrict__ lam_in,
+                                                 typename S::R *__restrict__ lam_out, double *__restrict__ gF)
+{
+    using R = typename S::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const int64_t n = ncanon(g), cc = canon(g, x, y, z), c = cell_of(g, x, y, z);
+    R s[Q];
+    load_natural<S>(g, f, x, y, z, s);
+    R Fx, Fy, Fz;
+    force_at<R, FORCE>(g, cc, n, Fx, Fy, Fz);
+    const Mom<R> m = moments_of<R, FORCE>(s, Fx, Fy, Fz);
+    const R usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
+    // mu_i = dL/df*_i: the transpose of streaming
+    R mu[Q];
+    const bool in = interior(g, x, y, z);
+    static_for<Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        if (in) {
+            const int64_t off = (int64_t)cz(i) * g.plane + (int64_t)cy(i) * g.nxp + cx(i);
+            mu[i] = lam_in[i * g.slot + c + off];
+        } else {
+            int tx, ty, tz;
+            bool lid;
+            if (link(g, x, y, z, cx(i), cy(i), cz(i), tx, ty, tz, lid))
+                mu[i] = lam_in[i * g.slot + cell_of(g, tx, ty, tz)];
+            else
+                mu[i] = lam_in[opp(i) * g.slot + c];
+        }
+    });
+    // a = sum mu_i dfeq_i/drho; b = sum mu_i dfeq_i/du; sv = sum mu_i dS_i/du;
+    // gv = sum mu_i dS_i/dF|_u
+    R a = R(0), bx = R(0), by = R(0), bz = R(0), sx = R(0), sy = R(0), sz = R(0);
+    R gx = R(0), gy = R(0), gz = R(0);
+    static_for<Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        const R wm = R(wgt(i)) * mu[i];
+        const R cu = R(cx(i)) * m.ux + R(cy(i)) * m.uy + R(cz(i)) * m.uz;
+        a += wm * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
+        const R t = R(3) + R(9) * cu;   // (3 c_a + 9 cu c_a) = c_a (3 + 9 cu)
+        bx += wm * m.rho * (R(cx(i)) * t - R(3) * m.ux);
+        by += wm * m.rho * (R(cy(i)) * t - R(3) * m.uy);
+        bz += wm * m.rho * (R(cz(i)) * t - R(3) * m.uz);
+        if constexpr (FORCE) {
+            const R cF = R(cx(i)) * Fx + R(cy(i)) * Fy + R(cz(i)) * Fz;
+            sx += wm * (R(-3) * Fx + R(9) * cF * R(cx(i)));
+            sy += wm * (R(-3) * Fy + R(9) * cF * R(cy(i)));
+            sz += wm * (R(-3) * Fz + R(9) * cF * R(cz(i)));
+        }
+        gx += wm * (R(cx(i)) * t - R(3) * m.ux);
+        gy += wm * (R(cy(i)) * t - R(3) * m.uy);
+        gz += wm * (R(cz(i)) * t - R(3) * m.uz);
+    });
+    const R ex = g.omega * bx + g.kf * sx, ey = g.omega * by + g.kf * sy, ez = g.omega * bz + g.kf * sz;
+    const R inv = R(1) / m.rho;
+    static_for<Q>([&](auto K) {
+        constexpr int j = decltype(K)::value;
+        const R v = (R(1) - g.omega) * mu[j] + g.omega * a +
+                    (ex * (R(cx(j)) - m.ux) + ey * (R(cy(j)) - m.uy) + ez * (R(cz(j)) - m.uz)) * inv;
+        lam_out[j * g.slot + c] = v;
+    });
+    if (gF) {
+        const R h = R(0.5) * inv;
+        gF[cc] += (double)(g.kf * gx + ex * h);
+        gF[n + cc] += (double)(g.kf * gy + ey * h);
+        gF[2 * n + cc] += (double)(g.kf * gz + ez * h);
+    }
+}
+
+// lam = dL/df for L(rho, u) of state f (natural parity); gF += dL/du / (2 rho).
+template <class S, bool FORCE>
+__global__ void k_adjoint_seed(Geom<typename S::R> g, const typename S::T *__restrict__ f, const void *dLdrho,
+                               const void *dLdu, int dtype, typename S::R *__restrict__ lam, double *__restrict__ gF)
+{
+    using R = typename S::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const int64_t n = ncanon(g), cc = canon(g, x, y, z), c = cell_of(g, x, y, z);
+    R s[Q];
+    load_natural<S>(g, f, x, y, z, s);
+    R Fx, Fy, Fz;
+    force_at<R, FORCE>(g, cc, n, Fx, Fy, Fz);
+    const Mom<R> m = moments_of<R, FORCE>(s, Fx, Fy, Fz);
+    R dr = R(0), dx, dy, dz;
+    if (dtype == 1) {
+        const double *du = (const double *)dLdu;
+        if (dLdrho) dr = (R)((const double *)dLdrho)[cc];
+        dx = (R)du[cc]; dy = (R)du[n + cc]; dz = (R)du[2 * n + cc];
+    } else {
+        const float *du = (const float *)dLdu;
+        if (dLdrho) dr = (R)((const float *)dLdrho)[cc];
+        dx = (R)du[cc]; dy = (R)du[n + cc]; dz = (R)du[2 * n + cc];
+    }
+    const R inv = R(1) / m.rho;
+    static_for<Q>([&](auto K) {
+        constexpr int j = decltype(K)::value;
+        lam[j * g.slot + c] = dr + (dx * (R(cx(j)) - m.ux) + dy * (R(cy(j)) - m.uy) + dz * (R(cz(j)) - m.uz)) * inv;
+    });
+    if (gF) {
+        const R h = R(0.5) * inv;
+        gF[cc] += (double)(dx * h);
+        gF[n + cc] += (double)(dy * h);
+        gF[2 * n + cc] += (double)(dz * h);
+    }
+}
+
+// Cast between a canonical array of dtype and an R array of pitch g.nxp.
+template <class R>
+__global__ void k_canon_to_pitched(Geom<R> g, const void *in, int dtype, R *__restrict__ out, int ncomp)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const int64_t n = ncanon(g), cc = canon(g, x, y, z), c = cell_of(g, x, y, z);
+    for (int k = 0; k < ncomp; ++k)
+        out[k * g.slot + c] = dtype == 1 ? (R)((const double *)in)[k * n + cc] : (R)((const float *)in)[k * n + cc];
+}
+template <class R>
+__global__ void k_pitched_to_canon(Geom<R> g, const R *__restrict__ in, void *out, int dtype, int ncomp)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const int64_t n = ncanon(g), cc = canon(g, x, y, z), c = cell_of(g, x, y, z);
+    for (int k = 0; k < ncomp; ++k) {
+        if (dtype == 1) ((double *)out)[k * n + cc] = (double)in[k * g.slot + c];
+        else ((float *)out)[k * n + cc] = (float)in[k * g.slot + c];
+    }
+}
+
+}  // namespace lbm

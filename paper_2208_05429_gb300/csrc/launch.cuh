@@ -1,0 +1,197 @@
+// launch.cuh -- host launchers of one storage format, gathered into a
+// StorageOps table by make_ops<S>().  Included once per inst_*.cu.
+#pragma once
+
+#include "kernels.cuh"
+#include "merged.cuh"
+
+namespace lbm {
+
+constexpr int CELL_BLOCK = 128;
+
+inline dim3 cell_grid(const HostGeom &h) { return dim3((h.nx + CELL_BLOCK - 1) / CELL_BLOCK, h.ny, h.nz); }
+
+template <class S>
+struct Launch {
+    using R = typename S::R;
+    using T = typename S::T;
+
+    static cudaError_t init_eq(const HostGeom &h, int64_t pitch, void *f, const void *rho, const void *u, int dtype,
+                               cudaStream_t st)
+    {
+        k_init_eq<S><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (T *)f, rho, u, dtype);
+        return cudaGetLastError();
+    }
+    static cudaError_t two_lattice(const HostGeom &h, int64_t pitch, bool force, const void *src, void *dst,
+                                   cudaStream_t st)
+    {
+        if (force) k_two_lattice<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (const T *)src, (T *)dst);
+        else k_two_lattice<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (const T *)src, (T *)dst);
+        return cudaGetLastError();
+    }
+    static cudaError_t aa_even(const HostGeom &h, int64_t pitch, bool force, void *f, cudaStream_t st)
+    {
+        if (force) k_aa_even<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (T *)f);
+        else k_aa_even<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (T *)f);
+        return cudaGetLastError();
+    }
+    static cudaError_t aa_odd(const HostGeom &h, int64_t pitch, bool force, void *f, cudaStream_t st)
+    {
+        if (force) k_aa_odd<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (T *)f);
+        else k_aa_odd<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (T *)f);
+        return cudaGetLastError();
+    }
+    static cudaError_t moments(const HostGeom &h, int64_t pitch, bool force, int parity, const void *f, void *rho,
+                               void *u, int dtype, cudaStream_t st)
+    {
+        const Geom<R> g = make_geom<R>(h, pitch);
+        const T *p = (const T *)f;
+        if (force) {
+            if (parity) k_moments<S, true, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, p, rho, u, dtype);
+            else k_moments<S, true, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, p, rho, u, dtype);
+        } else {
+            if (parity) k_moments<S, false, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, p, rho, u, dtype);
+            else k_moments<S, false, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, p, rho, u, dtype);
+        }
+        return cudaGetLastError();
+    }
+    static cudaError_t export_pop(const HostGeom &h, int64_t pitch, int parity, const void *f, void *out, int dtype,
+                                  cudaStream_t st)
+    {
+        const Geom<R> g = make_geom<R>(h, pitch);
+        if (parity) k_export<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, (const T *)f, out, dtype);
+        else k_export<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, (const T *)f, out, dtype);
+        return cudaGetLastError();
+    }
+    static cudaError_t import_pop(const HostGeom &h, int64_t pitch, void *f, const void *in, int dtype,
+                                  cudaStream_t st)
+    {
+        k_import<S><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (T *)f, in, dtype);
+        return cudaGetLastError();
+    }
+    static cudaError_t raw_natural(const HostGeom &h, int64_t pitch, const void *f, void *out, cudaStream_t st)
+    {
+        k_raw_natural<S><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (const T *)f, (T *)out);
+        return cudaGetLastError();
+    }
+    static cudaError_t reduce(const HostGeom &h, int64_t pitch, bool force, int parity, const void *f,
+                              double *partial, int nblocks, int *flag, double *out, cudaStream_t st)
+    {
+        const Geom<R> g = make_geom<R>(h, pitch);
+        const T *p = (const T *)f;
+        if (force) {
+            if (parity) k_reduce_partial<S, true, true><<<nblocks, RED_THREADS, 0, st>>>(g, p, partial, flag);
+            else k_reduce_partial<S, true, false><<<nblocks, RED_THREADS, 0, st>>>(g, p, partial, flag);
+        } else {
+            if (parity) k_reduce_partial<S, false, true><<<nblocks, RED_THREADS, 0, st>>>(g, p, partial, flag);
+            else k_reduce_partial<S, false, false><<<nblocks, RED_THREADS, 0, st>>>(g, p, partial, flag);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_reduce_final<<<1, RED_THREADS, 0, st>>>(partial, nblocks, out);
+        return cudaGetLastError();
+    }
+    static cudaError_t snapshot(const HostGeom &h, int64_t pitch, bool force, const void *f, void *G,
+                                const TileInfo &ti, cudaStream_t st)
+    {
+        const int64_t cz_ = ti.zshell ? 2LL * h.ny * h.nx : 0;
+        const int64_t cy_ = ti.yshell ? (int64_t)h.nz * 2 * ti.nty * h.nx : 0;
+        const int64_t cx_ = ti.xshell ? (int64_t)h.nz * 2 * ti.ntx * h.ny : 0;
+        const int64_t tot = cz_ + cy_ + cx_;
+        if (tot == 0) return cudaSuccess;
+        const unsigned blocks = (unsigned)((tot + 255) / 256);
+        const Geom<R> g = make_geom<R>(h, pitch);
+        if (force) k_snapshot<S, true><<<blocks, 256, 0, st>>>(g, (const T *)f, (T *)G, ti, cz_, cy_, cx_);
+        else k_snapshot<S, false><<<blocks, 256, 0, st>>>(g, (const T *)f, (T *)G, ti, cz_, cy_, cx_);
+        return cudaGetLastError();
+    }
+
+    template <int TX, int TY>
+    static cudaError_t merged_t(const HostGeom &h, int64_t pitch, bool force, void *f, const void *G,
+                                const TileInfo &ti, cudaStream_t st)
+    {
+        const size_t smem = (size_t)4 * Q * TX * TY * sizeof(R);
+        const dim3 grid(ti.ntx, ti.nty), block(TX, TY);
+        const Geom<R> g = make_geom<R>(h, pitch);
+        cudaError_t e;
+        if (force) {
+            e = cudaFuncSetAttribute(k_merged<S, true, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_merged<S, true, TX, TY><<<grid, block, smem, st>>>(g, (T *)f, (const T *)G, ti);
+        } else {
+            e = cudaFuncSetAttribute(k_merged<S, false, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_merged<S, false, TX, TY><<<grid, block, smem, st>>>(g, (T *)f, (const T *)G, ti);
+        }
+        return cudaGetLastError();
+    }
+    static cudaError_t merged(const HostGeom &h, int64_t pitch, bool force, void *f, const void *G,
+                              const TileInfo &ti, cudaStream_t st)
+    {
+        if (ti.TX != 32) return cudaErrorInvalidValue;
+        switch (ti.TY) {
+        case 4: return merged_t<32, 4>(h, pitch, force, f, G, ti, st);
+        case 8: return merged_t<32, 8>(h, pitch, force, f, G, ti, st);
+        case 16:
+            if constexpr (sizeof(R) == 4) return merged_t<32, 16>(h, pitch, force, f, G, ti, st);
+            else return cudaErrorInvalidValue;
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    static cudaError_t adjoint(const HostGeom &h, int64_t pitch, bool force, const void *f, const void *lam_in,
+                               void *lam_out, double *gF, cudaStream_t st)
+    {
+        const Geom<R> g = make_geom<R>(h, pitch);
+        if (force) k_adjoint<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, (const T *)f, (const R *)lam_in, (R *)lam_out, gF);
+        else k_adjoint<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, (const T *)f, (const R *)lam_in, (R *)lam_out, gF);
+        return cudaGetLastError();
+    }
+    static cudaError_t adjoint_seed(const HostGeom &h, int64_t pitch, bool force, const void *f, const void *dLdrho,
+                                    const void *dLdu, int dtype, void *lam, double *gF, cudaStream_t st)
+    {
+        const Geom<R> g = make_geom<R>(h, pitch);
+        if (force) k_adjoint_seed<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, (const T *)f, dLdrho, dLdu, dtype, (R *)lam, gF);
+        else k_adjoint_seed<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, (const T *)f, dLdrho, dLdu, dtype, (R *)lam, gF);
+        return cudaGetLastError();
+    }
+    static cudaError_t canon_to_pitched(const HostGeom &h, int64_t pitch, const void *in, int dtype, void *out,
+                                        int ncomp, cudaStream_t st)
+    {
+        k_canon_to_pitched<R><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), in, dtype, (R *)out, ncomp);
+        return cudaGetLastError();
+    }
+    static cudaError_t pitched_to_canon(const HostGeom &h, int64_t pitch, const void *in, void *out, int dtype,
+                                        int ncomp, cudaStream_t st)
+    {
+        k_pitched_to_canon<R><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (const R *)in, out, dtype, ncomp);
+        return cudaGetLastError();
+    }
+};
+
+template <class S>
+StorageOps make_ops()
+{
+    using L = Launch<S>;
+    StorageOps o;
+    o.elem_size = sizeof(typename S::T);
+    o.real_size = sizeof(typename S::R);
+    o.max_tile_y = sizeof(typename S::R) == 4 ? 16 : 8;
+    o.init_eq = &L::init_eq;
+    o.two_lattice = &L::two_lattice;
+    o.aa_even = &L::aa_even;
+    o.aa_odd = &L::aa_odd;
+    o.moments = &L::moments;
+    o.export_pop = &L::export_pop;
+    o.import_pop = &L::import_pop;
+    o.raw_natural = &L::raw_natural;
+    o.reduce = &L::reduce;
+    o.snapshot = &L::snapshot;
+    o.merged = &L::merged;
+    o.adjoint = &L::adjoint;
+    o.adjoint_seed = &L::adjoint_seed;
+    o.canon_to_pitched = &L::canon_to_pitched;
+    o.pitched_to_canon = &L::pitched_to_canon;
+    return o;
+}
+
+}  // namespace lbm

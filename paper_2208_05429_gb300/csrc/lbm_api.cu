@@ -1,0 +1,626 @@
+// lbm_api.cu -- the C ABI declared in include/lbm.h: configuration checks,
+// the handle and its device memory, AA parity bookkeeping, schedule dispatch
+// and the checkpointed adjoint driver.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "d3q19.cuh"
+#include "lbm.h"
+#include "ops.h"
+
+using namespace lbm;
+
+struct lbm_handle {
+    lbm_config cfg;
+    cudaStream_t stream;
+    int device;
+    const StorageOps *ops;
+    HostGeom hg;
+    int64_t nxp;
+    bool force;
+    bool owns;
+    void *base;
+    size_t bytes;
+    void *f;       // populations
+    void *f2;      // second lattice (TWO_LATTICE)
+    void *G;       // shell snapshot (MERGED)
+    TileInfo ti;
+    double *partial;
+    double *red_out;
+    int *flag;
+    int red_blocks;
+    int parity;
+    int64_t t;
+    bool force_set;
+    // per-kernel timing
+    bool prof_on;
+    std::vector<cudaEvent_t> *ev_pool;  // all events ever created
+    std::vector<int> *rec_kind;         // kernel class of record k (events 2k, 2k+1)
+    // adjoint driver state
+    bool adj_ready;
+    int64_t adj_T, adj_K;
+    void *adj_work;
+    size_t adj_bytes;
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+inline size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+const StorageOps *ops_for(int storage)
+{
+    switch (storage) {
+    case LBM_STORAGE_F64: return &ops_f64();
+    case LBM_STORAGE_F32: return &ops_f32();
+    case LBM_STORAGE_F32S: return &ops_f32s();
+    case LBM_STORAGE_F16S: return &ops_f16s();
+    case LBM_STORAGE_BF16S: return &ops_bf16s();
+    default: return nullptr;
+    }
+}
+
+// Row pitch: nx rounded up to 16 elements.
+inline int64_t pitch_of(const lbm_config &c) { return (c.nx + 15) / 16 * 16; }
+
+inline int64_t state_elems(const lbm_config &c) { return (int64_t)Q * c.nz * c.ny * pitch_of(c); }
+
+size_t elem_size_of(int storage)
+{
+    switch (storage) {
+    case LBM_STORAGE_F64: return 8;
+    case LBM_STORAGE_F32:
+    case LBM_STORAGE_F32S: return 4;
+    default: return 2;
+    }
+}
+size_t real_size_of(int storage) { return storage == LBM_STORAGE_F64 ? 8 : 4; }
+
+int default_tile_y(const lbm_config &c) { return c.storage == LBM_STORAGE_F64 ? 8 : 16; }
+
+TileInfo tile_info(const lbm_config &c)
+{
+    TileInfo ti;
+    memset(&ti, 0, sizeof(ti));
+    ti.TX = c.tile_x > 0 ? c.tile_x : 32;
+    ti.TY = c.tile_y > 0 ? c.tile_y : default_tile_y(c);
+    ti.ntx = (int)((c.nx + ti.TX - 1) / ti.TX);
+    ti.nty = (int)((c.ny + ti.TY - 1) / ti.TY);
+    ti.xshell = ti.ntx > 1;
+    ti.yshell = ti.nty > 1;
+    ti.zshell = c.face_bc[4] == LBM_BC_PERIODIC;
+    ti.gy_slot = ti.yshell ? (int64_t)c.nz * 2 * ti.nty * c.nx : 0;
+    ti.gx_slot = ti.xshell ? (int64_t)c.nz * 2 * ti.ntx * c.ny : 0;
+    ti.gz_slot = ti.zshell ? 2LL * c.ny * c.nx : 0;
+    ti.gy_off = 0;
+    ti.gx_off = (int64_t)Q * ti.gy_slot;
+    ti.gz_off = (int64_t)Q * (ti.gy_slot + ti.gx_slot);
+    return ti;
+}
+
+int64_t ghost_elems(const lbm_config &c)
+{
+    if (c.variant != LBM_VARIANT_MERGED) return 0;
+    const TileInfo ti = tile_info(c);
+    return (int64_t)Q * (ti.gy_slot + ti.gx_slot + ti.gz_slot);
+}
+
+struct Layout {
+    size_t f, f2, G, partial, red_out, flag, total;
+};
+
+Layout layout_of(const lbm_config &c)
+{
+    Layout L;
+    const size_t es = elem_size_of(c.storage);
+    const size_t pop = align_up((size_t)state_elems(c) * es);
+    size_t off = 0;
+    L.f = off; off += pop;
+    L.f2 = off; if (c.variant == LBM_VARIANT_TWO_LATTICE) off += pop;
+    L.G = off; off += align_up((size_t)ghost_elems(c) * es);
+    L.partial = off; off += align_up(sizeof(double) * 5 * RED_BLOCKS_MAX);
+    L.red_out = off; off += align_up(sizeof(double) * 5);
+    L.flag = off; off += align_up(sizeof(int));
+    L.total = off;
+    return L;
+}
+
+HostGeom host_geom(const lbm_config &c)
+{
+    HostGeom h;
+    memset(&h, 0, sizeof(h));
+    h.nx = (int)c.nx; h.ny = (int)c.ny; h.nz = (int)c.nz;
+    for (int a = 0; a < 3; ++a) h.per[a] = c.face_bc[2 * a] == LBM_BC_PERIODIC;
+    for (int k = 0; k < 6; ++k) h.lid[k] = c.face_bc[k] == LBM_BC_LID;
+    h.omega = 1.0 / c.tau;
+    h.kf = 1.0 - 0.5 * h.omega;
+    for (int k = 0; k < Q; ++k) {
+        const double cu = cx(k) * c.u_lid[0] + cy(k) * c.u_lid[1] + cz(k) * c.u_lid[2];
+        h.L[k] = 6.0 * wgt(k) * c.rho_wall * cu;
+    }
+    if (c.force_mode == LBM_FORCE_UNIFORM)
+        for (int a = 0; a < 3; ++a) h.Fu[a] = c.force_uniform[a];
+    h.Ff = nullptr;
+    return h;
+}
+
+// Keeps the handle's device current for the duration of an API call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+#define CK(call)                                   \
+    do {                                           \
+        if ((call) != cudaSuccess) return LBM_ECUDA; \
+    } while (0)
+
+int check_dtype(int32_t dtype) { return dtype == LBM_DTYPE_F32 || dtype == LBM_DTYPE_F64 ? LBM_OK : LBM_EINVAL; }
+
+const StorageOps *ops_for_dtype(int32_t dtype) { return dtype == LBM_DTYPE_F64 ? &ops_f64() : &ops_f32(); }
+
+
+}  // namespace
+
+// Bracket one launch with profiling events when profiling is on.
+template <class F>
+static cudaError_t timed(lbm_handle *h, int kind, F &&launch)
+{
+    if (!h->prof_on) return launch();
+    const size_t k = h->rec_kind->size();
+    while (h->ev_pool->size() < 2 * (k + 1)) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        h->ev_pool->push_back(e);
+    }
+    cudaError_t r = cudaEventRecord((*h->ev_pool)[2 * k], h->stream);
+    if (r != cudaSuccess) return r;
+    r = launch();
+    if (r != cudaSuccess) return r;
+    r = cudaEventRecord((*h->ev_pool)[2 * k + 1], h->stream);
+    if (r != cudaSuccess) return r;
+    h->rec_kind->push_back(kind);
+    return cudaSuccess;
+}
+
+extern "C" {
+
+void lbm_config_default(lbm_config *cfg)
+{
+    if (!cfg) return;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->nx = cfg->ny = cfg->nz = 32;
+    cfg->tau = 0.6;
+    for (int k = 0; k < 6; ++k) cfg->face_bc[k] = LBM_BC_PERIODIC;
+    cfg->rho_wall = 1.0;
+    cfg->storage = LBM_STORAGE_F32;
+    cfg->variant = LBM_VARIANT_AA;
+    cfg->force_mode = LBM_FORCE_NONE;
+}
+
+int lbm_validate(const lbm_config *c)
+{
+    if (!c) return LBM_EINVAL;
+    if (c->nx < 1 || c->ny < 1 || c->nz < 1) return LBM_EINVAL;
+    if (c->ny > 65535 || c->nz > 65535 || c->nx > (1LL << 30)) return LBM_EINVAL;
+    if ((double)c->nx * (double)c->ny * (double)c->nz > 2147483647.0) return LBM_EINVAL;
+    if (!(c->tau > 0.5) || !isfinite(c->tau)) return LBM_EINVAL;
+    for (int k = 0; k < 6; ++k)
+        if (c->face_bc[k] < LBM_BC_PERIODIC || c->face_bc[k] > LBM_BC_LID) return LBM_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if ((c->face_bc[2 * a] == LBM_BC_PERIODIC) != (c->face_bc[2 * a + 1] == LBM_BC_PERIODIC)) return LBM_EINVAL;
+    const double ul = sqrt(c->u_lid[0] * c->u_lid[0] + c->u_lid[1] * c->u_lid[1] + c->u_lid[2] * c->u_lid[2]);
+    if (!(ul < 0.3)) return LBM_EINVAL;
+    if (!(c->rho_wall > 0.0) || !isfinite(c->rho_wall)) return LBM_EINVAL;
+    if (c->storage < LBM_STORAGE_F64 || c->storage > LBM_STORAGE_BF16S) return LBM_EINVAL;
+    if (c->variant < LBM_VARIANT_TWO_LATTICE || c->variant > LBM_VARIANT_MERGED) return LBM_EINVAL;
+    if (c->force_mode < LBM_FORCE_NONE || c->force_mode > LBM_FORCE_FIELD) return LBM_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(c->force_uniform[a])) return LBM_EINVAL;
+    if (c->tile_x != 0 && c->tile_x != 32) return LBM_EINVAL;
+    if (c->tile_y != 0 && c->tile_y != 4 && c->tile_y != 8 && c->tile_y != 16) return LBM_EINVAL;
+    if (c->tile_y == 16 && c->storage == LBM_STORAGE_F64) return LBM_EINVAL;
+    return LBM_OK;
+}
+
+int lbm_required_bytes(const lbm_config *cfg, size_t *bytes)
+{
+    const int v = lbm_validate(cfg);
+    if (v != LBM_OK) return v;
+    if (!bytes) return LBM_EINVAL;
+    *bytes = layout_of(*cfg).total;
+    return LBM_OK;
+}
+
+static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t bytes, bool own, lbm_handle **out)
+{
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    const int v = lbm_validate(cfg);
+    if (v != LBM_OK) return v;
+    const Layout L = layout_of(*cfg);
+    lbm_handle *h = new (std::nothrow) lbm_handle;
+    if (!h) return LBM_ENOMEM;
+    memset((void *)h, 0, sizeof(*h));
+    h->cfg = *cfg;
+    h->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return LBM_ECUDA; }
+    h->ops = ops_for(cfg->storage);
+    h->hg = host_geom(*cfg);
+    h->nxp = pitch_of(*cfg);
+    h->force = cfg->force_mode != LBM_FORCE_NONE;
+    h->force_set = cfg->force_mode != LBM_FORCE_FIELD;
+    h->ti = tile_info(*cfg);
+    h->ev_pool = new (std::nothrow) std::vector<cudaEvent_t>();
+    h->rec_kind = new (std::nothrow) std::vector<int>();
+    if (!h->ev_pool || !h->rec_kind) {
+        delete h->ev_pool;
+        delete h->rec_kind;
+        delete h;
+        return LBM_ENOMEM;
+    }
+    if (own) {
+        if (cudaMalloc(&buf, L.total) != cudaSuccess) { delete h->ev_pool; delete h->rec_kind; delete h; return LBM_ENOMEM; }
+        bytes = L.total;
+    } else {
+        if (!buf || ((uintptr_t)buf % ALIGN) != 0) { delete h->ev_pool; delete h->rec_kind; delete h; return LBM_EINVAL; }
+        if (bytes < L.total) { delete h->ev_pool; delete h->rec_kind; delete h; return LBM_ENOMEM; }
+    }
+    h->owns = own;
+    h->base = buf;
+    h->bytes = bytes;
+    char *b = (char *)buf;
+    h->f = b + L.f;
+    h->f2 = cfg->variant == LBM_VARIANT_TWO_LATTICE ? b + L.f2 : nullptr;
+    h->G = cfg->variant == LBM_VARIANT_MERGED ? b + L.G : nullptr;
+    h->partial = (double *)(b + L.partial);
+    h->red_out = (double *)(b + L.red_out);
+    h->flag = (int *)(b + L.flag);
+    const int64_t n = cfg->nx * cfg->ny * cfg->nz;
+    int64_t nb = (n + 255) / 256;
+    h->red_blocks = (int)(nb < RED_BLOCKS_MAX ? nb : RED_BLOCKS_MAX);
+    if (cudaMemsetAsync(buf, 0, L.total, h->stream) != cudaSuccess) {
+        if (own) cudaFree(buf);
+        delete h->ev_pool;
+        delete h->rec_kind;
+        delete h;
+        return LBM_ECUDA;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_config *cfg, void *stream, lbm_handle **out)
+{
+    return create_impl(cfg, stream, nullptr, 0, true, out);
+}
+
+int lbm_create_with_buffer(const lbm_config *cfg, void *stream, void *device_buffer, size_t bytes, lbm_handle **out)
+{
+    return create_impl(cfg, stream, device_buffer, bytes, false, out);
+}
+
+void lbm_destroy(lbm_handle *h)
+{
+    if (!h) return;
+    {
+        DeviceGuard g(h->device);
+        cudaStreamSynchronize(h->stream);
+        if (h->owns && h->base) cudaFree(h->base);
+        if (h->ev_pool)
+            for (cudaEvent_t e : *h->ev_pool) cudaEventDestroy(e);
+    }
+    delete h->ev_pool;
+    delete h->rec_kind;
+    delete h;
+}
+
+const char *lbm_strerror(int s)
+{
+    switch (s) {
+    case LBM_OK: return "success";
+    case LBM_EINVAL: return "invalid argument or configuration";
+    case LBM_ENOMEM: return "device allocation failed or buffer too small";
+    case LBM_ECUDA: return "CUDA runtime error";
+    case LBM_ESTATE: return "call not valid in the current state";
+    case LBM_ENONFINITE: return "non-finite value in the lattice";
+    case LBM_ETIMEOUT: return "bounded device wait gave up";
+    case LBM_EUNSUPPORTED: return "unsupported combination";
+    default: return "unknown status";
+    }
+}
+
+int lbm_lattice(int32_t *c, double *w)
+{
+    for (int i = 0; i < Q; ++i) {
+        if (c) { c[3 * i] = cx(i); c[3 * i + 1] = cy(i); c[3 * i + 2] = cz(i); }
+        if (w) w[i] = wgt(i);
+    }
+    return LBM_OK;
+}
+
+int lbm_init_equilibrium(lbm_handle *h, const void *rho, const void *u, int32_t dtype)
+{
+    if (!h || check_dtype(dtype)) return LBM_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return LBM_ECUDA;
+    CK(h->ops->init_eq(h->hg, h->nxp, h->f, rho, u, dtype, h->stream));
+    h->parity = PARITY_NATURAL;
+    h->t = 0;
+    h->adj_ready = false;
+    return LBM_OK;
+}
+
+int lbm_set_force(lbm_handle *h, const float *F)
+{
+    if (!h || !F) return LBM_EINVAL;
+    if (h->cfg.force_mode != LBM_FORCE_FIELD) return LBM_ESTATE;
+    h->hg.Ff = F;
+    h->force_set = true;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle *h, int64_t n)
+{
+    if (!h || n < 0) return LBM_EINVAL;
+    if (!h->force_set) return LBM_ESTATE;
+    DeviceGuard g(h->device);
+    if (!g.ok) return LBM_ECUDA;
+    const StorageOps &o = *h->ops;
+    while (n > 0) {
+        switch (h->cfg.variant) {
+        case LBM_VARIANT_TWO_LATTICE: {
+            CK(timed(h, LBM_KERNEL_TWO_LATTICE, [&] { return o.two_lattice(h->hg, h->nxp, h->force, h->f, h->f2, h->stream); }));
+            void *t = h->f; h->f = h->f2; h->f2 = t;
+            n -= 1; h->t += 1;
+            break;
+        }
+        case LBM_VARIANT_AA:
+            if (h->parity == PARITY_NATURAL) {
+                CK(timed(h, LBM_KERNEL_AA_EVEN, [&] { return o.aa_even(h->hg, h->nxp, h->force, h->f, h->stream); }));
+                h->parity = PARITY_A;
+            } else {
+                CK(timed(h, LBM_KERNEL_AA_ODD, [&] { return o.aa_odd(h->hg, h->nxp, h->force, h->f, h->stream); }));
+                h->parity = PARITY_NATURAL;
+            }
+            n -= 1; h->t += 1;
+            break;
+        default:  // MERGED
+            if (h->parity == PARITY_A) {
+                CK(timed(h, LBM_KERNEL_AA_ODD, [&] { return o.aa_odd(h->hg, h->nxp, h->force, h->f, h->stream); }));
+                h->parity = PARITY_NATURAL;
+                n -= 1; h->t += 1;
+            } else if (n >= 2) {
+                CK(timed(h, LBM_KERNEL_SNAPSHOT, [&] { return o.snapshot(h->hg, h->nxp, h->force, h->f, h->G, h->ti, h->stream); }));
+                CK(timed(h, LBM_KERNEL_MERGED, [&] { return o.merged(h->hg, h->nxp, h->force, h->f, h->G, h->ti, h->stream); }));
+                n -= 2; h->t += 2;
+            } else {
+                CK(timed(h, LBM_KERNEL_AA_EVEN, [&] { return o.aa_even(h->hg, h->nxp, h->force, h->f, h->stream); }));
+                h->parity = PARITY_A;
+                n -= 1; h->t += 1;
+            }
+            break;
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_time(const lbm_handle *h, int64_t *t)
+{
+    if (!h || !t) return LBM_EINVAL;
+    *t = h->t;
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_handle *h, void *rho, void *u, int32_t dtype)
+{
+    if (!h || check_dtype(dtype)) return LBM_EINVAL;
+    if (!h->force_set) return LBM_ESTATE;
+    if (!rho && !u) return LBM_OK;
+    DeviceGuard g(h->device);
+    if (!g.ok) return LBM_ECUDA;
+    CK(h->ops->moments(h->hg, h->nxp, h->force, h->parity, h->f, rho, u, dtype, h->stream));
+    return LBM_OK;
+}
+
+int lbm_populations(lbm_handle *h, void *f_out, int32_t dtype)
+{
+    if (!h || !f_out || check_dtype(dtype)) return LBM_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return LBM_ECUDA;
+    CK(h->ops->export_pop(h->hg, h->nxp, h->parity, h->f, f_out, dtype, h->stream));
+    return LBM_OK;
+}
+
+int lbm_init_populations(lbm_handle *h, const void *f_in, int32_t dtype)
+{
+    if (!h || !f_in || check_dtype(dtype)) return LBM_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return LBM_ECUDA;
+    CK(h->ops->import_pop(h->hg, h->nxp, h->f, f_in, dtype, h->stream));
+    h->parity = PARITY_NATURAL;
+    h->t = 0;
+    h->adj_ready = false;
+    return LBM_OK;
+}
+
+int lbm_reduce(lbm_handle *h, double *out)
+{
+    if (!h || !out) return LBM_EINVAL;
+    if (!h->force_set) return LBM_ESTATE;
+    DeviceGuard g(h->device);
+    if (!g.ok) return LBM_ECUDA;
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+    CK(h->ops->reduce(h->hg, h->nxp, h->force, h->parity, h->f, h->partial, h->red_blocks, h->flag, h->red_out,
+                      h->stream));
+    int bad = 0;
+    CK(cudaMemcpyAsync(out, h->red_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return bad ? LBM_ENONFINITE : LBM_OK;
+}
+
+int lbm_profile(lbm_handle *h, int32_t enable)
+{
+    if (!h) return LBM_EINVAL;
+    if (enable) h->rec_kind->clear();
+    h->prof_on = enable != 0;
+    return LBM_OK;
+}
+
+int lbm_profile_read(lbm_handle *h, int32_t kernel, int64_t *launches, double *total_ms)
+{
+    if (!h || kernel < 0 || kernel >= LBM_KERNEL_COUNT) return LBM_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return LBM_ECUDA;
+    int64_t cnt = 0;
+    double ms = 0.0;
+    for (size_t k = 0; k < h->rec_kind->size(); ++k) {
+        if ((*h->rec_kind)[k] != kernel) continue;
+        CK(cudaEventSynchronize((*h->ev_pool)[2 * k + 1]));
+        float e = 0.f;
+        CK(cudaEventElapsedTime(&e, (*h->ev_pool)[2 * k], (*h->ev_pool)[2 * k + 1]));
+        ms += e;
+        ++cnt;
+    }
+    if (launches) *launches = cnt;
+    if (total_ms) *total_ms = ms;
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------- adjoint
+
+int lbm_adjoint_step(lbm_handle *h, const void *f_t, const void *lambda_in, void *lambda_out, int32_t dtype,
+                     double *dLdF)
+{
+    if (!h || !f_t || !lambda_in || !lambda_out || lambda_in == lambda_out || check_dtype(dtype)) return LBM_EINVAL;
+    if (!h->force_set) return LBM_ESTATE;
+    DeviceGuard g(h->device);
+    if (!g.ok) return LBM_ECUDA;
+    CK(ops_for_dtype(dtype)->adjoint(h->hg, h->cfg.nx, h->force, f_t, lambda_in, lambda_out, dLdF, h->stream));
+    return LBM_OK;
+}
+
+int lbm_adjoint_seed(lbm_handle *h, const void *dLdrho, const void *dLdu, void *lambda, int32_t dtype, double *dLdF)
+{
+    if (!h || !dLdu || !lambda || check_dtype(dtype)) return LBM_EINVAL;
+    if (!h->force_set) return LBM_ESTATE;
+    DeviceGuard g(h->device);
+    if (!g.ok) return LBM_ECUDA;
+    // the caller's lambda buffer first receives the canonical populations;
+    // the seed kernel then replaces each cell's populations by its lambda
+    CK(h->ops->export_pop(h->hg, h->nxp, h->parity, h->f, lambda, dtype, h->stream));
+    CK(ops_for_dtype(dtype)->adjoint_seed(h->hg, h->cfg.nx, h->force, lambda, dLdrho, dLdu, dtype, lambda, dLdF,
+                                          h->stream));
+    return LBM_OK;
+}
+
+namespace {
+struct AdjLayout {
+    size_t state, lam, ckpt0, nck, seg0, nseg, lam0, total;
+};
+AdjLayout adj_layout(const lbm_handle *h, int64_t T, int64_t K)
+{
+    AdjLayout A;
+    A.state = align_up((size_t)state_elems(h->cfg) * h->ops->elem_size);
+    A.lam = align_up((size_t)state_elems(h->cfg) * h->ops->real_size);
+    A.nck = (size_t)((T + K - 1) / K) + 1;  // checkpoints at 0, K, 2K, ... plus f^T
+    A.nseg = (size_t)(K < 2 ? 2 : K);
+    A.ckpt0 = 0;
+    A.seg0 = A.nck * A.state;
+    A.lam0 = A.seg0 + A.nseg * A.state;
+    A.total = A.lam0 + 2 * A.lam;
+    return A;
+}
+}  // namespace
+
+int lbm_adjoint_workspace_bytes(const lbm_handle *h, int64_t T, int64_t K, size_t *bytes)
+{
+    if (!h || !bytes || T < 1 || K < 1) return LBM_EINVAL;
+    *bytes = adj_layout(h, T, K).total;
+    return LBM_OK;
+}
+
+int lbm_adjoint_forward(lbm_handle *h, int64_t T, int64_t K, void *work, size_t work_bytes)
+{
+    if (!h || !work || T < 1 || K < 1 || ((uintptr_t)work % ALIGN) != 0) return LBM_EINVAL;
+    if (!h->force_set) return LBM_ESTATE;
+    const AdjLayout A = adj_layout(h, T, K);
+    if (work_bytes < A.total) return LBM_ENOMEM;
+    DeviceGuard g(h->device);
+    if (!g.ok) return LBM_ECUDA;
+    const StorageOps &o = *h->ops;
+    char *w = (char *)work;
+    const size_t sb = (size_t)state_elems(h->cfg) * o.elem_size;
+    // f^0 in natural parity, exactly
+    if (h->parity == PARITY_A) CK(o.raw_natural(h->hg, h->nxp, h->f, w + A.ckpt0, h->stream));
+    else CK(cudaMemcpyAsync(w + A.ckpt0, h->f, sb, cudaMemcpyDeviceToDevice, h->stream));
+    void *cur = w + A.seg0, *nxt = w + A.seg0 + A.state;
+    CK(cudaMemcpyAsync(cur, w + A.ckpt0, sb, cudaMemcpyDeviceToDevice, h->stream));
+    for (int64_t t = 0; t < T; ++t) {
+        CK(o.two_lattice(h->hg, h->nxp, h->force, cur, nxt, h->stream));
+        void *tmp = cur; cur = nxt; nxt = tmp;
+        if ((t + 1) % K == 0 && t + 1 < T)
+            CK(cudaMemcpyAsync(w + A.ckpt0 + (size_t)((t + 1) / K) * A.state, cur, sb, cudaMemcpyDeviceToDevice,
+                               h->stream));
+    }
+    // f^T: kept for the seed and installed as the handle's state
+    CK(cudaMemcpyAsync(w + (A.nck - 1) * A.state, cur, sb, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->f, cur, sb, cudaMemcpyDeviceToDevice, h->stream));
+    h->parity = PARITY_NATURAL;
+    h->t += T;
+    h->adj_ready = true;
+    h->adj_T = T;
+    h->adj_K = K;
+    h->adj_work = work;
+    h->adj_bytes = work_bytes;
+    return LBM_OK;
+}
+
+int lbm_adjoint_backward(lbm_handle *h, const void *dLdrho, const void *dLdu, int32_t dtype, void *dLdf0,
+                         double *dLdF, void *work, size_t work_bytes)
+{
+    if (!h || !dLdu || check_dtype(dtype)) return LBM_EINVAL;
+    if (!h->adj_ready || work != h->adj_work || work_bytes != h->adj_bytes) return LBM_ESTATE;
+    DeviceGuard g(h->device);
+    if (!g.ok) return LBM_ECUDA;
+    const StorageOps &o = *h->ops;
+    const int64_t T = h->adj_T, K = h->adj_K;
+    const AdjLayout A = adj_layout(h, T, K);
+    char *w = (char *)work;
+    const size_t sb = (size_t)state_elems(h->cfg) * o.elem_size;
+    void *la = w + A.lam0, *lb = w + A.lam0 + A.lam;
+    CK(o.adjoint_seed(h->hg, h->nxp, h->force, w + (A.nck - 1) * A.state, dLdrho, dLdu, dtype, la, dLdF, h->stream));
+    const int64_t nseg = (T + K - 1) / K;
+    for (int64_t s = nseg - 1; s >= 0; --s) {
+        const int64_t t0 = s * K, t1 = (t0 + K < T) ? t0 + K : T;
+        char *seg = w + A.seg0;
+        CK(cudaMemcpyAsync(seg, w + A.ckpt0 + (size_t)s * A.state, sb, cudaMemcpyDeviceToDevice, h->stream));
+        for (int64_t j = 1; j < t1 - t0; ++j)
+            CK(o.two_lattice(h->hg, h->nxp, h->force, seg + (size_t)(j - 1) * A.state, seg + (size_t)j * A.state,
+                             h->stream));
+        for (int64_t t = t1 - 1; t >= t0; --t) {
+            CK(o.adjoint(h->hg, h->nxp, h->force, seg + (size_t)(t - t0) * A.state, la, lb, dLdF, h->stream));
+            void *tmp = la; la = lb; lb = tmp;
+        }
+    }
+    if (dLdf0) CK(o.pitched_to_canon(h->hg, h->nxp, la, dLdf0, dtype, Q, h->stream));
+    return LBM_OK;
+}
+
+}  // extern "C"

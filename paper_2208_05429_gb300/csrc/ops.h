@@ -1,0 +1,78 @@
+// ops.h -- host-side interface between the C ABI (lbm_api.cu) and the
+// per-storage kernel instantiations (inst_*.cu).  Internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// Problem description in double precision; converted to the compute type by
+// each instantiation.
+struct HostGeom {
+    int nx, ny, nz;
+    int per[3];
+    int lid[6];
+    double omega, kf;
+    double L[19];
+    double Fu[3];
+    const float *Ff;
+};
+
+// Tile geometry of the merged sweep and the layout of its shell snapshot.
+struct TileInfo {
+    int TX, TY;
+    int ntx, nty;
+    int xshell, yshell, zshell;
+    int64_t gx_off, gy_off, gz_off;
+    int64_t gx_slot, gy_slot, gz_slot;
+};
+
+enum { PARITY_NATURAL = 0, PARITY_A = 1 };
+
+// Launchers of one storage format.  `pitch` is the row pitch (elements) of
+// the population arrays passed in; canonical arrays use pitch = nx.
+struct StorageOps {
+    size_t elem_size;  // bytes of a stored population
+    size_t real_size;  // bytes of the compute type
+    int max_tile_y;    // largest merged tile height the shared memory allows
+    cudaError_t (*init_eq)(const HostGeom &, int64_t pitch, void *f, const void *rho, const void *u, int dtype,
+                           cudaStream_t);
+    cudaError_t (*two_lattice)(const HostGeom &, int64_t pitch, bool force, const void *src, void *dst,
+                               cudaStream_t);
+    cudaError_t (*aa_even)(const HostGeom &, int64_t pitch, bool force, void *f, cudaStream_t);
+    cudaError_t (*aa_odd)(const HostGeom &, int64_t pitch, bool force, void *f, cudaStream_t);
+    cudaError_t (*moments)(const HostGeom &, int64_t pitch, bool force, int parity, const void *f, void *rho,
+                           void *u, int dtype, cudaStream_t);
+    cudaError_t (*export_pop)(const HostGeom &, int64_t pitch, int parity, const void *f, void *out, int dtype,
+                              cudaStream_t);
+    cudaError_t (*import_pop)(const HostGeom &, int64_t pitch, void *f, const void *in, int dtype, cudaStream_t);
+    cudaError_t (*raw_natural)(const HostGeom &, int64_t pitch, const void *f, void *out, cudaStream_t);
+    // partial: 5 * nblocks doubles; out: 5 doubles (device)
+    cudaError_t (*reduce)(const HostGeom &, int64_t pitch, bool force, int parity, const void *f, double *partial,
+                          int nblocks, int *flag, double *out, cudaStream_t);
+    cudaError_t (*snapshot)(const HostGeom &, int64_t pitch, bool force, const void *f, void *G, const TileInfo &,
+                            cudaStream_t);
+    cudaError_t (*merged)(const HostGeom &, int64_t pitch, bool force, void *f, const void *G, const TileInfo &,
+                          cudaStream_t);
+    // lam_* are arrays of the compute type with the given pitch
+    cudaError_t (*adjoint)(const HostGeom &, int64_t pitch, bool force, const void *f, const void *lam_in,
+                           void *lam_out, double *gF, cudaStream_t);
+    cudaError_t (*adjoint_seed)(const HostGeom &, int64_t pitch, bool force, const void *f, const void *dLdrho,
+                                const void *dLdu, int dtype, void *lam, double *gF, cudaStream_t);
+    cudaError_t (*canon_to_pitched)(const HostGeom &, int64_t pitch, const void *in, int dtype, void *out, int ncomp,
+                                    cudaStream_t);
+    cudaError_t (*pitched_to_canon)(const HostGeom &, int64_t pitch, const void *in, void *out, int dtype, int ncomp,
+                                    cudaStream_t);
+};
+
+const StorageOps &ops_f64();
+const StorageOps &ops_f32();
+const StorageOps &ops_f32s();
+const StorageOps &ops_f16s();
+const StorageOps &ops_bf16s();
+
+constexpr int RED_BLOCKS_MAX = 1024;
+
+}  // namespace lbm

@@ -1,0 +1,96 @@
+"""The C-ABI library loads, exports every symbol include/lbm.h declares and
+validates configurations on the host (no GPU needed)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2208_05429_gb300 import lbm
+
+
+def test_every_declared_symbol_is_exported(cuda_lib):
+    names = lbm.declared_symbols()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(cuda_lib, n)]
+    assert not missing, missing
+    # and the binding wraps each of them
+    assert set(names) <= set(lbm._SIGNATURES)
+
+
+def test_lattice_table(cuda_lib):
+    c, w = lbm.lbm_lattice()
+    vecs = {tuple(v) for v in c}
+    assert len(vecs) == 19 and tuple(c[0]) == (0, 0, 0)
+    assert all(max(abs(v) for v in cv) <= 1 and sum(a * a for a in cv) <= 2 for cv in vecs)
+    for i in range(1, 10):
+        assert next(v for v in c[i] if v != 0) == -1
+        assert np.array_equal(c[i + 9], -c[i])
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.allclose(np.einsum("q,qa,qb->ab", w, c, c), np.eye(3) / 3, atol=1e-16)
+
+
+def test_default_config_valid(cuda_lib):
+    cfg = lbm.lbm_config_default()
+    assert (cfg.nx, cfg.ny, cfg.nz) == (32, 32, 32)
+    assert lbm.lbm_validate(cfg) == lbm.LBM_OK
+    assert lbm.lbm_required_bytes(cfg) >= 19 * 32 ** 3 * 4
+
+
+@pytest.mark.parametrize("field,value", [
+    ("nx", 0), ("ny", -3), ("nz", 70000), ("tau", 0.5), ("tau", float("nan")), ("rho_wall", 0.0),
+    ("storage", 9), ("variant", 3), ("force_mode", 5), ("tile_x", 16), ("tile_y", 5),
+])
+def test_invalid_configs_rejected(cuda_lib, field, value):
+    cfg = lbm.lbm_config_default()
+    setattr(cfg, field, value)
+    assert lbm.lbm_validate(cfg) == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_required_bytes(cfg)
+
+
+def test_invalid_faces_and_lid(cuda_lib):
+    cfg = lbm.lbm_config_default()
+    cfg.face_bc[0] = lbm.LBM_BC_WALL  # x- wall with x+ periodic
+    assert lbm.lbm_validate(cfg) == lbm.LBM_EINVAL
+    cfg = lbm.make_config((8, 8, 8), 0.6, lbm.CAVITY_BC, u_lid=(0.3, 0.0, 0.0))
+    assert lbm.lbm_validate(cfg) == lbm.LBM_EINVAL
+    cfg = lbm.make_config((8, 8, 8), 0.6, lbm.CAVITY_BC, u_lid=(0.05, 0.0, 0.0), storage="f64", tile=(32, 16))
+    assert lbm.lbm_validate(cfg) == lbm.LBM_EINVAL
+    cfg = lbm.make_config((2000, 2000, 2000), 0.6)
+    assert lbm.lbm_validate(cfg) == lbm.LBM_EINVAL
+
+
+def test_required_bytes_scale(cuda_lib):
+    aa = lbm.make_config((64, 64, 64), 0.6, storage="f32", variant="aa")
+    tl = lbm.make_config((64, 64, 64), 0.6, storage="f32", variant="two_lattice")
+    mg = lbm.make_config((64, 64, 64), 0.6, storage="f32", variant="merged")
+    h16 = lbm.make_config((64, 64, 64), 0.6, storage="f16s", variant="aa")
+    pop = 19 * 64 ** 3 * 4
+    assert pop <= lbm.lbm_required_bytes(aa) < pop * 1.01
+    assert 2 * pop <= lbm.lbm_required_bytes(tl) < 2 * pop * 1.01
+    assert pop < lbm.lbm_required_bytes(mg) < 1.6 * pop
+    assert pop // 2 <= lbm.lbm_required_bytes(h16) < pop
+
+
+def test_strerror(cuda_lib):
+    assert lbm.lbm_strerror(0) == "success"
+    assert "non-finite" in lbm.lbm_strerror(lbm.LBM_ENONFINITE)
+    assert lbm.lbm_strerror(12345) == "unknown status"
+
+
+def test_config_struct_layout_matches_header(cuda_lib):
+    """The ctypes mirror of lbm_config has the C layout (checked through a
+    round trip: lbm_config_default writes every field)."""
+    assert ctypes.sizeof(lbm.lbm_config) == 136
+    cfg = lbm.lbm_config_default()
+    assert cfg.tau == 0.6 and cfg.rho_wall == 1.0 and list(cfg.face_bc) == [0] * 6
+    assert cfg.storage == lbm.LBM_STORAGE_F32 and cfg.variant == lbm.LBM_VARIANT_AA
+
+
+def test_create_without_gpu_fails_cleanly(cuda_lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    cfg = lbm.lbm_config_default()
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_create(cfg, 0)

@@ -1,0 +1,157 @@
+"""GPU adjoint against the FP64 oracle adjoint (tiny grids) and against
+central finite differences on the differentiable-channel workload
+(128 x 64 x 64, periodic x, walls y and z, tau = 0.6, 200 steps, checkpoint
+every 20, per-cell force N(0, 1e-12) + 1e-5 x-hat, seed 2208; loss = mean
+squared difference between u_x on the outlet plane x = 127 and a parabolic
+target; 16 cells drawn with seed 5429, h = 1e-4 * max(|F|, 1e-5)).
+
+Tolerances (relative): FP64 adjoint vs oracle 1e-11; FP32 adjoint vs oracle
+1e-4; adjoint gradient vs finite differences 1e-4 (FP32 adjoint) and 1e-6
+(FP64 adjoint)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import BC_LID, BC_PERIODIC, BC_WALL, FORCE_FIELD
+from gpu_cases import gpu_perm, to_gpu_order, to_oracle_order
+from helpers import noisy_equilibrium, relmax
+from paper_2208_05429_gb300 import inputs
+from paper_2208_05429_gb300.lbm import Lattice
+
+pytestmark = pytest.mark.gpu
+
+
+def _small(lid=True, nx=8, ny=6, nz=5):
+    cfg = oracle.Config(nx=nx, ny=ny, nz=nz, tau=0.6, bc=(BC_PERIODIC, BC_PERIODIC, BC_WALL, BC_WALL, BC_WALL,
+                                                          BC_LID if lid else BC_WALL),
+                        u_lid=(0.03, 0.0, 0.0), force_mode=FORCE_FIELD)
+    cfg.force_field = inputs.channel_force(nx, ny, nz, seed=2208, sigma=1e-4, bias_x=1e-4).astype(np.float32).astype(np.float64)
+    return cfg
+
+
+def _gpu(cfg, storage):
+    import torch
+    return Lattice((cfg.nx, cfg.ny, cfg.nz), cfg.tau, bc=tuple(cfg.bc), u_lid=tuple(cfg.u_lid), storage=storage,
+                   variant="aa", force=torch.tensor(cfg.force_field, dtype=torch.float32, device="cuda"))
+
+
+@pytest.mark.parametrize("lid", [False, True])
+def test_adjoint_step_fp64_vs_oracle(gpu, lid):
+    import torch
+    cfg = _small(lid)
+    f = noisy_equilibrium(cfg, seed=4)
+    lam = np.random.default_rng(1).normal(size=f.shape)
+    gF_ref = np.zeros((3, *cfg.shape))
+    lam_ref = oracle.adjoint_step(cfg, f, lam, gF_ref)
+    lat = _gpu(cfg, "f64")
+    dev = lat.device
+    ft = torch.tensor(to_gpu_order(f), device=dev)
+    li = torch.tensor(to_gpu_order(lam), device=dev)
+    lo = torch.empty_like(li)
+    gF = torch.zeros((3, *cfg.shape), dtype=torch.float64, device=dev)
+    lat.adjoint_step(ft, li, lo, gF)
+    assert relmax(to_oracle_order(lo.cpu().numpy()), lam_ref) <= 1e-12
+    assert relmax(gF.cpu().numpy(), gF_ref) <= 1e-12
+
+
+def _plane_loss_grad(u, target):
+    g = np.zeros_like(u)
+    g[0, :, :, -1] = 2.0 * (u[0, :, :, -1] - target) / target.size
+    return g
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-11), ("f32", 1e-4)])
+def test_checkpointed_adjoint_vs_oracle(gpu, storage, tol):
+    import torch
+    cfg = _small(True)
+    T, K = 7, 3
+    f0 = noisy_equilibrium(cfg, seed=6, amp=0.01)
+    target = inputs.parabolic_target(cfg.ny, cfg.nz, Ut=1e-2)
+    lam_ref, gF_ref = oracle.adjoint_run(cfg, f0, T, lambda rho, u: _plane_loss_grad(u, target))
+    lat = _gpu(cfg, storage)
+    dev = lat.device
+    lat.init_populations(torch.tensor(to_gpu_order(f0), device=dev))
+    lat.adjoint_forward(T, K)
+    _, u = lat.moments(torch.float64)
+    dLdu = torch.tensor(_plane_loss_grad(u.cpu().numpy(), target), device=dev)
+    dt = torch.float64 if storage == "f64" else torch.float32
+    dLdf0, dLdF = lat.adjoint_backward(dLdu.to(dt))
+    assert relmax(to_oracle_order(dLdf0.double().cpu().numpy()), lam_ref) <= tol
+    assert relmax(dLdF.cpu().numpy(), gF_ref) <= tol
+    # the handle was left at f^T, bit-identical to stepping T times
+    ref = _gpu(cfg, storage)
+    ref.init_populations(torch.tensor(to_gpu_order(f0), device=dev))
+    ref.step(T)
+    assert torch.equal(ref.populations(torch.float64), lat.populations(torch.float64))
+
+
+# ----------------------------------------------------------- channel workload
+
+NX, NY, NZ, TAU, T, K = 128, 64, 64, 0.6, 200, 20
+
+
+def _channel_lattice(storage, F):
+    return Lattice((NX, NY, NZ), TAU, bc=("periodic", "periodic", "wall", "wall", "wall", "wall"),
+                   storage=storage, variant="merged", force=F)
+
+
+def _loss_and_grad(u, target):
+    d = u[0, :, :, NX - 1] - target
+    L = (d * d).mean()
+    g = np.zeros_like(u)
+    g[0, :, :, NX - 1] = 2.0 * d / d.size
+    return L, g
+
+
+def test_channel_gradient_vs_finite_differences(gpu):
+    import torch
+    from paper_2208_05429_gb300.autograd import simulate
+    dev = torch.device("cuda", 0)
+    F32 = inputs.channel_force(NX, NY, NZ, seed=2208, sigma=1e-6, bias_x=1e-5)
+    target = inputs.parabolic_target(NY, NZ, Ut=1e-3)
+    t_target = torch.tensor(target, device=dev)
+
+    def outlet_u(Fnp, storage="f64"):
+        lat = _channel_lattice(storage, torch.tensor(Fnp, device=dev))
+        lat.init_equilibrium()
+        lat.step(T)
+        _, u = lat.moments(torch.float64)
+        return u[0, :, :, NX - 1].clone()
+
+    grads = {}
+    for storage in ("f64", "f32"):
+        lat = _channel_lattice(storage, torch.tensor(F32, device=dev))
+        lat.init_equilibrium()
+        dt = torch.float64 if storage == "f64" else torch.float32
+        f0 = lat.populations(dt)
+        Fp = torch.tensor(F32, device=dev, requires_grad=True)
+        u = simulate(f0.requires_grad_(True), Fp, lat, T, K)
+        d = u[0, :, :, NX - 1] - t_target.to(dt)
+        loss = (d * d).mean()
+        loss.backward()
+        grads[storage] = Fp.grad.double().cpu().numpy()
+        assert f0.grad is not None and torch.isfinite(f0.grad).all()
+
+    cells = inputs.sample_cells(NX, NY, NZ, 16, seed=5429)
+    rng = np.random.default_rng(5429)
+    worst = {"f64": 0.0, "f32": 0.0}
+    for (x, y, z) in cells:
+        a = int(rng.integers(3))
+        base = float(F32[a, z, y, x])
+        h = 1e-4 * max(abs(base), 1e-5)
+        Fp, Fm = F32.copy(), F32.copy()
+        Fp[a, z, y, x] = np.float32(base + h)
+        Fm[a, z, y, x] = np.float32(base - h)
+        step = float(Fp[a, z, y, x]) - float(Fm[a, z, y, x])
+        # L(F+) - L(F-) written as mean((u+ - u-)(u+ + u- - 2 target)): the
+        # same central difference without subtracting two nearly equal losses
+        up, um = outlet_u(Fp), outlet_u(Fm)
+        fd = float(((up - um) * (up + um - 2.0 * t_target)).mean()) / step
+        for s in ("f64", "f32"):
+            g = grads[s][a, z, y, x]
+            rel = abs(g - fd) / max(abs(fd), 1e-30)
+            worst[s] = max(worst[s], rel)
+            print(f"cell ({x},{y},{z}) comp {a}: fd {fd:.6e} adjoint {s} {g:.6e} rel {rel:.2e}")
+    print(f"adjoint vs central differences on 16 cells: worst rel err FP64 {worst['f64']:.2e}, FP32 {worst['f32']:.2e}")
+    assert worst["f64"] <= 1e-6
+    assert worst["f32"] <= 1e-4

@@ -1,0 +1,84 @@
+"""The three schedules agree bit for bit (the paper verifies its two-step
+solvers against the single-step ones, Sec. 5.1; here the check is exact):
+TWO_LATTICE == AA == MERGED for every storage format, every MERGED tile
+shape, odd and even step counts and mixed step(n) sequences."""
+import numpy as np
+import pytest
+
+from gpu_cases import cases, load_state, make_gpu, oracle_force_as_f32, start_state
+
+pytestmark = pytest.mark.gpu
+
+CASES = cases()
+STORAGES = ["f64", "f32", "f32s", "f16s", "bf16s"]
+
+
+def _raw(lat):
+    import torch
+    return lat.populations(torch.float64)
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("nsteps", [5, 6])
+def test_schedules_bitwise_equal(gpu, storage, name, nsteps):
+    import torch
+    cfg = oracle_force_as_f32(CASES[name])
+    f0 = start_state(cfg, seed=3)
+    ref = None
+    tiles = [(32, 4), (32, 8)] + ([] if storage == "f64" else [(32, 16)])
+    runs = [("two_lattice", (0, 0)), ("aa", (0, 0))] + [("merged", t) for t in tiles]
+    for variant, tile in runs:
+        lat = make_gpu(cfg, storage, variant, tile=tile)
+        load_state(lat, f0)
+        lat.step(nsteps)
+        got = _raw(lat)
+        if ref is None:
+            ref = got
+        else:
+            assert torch.equal(got, ref), (variant, tile)
+        rho, u = lat.moments(torch.float64)
+        assert torch.isfinite(u).all()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_mixed_step_sequences(gpu, storage):
+    """MERGED stepped 1, 2, 3, 1, 2 steps at a time (crossing AA parities)
+    equals AA stepped 9 times and TWO_LATTICE stepped one by one."""
+    import torch
+    cfg = oracle_force_as_f32(CASES["channel_37x19x23"])
+    f0 = start_state(cfg, seed=9)
+    a = make_gpu(cfg, storage, "aa")
+    load_state(a, f0)
+    a.step(9)
+    m = make_gpu(cfg, storage, "merged", tile=(32, 8))
+    load_state(m, f0)
+    for k in (1, 2, 3, 1, 2):
+        m.step(k)
+    t = make_gpu(cfg, storage, "two_lattice")
+    load_state(t, f0)
+    for _ in range(9):
+        t.step(1)
+    assert m.time == a.time == t.time == 9
+    ra, rm, rt = _raw(a), _raw(m), _raw(t)
+    assert torch.equal(ra, rm) and torch.equal(ra, rt)
+    # moments agree at both parities (a is at the odd parity after 9 steps)
+    for lat in (a, m, t):
+        rho, u = lat.moments(torch.float64)
+        r0, u0 = a.moments(torch.float64)
+        assert torch.equal(rho, r0) and torch.equal(u, u0)
+
+
+def test_equilibrium_init_matches_oracle(gpu):
+    import torch
+    import oracle
+    from paper_2208_05429_gb300 import inputs
+    from gpu_cases import gpu_state
+    from helpers import relmax
+    cfg = oracle.Config(nx=24, ny=20, nz=18, tau=0.6)
+    u0 = inputs.taylor_green_velocity(24, 20, 18, 0.04)
+    rho0, _ = inputs.random_density_velocity(24, 20, 18, seed=2)
+    ref = oracle.init_equilibrium(cfg, rho0, u0)
+    lat = make_gpu(cfg, "f64", "aa")
+    lat.init_equilibrium(torch.tensor(rho0, device=lat.device), torch.tensor(u0, device=lat.device))
+    assert relmax(gpu_state(lat), ref) <= 1e-15
