@@ -106,8 +106,9 @@ void lbm_config_default(lbm_config *cfg);
 /* Check a configuration without allocating.  LBM_EINVAL on: a dimension < 1,
  * cell count beyond 2^31, tau <= 0.5, a face type out of range, an axis with
  * one periodic and one non-periodic face, |u_lid| >= 0.3, rho_wall <= 0,
- * unknown storage/variant/force mode, negative tile sizes or a tile_x that is
- * not a multiple of 32. */
+ * unknown storage/variant/force mode, a tile_x other than 0 or 32, or a
+ * tile_y other than 0, 4, 8, 16 or too large for the shared memory of the
+ * merged kernel in this storage format (F64 allows 4 only). */
 int lbm_validate(const lbm_config *cfg);
 
 /* Device bytes a handle of this configuration uses (populations, second
@@ -179,7 +180,10 @@ int lbm_init_populations(lbm_handle *h, const void *f_in, int32_t dtype);
  *   out[4] = sum 1/2 rho |u|^2    (kinetic energy, u as in lbm_moments)
  * Deterministic (fixed summation tree).  Synchronises the stream.
  * LBM_ENONFINITE if any cell has a non-finite density or velocity; out is
- * still written. */
+ * still written.  LBM_ETIMEOUT if, since the previous call, a merged sweep
+ * gave up waiting for one of its asynchronous plane copies (every wait in
+ * the kernels is bounded); the lattice is then invalid and the flag is
+ * cleared. */
 int lbm_reduce(lbm_handle *h, double *out);
 
 /* ---------------- per-kernel timing ----------------

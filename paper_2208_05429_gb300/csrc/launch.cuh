@@ -5,6 +5,8 @@
 #include "kernels.cuh"
 #include "merged.cuh"
 
+#include <string.h>
+
 namespace lbm {
 
 constexpr int CELL_BLOCK = 128;
@@ -101,39 +103,57 @@ struct Launch {
         if (tot == 0) return cudaSuccess;
         const unsigned blocks = (unsigned)((tot + 255) / 256);
         const Geom<R> g = make_geom<R>(h, pitch);
-        if (force) k_snapshot<S, true><<<blocks, 256, 0, st>>>(g, (const T *)f, (T *)G, ti, cz_, cy_, cx_);
-        else k_snapshot<S, false><<<blocks, 256, 0, st>>>(g, (const T *)f, (T *)G, ti, cz_, cy_, cx_);
+        if (force) k_snapshot<S, true><<<blocks, 256, 0, st>>>(g, (const T *)f, (R *)G, ti, cz_, cy_, cx_);
+        else k_snapshot<S, false><<<blocks, 256, 0, st>>>(g, (const T *)f, (R *)G, ti, cz_, cy_, cx_);
         return cudaGetLastError();
+    }
+
+    template <int TY>
+    static constexpr size_t smem_of() { return MergedSmem<32, TY, T, R>::bytes; }
+    static size_t merged_smem(int ty)
+    {
+        constexpr size_t LIMIT = 232448;  // opt-in shared memory per block
+        size_t b = 0;
+        if (ty == 4) b = smem_of<4>();
+        else if (ty == 8) b = smem_of<8>();
+        else if (ty == 16) b = smem_of<16>();
+        return b <= LIMIT ? b : 0;
     }
 
     template <int TX, int TY>
     static cudaError_t merged_t(const HostGeom &h, int64_t pitch, bool force, void *f, const void *G,
-                                const TileInfo &ti, cudaStream_t st)
+                                const TileInfo &ti, const void *tmap, int *status, cudaStream_t st)
     {
-        const size_t smem = (size_t)4 * Q * TX * TY * sizeof(R);
+        const size_t smem = MergedSmem<TX, TY, T, R>::bytes;
         const dim3 grid(ti.ntx, ti.nty), block(TX, TY);
         const Geom<R> g = make_geom<R>(h, pitch);
+        CUtensorMap map;
+        memcpy(&map, tmap, sizeof(map));
         cudaError_t e;
         if (force) {
             e = cudaFuncSetAttribute(k_merged<S, true, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            k_merged<S, true, TX, TY><<<grid, block, smem, st>>>(g, (T *)f, (const T *)G, ti);
+            k_merged<S, true, TX, TY><<<grid, block, smem, st>>>(map, g, (T *)f, (const R *)G, ti, status);
         } else {
             e = cudaFuncSetAttribute(k_merged<S, false, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            k_merged<S, false, TX, TY><<<grid, block, smem, st>>>(g, (T *)f, (const T *)G, ti);
+            k_merged<S, false, TX, TY><<<grid, block, smem, st>>>(map, g, (T *)f, (const R *)G, ti, status);
         }
         return cudaGetLastError();
     }
     static cudaError_t merged(const HostGeom &h, int64_t pitch, bool force, void *f, const void *G,
-                              const TileInfo &ti, cudaStream_t st)
+                              const TileInfo &ti, const void *tmap, int *status, cudaStream_t st)
     {
-        if (ti.TX != 32) return cudaErrorInvalidValue;
+        if (ti.TX != 32 || merged_smem(ti.TY) == 0) return cudaErrorInvalidValue;
         switch (ti.TY) {
-        case 4: return merged_t<32, 4>(h, pitch, force, f, G, ti, st);
-        case 8: return merged_t<32, 8>(h, pitch, force, f, G, ti, st);
+        case 4: return merged_t<32, 4>(h, pitch, force, f, G, ti, tmap, status, st);
+        case 8:
+            if constexpr (MergedSmem<32, 8, T, R>::bytes <= 232448)
+                return merged_t<32, 8>(h, pitch, force, f, G, ti, tmap, status, st);
+            else return cudaErrorInvalidValue;
         case 16:
-            if constexpr (sizeof(R) == 4) return merged_t<32, 16>(h, pitch, force, f, G, ti, st);
+            if constexpr (MergedSmem<32, 16, T, R>::bytes <= 232448)
+                return merged_t<32, 16>(h, pitch, force, f, G, ti, tmap, status, st);
             else return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
         }
@@ -175,7 +195,8 @@ StorageOps make_ops()
     StorageOps o;
     o.elem_size = sizeof(typename S::T);
     o.real_size = sizeof(typename S::R);
-    o.max_tile_y = sizeof(typename S::R) == 4 ? 16 : 8;
+    o.max_tile_y = L::merged_smem(16) ? 16 : (L::merged_smem(8) ? 8 : 4);
+    o.merged_smem = &L::merged_smem;
     o.init_eq = &L::init_eq;
     o.two_lattice = &L::two_lattice;
     o.aa_even = &L::aa_even;

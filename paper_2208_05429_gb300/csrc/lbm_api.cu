@@ -1,6 +1,7 @@
 // lbm_api.cu -- the C ABI declared in include/lbm.h: configuration checks,
 // the handle and its device memory, AA parity bookkeeping, schedule dispatch
 // and the checkpointed adjoint driver.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -29,6 +30,8 @@ struct lbm_handle {
     void *f2;      // second lattice (TWO_LATTICE)
     void *G;       // shell snapshot (MERGED)
     TileInfo ti;
+    CUtensorMap tmap;  // TMA descriptor of f (MERGED)
+    int *status;       // device status word: bit 2 = a bounded wait gave up
     double *partial;
     double *red_out;
     int *flag;
@@ -80,7 +83,7 @@ size_t elem_size_of(int storage)
 }
 size_t real_size_of(int storage) { return storage == LBM_STORAGE_F64 ? 8 : 4; }
 
-int default_tile_y(const lbm_config &c) { return c.storage == LBM_STORAGE_F64 ? 8 : 16; }
+int default_tile_y(const lbm_config &c) { return ops_for(c.storage)->max_tile_y; }
 
 TileInfo tile_info(const lbm_config &c)
 {
@@ -110,7 +113,7 @@ int64_t ghost_elems(const lbm_config &c)
 }
 
 struct Layout {
-    size_t f, f2, G, partial, red_out, flag, total;
+    size_t f, f2, G, partial, red_out, flag, status, total;
 };
 
 Layout layout_of(const lbm_config &c)
@@ -121,10 +124,11 @@ Layout layout_of(const lbm_config &c)
     size_t off = 0;
     L.f = off; off += pop;
     L.f2 = off; if (c.variant == LBM_VARIANT_TWO_LATTICE) off += pop;
-    L.G = off; off += align_up((size_t)ghost_elems(c) * es);
+    L.G = off; off += align_up((size_t)ghost_elems(c) * real_size_of(c.storage));
     L.partial = off; off += align_up(sizeof(double) * 5 * RED_BLOCKS_MAX);
     L.red_out = off; off += align_up(sizeof(double) * 5);
     L.flag = off; off += align_up(sizeof(int));
+    L.status = off; off += align_up(sizeof(int));
     L.total = off;
     return L;
 }
@@ -168,6 +172,50 @@ struct DeviceGuard {
     do {                                           \
         if ((call) != cudaSuccess) return LBM_ECUDA; \
     } while (0)
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no
+// link-time dependency on libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 4D map over f[q][z][y][x] (x extent nx, row pitch nxp) with a box of one
+// tile plane and all 19 directions.
+bool make_tmap(const lbm_config &c, const TileInfo &ti, void *f, CUtensorMap *map)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    CUtensorMapDataType dt;
+    switch (c.storage) {
+    case LBM_STORAGE_F64: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT64; break;
+    case LBM_STORAGE_F16S: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; break;
+    case LBM_STORAGE_BF16S: dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; break;
+    default: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; break;
+    }
+    const cuuint64_t es = elem_size_of(c.storage), nxp = (cuuint64_t)pitch_of(c);
+    const cuuint64_t dims[4] = {(cuuint64_t)c.nx, (cuuint64_t)c.ny, (cuuint64_t)c.nz, (cuuint64_t)Q};
+    const cuuint64_t strides[3] = {nxp * es, nxp * (cuuint64_t)c.ny * es, nxp * (cuuint64_t)c.ny * (cuuint64_t)c.nz * es};
+    const cuuint32_t box[4] = {(cuuint32_t)ti.TX, (cuuint32_t)ti.TY, 1u, (cuuint32_t)Q};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    return fn(map, dt, 4, f, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 int check_dtype(int32_t dtype) { return dtype == LBM_DTYPE_F32 || dtype == LBM_DTYPE_F64 ? LBM_OK : LBM_EINVAL; }
 
@@ -234,7 +282,7 @@ int lbm_validate(const lbm_config *c)
         if (!isfinite(c->force_uniform[a])) return LBM_EINVAL;
     if (c->tile_x != 0 && c->tile_x != 32) return LBM_EINVAL;
     if (c->tile_y != 0 && c->tile_y != 4 && c->tile_y != 8 && c->tile_y != 16) return LBM_EINVAL;
-    if (c->tile_y == 16 && c->storage == LBM_STORAGE_F64) return LBM_EINVAL;
+    if (c->tile_y != 0 && ops_for(c->storage)->merged_smem(c->tile_y) == 0) return LBM_EINVAL;
     return LBM_OK;
 }
 
@@ -291,10 +339,12 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
     h->partial = (double *)(b + L.partial);
     h->red_out = (double *)(b + L.red_out);
     h->flag = (int *)(b + L.flag);
+    h->status = (int *)(b + L.status);
     const int64_t n = cfg->nx * cfg->ny * cfg->nz;
     int64_t nb = (n + 255) / 256;
     h->red_blocks = (int)(nb < RED_BLOCKS_MAX ? nb : RED_BLOCKS_MAX);
-    if (cudaMemsetAsync(buf, 0, L.total, h->stream) != cudaSuccess) {
+    if ((cfg->variant == LBM_VARIANT_MERGED && !make_tmap(*cfg, h->ti, h->f, &h->tmap)) ||
+        cudaMemsetAsync(buf, 0, L.total, h->stream) != cudaSuccess) {
         if (own) cudaFree(buf);
         delete h->ev_pool;
         delete h->rec_kind;
@@ -407,7 +457,9 @@ int lbm_step(lbm_handle *h, int64_t n)
                 n -= 1; h->t += 1;
             } else if (n >= 2) {
                 CK(timed(h, LBM_KERNEL_SNAPSHOT, [&] { return o.snapshot(h->hg, h->nxp, h->force, h->f, h->G, h->ti, h->stream); }));
-                CK(timed(h, LBM_KERNEL_MERGED, [&] { return o.merged(h->hg, h->nxp, h->force, h->f, h->G, h->ti, h->stream); }));
+                CK(timed(h, LBM_KERNEL_MERGED, [&] {
+                    return o.merged(h->hg, h->nxp, h->force, h->f, h->G, h->ti, &h->tmap, h->status, h->stream);
+                }));
                 n -= 2; h->t += 2;
             } else {
                 CK(timed(h, LBM_KERNEL_AA_EVEN, [&] { return o.aa_even(h->hg, h->nxp, h->force, h->f, h->stream); }));
@@ -468,10 +520,15 @@ int lbm_reduce(lbm_handle *h, double *out)
     CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
     CK(h->ops->reduce(h->hg, h->nxp, h->force, h->parity, h->f, h->partial, h->red_blocks, h->flag, h->red_out,
                       h->stream));
-    int bad = 0;
+    int bad = 0, st = 0;
     CK(cudaMemcpyAsync(out, h->red_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (st) {
+        CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+        return LBM_ETIMEOUT;
+    }
     return bad ? LBM_ENONFINITE : LBM_OK;
 }
 

@@ -52,10 +52,13 @@ struct StorageOps {
     // partial: 5 * nblocks doubles; out: 5 doubles (device)
     cudaError_t (*reduce)(const HostGeom &, int64_t pitch, bool force, int parity, const void *f, double *partial,
                           int nblocks, int *flag, double *out, cudaStream_t);
+    // G holds compute-type values; tmap is the CUtensorMap of f (64 bytes,
+    // host memory); status receives bit 2 when a bounded wait gave up
     cudaError_t (*snapshot)(const HostGeom &, int64_t pitch, bool force, const void *f, void *G, const TileInfo &,
                             cudaStream_t);
     cudaError_t (*merged)(const HostGeom &, int64_t pitch, bool force, void *f, const void *G, const TileInfo &,
-                          cudaStream_t);
+                          const void *tmap, int *status, cudaStream_t);
+    size_t (*merged_smem)(int tile_y);  // dynamic shared memory of the merged kernel (0 = not built)
     // lam_* are arrays of the compute type with the given pitch
     cudaError_t (*adjoint)(const HostGeom &, int64_t pitch, bool force, const void *f, const void *lam_in,
                            void *lam_out, double *gF, cudaStream_t);
