@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--size", type=int, default=256)
     p.add_argument("--storage", default="f32", choices=sorted(ELEM))
-    p.add_argument("--variant", default="merged", choices=["merged", "aa", "two_lattice"])
+    p.add_argument("--variant", default="merged", choices=["merged", "wavefront", "aa", "two_lattice"])
     p.add_argument("--tile-y", type=int, default=0)
     p.add_argument("--no-extras", action="store_true", help="skip the per-variant, adjoint and CPU legs")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle baseline")
@@ -410,7 +410,7 @@ def main():
     del lat
 
     value = world * cells * 2 * args.steps / (ms * 1e3)
-    dominant = "merged" if args.variant == "merged" else ("aa_odd" if args.variant == "aa" else "two_lattice")
+    dominant = {"merged": "merged", "wavefront": "wavefront", "aa": "aa_odd"}.get(args.variant, "two_lattice")
     roof = roofline_of(prof, dominant, args.storage, cells, peak, peak_kind)
     launches = sum(v[0] for v in prof.values())
     if "snapshot" in prof and roof is not None:
@@ -438,14 +438,15 @@ def main():
         except Exception as e:  # keep the main line if a secondary leg fails
             line["e2e"] = {"error": repr(e)}
         variants = {}
-        for st, var in (("f32", "aa"), ("f32", "two_lattice"), ("f16s", "merged"), ("bf16s", "merged"),
-                        ("f16s", "aa"), ("f64", "merged")):
+        for st, var in (("f32", "merged"), ("f32", "wavefront"), ("f32", "aa"), ("f32", "two_lattice"),
+                        ("f16s", "wavefront"), ("bf16s", "wavefront"), ("f16s", "merged"), ("f16s", "aa"),
+                        ("f64", "wavefront")):
             if (st, var) == (args.storage, args.variant):
                 continue
             k = min(args.steps, 300)
             vms, vprof, vl = time_variant(n, st, var, k, 5)
             del vl
-            dk = "merged" if var == "merged" else ("aa_odd" if var == "aa" else "two_lattice")
+            dk = {"merged": "merged", "wavefront": "wavefront", "aa": "aa_odd"}.get(var, "two_lattice")
             r = roofline_of(vprof, dk, st, cells, peak, peak_kind)
             variants[f"{var}_{st}"] = {"MLUPS": round(cells * 2 * k / (vms * 1e3), 1),
                                        "kernel_frac_of_peak": r["frac"] if r else None,

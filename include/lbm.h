@@ -77,8 +77,17 @@ enum { LBM_STORAGE_F64 = 0, LBM_STORAGE_F32 = 1, LBM_STORAGE_F32S = 2,
  *                kernel marching z performs the even and the odd step of a
  *                column in one pass; a pre-pass snapshots the tile shells so
  *                that tiles never read what a neighbouring tile has already
- *                overwritten (the role of Stage I of Alg. 3). */
-enum { LBM_VARIANT_TWO_LATTICE = 0, LBM_VARIANT_AA = 1, LBM_VARIANT_MERGED = 2 };
+ *                overwritten (the role of Stage I of Alg. 3).
+ *   WAVEFRONT    single copy, two time steps per DRAM round trip through the
+ *                L2 cache (the cache reuse of Sec. 4.1 and 5.2): one
+ *                persistent kernel runs the even step of plane p+L+1 and the
+ *                odd step of plane p as ordered work items; the few planes in
+ *                flight stay in L2 between their two steps.  The lead L
+ *                (default 4 planes) can be set at handle creation with the
+ *                environment variable LBM_WAVEFRONT_AHEAD (1..64), the
+ *                cells per work item (default 4096, whole rows) with
+ *                LBM_WAVEFRONT_ITEM_CELLS. */
+enum { LBM_VARIANT_TWO_LATTICE = 0, LBM_VARIANT_AA = 1, LBM_VARIANT_MERGED = 2, LBM_VARIANT_WAVEFRONT = 3 };
 
 /* Body force (Guo forcing): none, one vector for every cell, or a per-cell
  * FP32 field [3][z][y][x] set with lbm_set_force(). */
@@ -112,8 +121,9 @@ void lbm_config_default(lbm_config *cfg);
 int lbm_validate(const lbm_config *cfg);
 
 /* Device bytes a handle of this configuration uses (populations, second
- * lattice for TWO_LATTICE, tile-shell snapshot for MERGED, reduction
- * scratch), each region aligned to 256 bytes.  *bytes is a host output. */
+ * lattice for TWO_LATTICE, tile-shell snapshot for MERGED, work schedule
+ * for WAVEFRONT, reduction scratch), each region aligned to 256 bytes.
+ * *bytes is a host output. */
 int lbm_required_bytes(const lbm_config *cfg, size_t *bytes);
 
 /* Create a handle that allocates its own device memory (cudaMalloc on the
@@ -180,16 +190,16 @@ int lbm_init_populations(lbm_handle *h, const void *f_in, int32_t dtype);
  *   out[4] = sum 1/2 rho |u|^2    (kinetic energy, u as in lbm_moments)
  * Deterministic (fixed summation tree).  Synchronises the stream.
  * LBM_ENONFINITE if any cell has a non-finite density or velocity; out is
- * still written.  LBM_ETIMEOUT if, since the previous call, a merged sweep
- * gave up waiting for one of its asynchronous plane copies (every wait in
- * the kernels is bounded); the lattice is then invalid and the flag is
- * cleared. */
+ * still written.  LBM_ETIMEOUT if, since the previous call, a MERGED sweep
+ * gave up waiting for one of its asynchronous plane copies or a WAVEFRONT
+ * sweep for one of its work items (every wait in the kernels is bounded);
+ * the lattice is then invalid and the flag is cleared. */
 int lbm_reduce(lbm_handle *h, double *out);
 
 /* ---------------- per-kernel timing ----------------
  * Kernel classes launched by lbm_step(). */
 enum { LBM_KERNEL_TWO_LATTICE = 0, LBM_KERNEL_AA_EVEN = 1, LBM_KERNEL_AA_ODD = 2,
-       LBM_KERNEL_SNAPSHOT = 3, LBM_KERNEL_MERGED = 4, LBM_KERNEL_COUNT = 5 };
+       LBM_KERNEL_SNAPSHOT = 3, LBM_KERNEL_MERGED = 4, LBM_KERNEL_WAVEFRONT = 5, LBM_KERNEL_COUNT = 6 };
 
 /* enable = 1: from now on every kernel lbm_step() launches is bracketed by
  * two CUDA events recorded on the handle's stream (earlier records are

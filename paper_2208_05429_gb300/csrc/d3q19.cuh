@@ -233,7 +233,29 @@ struct Geom {
     R L[Q];              // 6 w_k rho_w (c_k . u_lid): added to incoming slot k of a lid link
     R Fu[3];             // uniform force
     const float *Ff;     // per-cell force field [3][N] canonical, or nullptr
+    int32_t noff[Q];     // cell-index offset of the neighbour x + c_i (no wrap)
 };
+
+// Base pointer of every direction slot, passed by value so that each access
+// is one 32-bit cell index away from a kernel-parameter pointer.
+template <class T>
+struct Dirs {
+    T *p[Q];
+};
+
+// Per-cell face information: the index correction of a step that wraps
+// through a periodic face, and which faces are walls / moving lids.  Bits
+// and adj[] entries are ordered x-, x+, y-, y+, z-, z+.
+struct Faces {
+    int32_t adj[6];
+    unsigned wall, lid;
+};
+
+// Face bits crossed by a step along (dx, dy, dz) from a cell next to them.
+__host__ __device__ constexpr unsigned face_mask(int dx, int dy, int dz)
+{
+    return (dx < 0 ? 1u : dx > 0 ? 2u : 0u) | (dy < 0 ? 4u : dy > 0 ? 8u : 0u) | (dz < 0 ? 16u : dz > 0 ? 32u : 0u);
+}
 
 // Link from (x,y,z) along d: returns true and the wrapped target cell, or
 // false for a wall link (and tells whether a lid face is crossed).
@@ -263,6 +285,51 @@ template <class R>
 __device__ __forceinline__ int64_t cell_of(const Geom<R> &g, int x, int y, int z)
 {
     return (int64_t)z * g.plane + (int64_t)y * g.nxp + x;
+}
+
+// 32-bit cell index inside one direction slot (slot sizes are below 2^31).
+template <class R>
+__device__ __forceinline__ int cell32(const Geom<R> &g, int x, int y, int z)
+{
+    return z * (int)g.plane + y * (int)g.nxp + x;
+}
+
+template <class R>
+__device__ __forceinline__ Faces faces_of(const Geom<R> &g, int x, int y, int z)
+{
+    Faces fc;
+    fc.wall = 0u;
+    fc.lid = 0u;
+    for (int k = 0; k < 6; ++k) fc.adj[k] = 0;
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const int p[3] = {x, y, z};
+    const int stride[3] = {1, (int)g.nxp, (int)g.plane};
+    for (int a = 0; a < 3; ++a) {
+        if (p[a] == 0) {
+            if (g.per[a]) fc.adj[2 * a] = n[a] * stride[a];
+            else { fc.wall |= 1u << (2 * a); if (g.lid[2 * a]) fc.lid |= 1u << (2 * a); }
+        }
+        if (p[a] == n[a] - 1) {
+            if (g.per[a]) fc.adj[2 * a + 1] = -n[a] * stride[a];
+            else { fc.wall |= 2u << (2 * a); if (g.lid[2 * a + 1]) fc.lid |= 2u << (2 * a); }
+        }
+    }
+    return fc;
+}
+
+// Cell-index offset of the step (DX, DY, DZ) from a cell with faces fc
+// (wrapping through periodic faces; meaningless across a wall).
+template <int DX, int DY, int DZ, class R>
+__device__ __forceinline__ int step_offset(const Geom<R> &g, const Faces &fc)
+{
+    int o = DZ * (int)g.plane + DY * (int)g.nxp + DX;
+    if constexpr (DX < 0) o += fc.adj[0];
+    if constexpr (DX > 0) o += fc.adj[1];
+    if constexpr (DY < 0) o += fc.adj[2];
+    if constexpr (DY > 0) o += fc.adj[3];
+    if constexpr (DZ < 0) o += fc.adj[4];
+    if constexpr (DZ > 0) o += fc.adj[5];
+    return o;
 }
 
 // True when every neighbour of (x,y,z) is an ordinary, unwrapped cell.

@@ -39,7 +39,16 @@ inline Geom<R> make_geom(const HostGeom &h, int64_t pitch)
     for (int i = 0; i < Q; ++i) g.L[i] = R(h.L[i]);
     for (int a = 0; a < 3; ++a) g.Fu[a] = R(h.Fu[a]);
     g.Ff = h.Ff;
+    for (int i = 0; i < Q; ++i) g.noff[i] = (int32_t)(cz(i) * g.plane + cy(i) * pitch + cx(i));
     return g;
+}
+
+template <class T>
+inline Dirs<T> make_dirs(T *base, int64_t slot)
+{
+    Dirs<T> d;
+    for (int i = 0; i < Q; ++i) d.p[i] = base + (size_t)i * slot;
+    return d;
 }
 
 template <class R>
@@ -130,6 +139,63 @@ __device__ __forceinline__ void push_store(const Geom<typename S::R> &g, typenam
     }
 }
 
+// ----- the same three access patterns on per-direction base pointers -----
+
+template <class S>
+__device__ __forceinline__ void load_natural_d(const Dirs<const typename S::T> &f, int c, typename S::R (&s)[Q])
+{
+    static_for<Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        s[i] = decode<S, i>(f.p[i][c]);
+    });
+}
+
+// A parity: f_k(x) in slot opp(k) of x - c_k, or (wall link) slot k of x.
+template <class S>
+__device__ __forceinline__ void load_aparity_d(const Geom<typename S::R> &g, const Dirs<const typename S::T> &f,
+                                               int x, int y, int z, int c, typename S::R (&s)[Q])
+{
+    if (interior(g, x, y, z)) {
+        static_for<Q>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            s[k] = decode<S, k>(f.p[opp(k)][c - g.noff[k]]);
+        });
+    } else {
+        const Faces fc = faces_of(g, x, y, z);
+        static_for<Q>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            if (fc.wall & face_mask(-cx(k), -cy(k), -cz(k))) s[k] = decode<S, k>(f.p[k][c]);
+            else s[k] = decode<S, k>(f.p[opp(k)][c + step_offset<-cx(k), -cy(k), -cz(k)>(g, fc)]);
+        });
+    }
+}
+
+// Two-lattice push: slot i of x + c_i, or slot opp(i) of x (+ lid term).
+template <class S>
+__device__ __forceinline__ void push_store_d(const Geom<typename S::R> &g, const Dirs<typename S::T> &dst, int x,
+                                             int y, int z, int c, const typename S::R (&s)[Q])
+{
+    if (interior(g, x, y, z)) {
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            dst.p[i][c + g.noff[i]] = encode<S, i>(s[i]);
+        });
+    } else {
+        const Faces fc = faces_of(g, x, y, z);
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            constexpr unsigned m = face_mask(cx(i), cy(i), cz(i));
+            if (fc.wall & m) {
+                typename S::R v = s[i];
+                if (fc.lid & m) v = radd(v, g.L[opp(i)]);
+                dst.p[opp(i)][c] = encode<S, opp(i)>(v);
+            } else {
+                dst.p[i][c + step_offset<cx(i), cy(i), cz(i)>(g, fc)] = encode<S, i>(s[i]);
+            }
+        });
+    }
+}
+
 // ---------------------------------------------------------------------------
 // K0: equilibrium initialisation (natural parity)
 // ---------------------------------------------------------------------------
@@ -169,49 +235,54 @@ __global__ void k_init_eq(Geom<typename S::R> g, typename S::T *__restrict__ f, 
 // K1: two-lattice fused collide-and-push (natural -> natural)
 // ---------------------------------------------------------------------------
 template <class S, bool FORCE>
-__global__ void __launch_bounds__(128) k_two_lattice(Geom<typename S::R> g, const typename S::T *__restrict__ src,
-                                                     typename S::T *__restrict__ dst)
+__global__ void __launch_bounds__(128) k_two_lattice(Geom<typename S::R> g, Dirs<const typename S::T> src,
+                                                     Dirs<typename S::T> dst)
 {
     using R = typename S::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     if (x >= g.nx) return;
+    const int c = cell32(g, x, y, z);
     R s[Q];
-    load_natural<S>(g, src, x, y, z, s);
+    load_natural_d<S>(src, c, s);
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
     bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
-    push_store<S>(g, dst, x, y, z, s);
+    push_store_d<S>(g, dst, x, y, z, c, s);
 }
 
 // ---------------------------------------------------------------------------
 // K2: AA even step (natural -> A parity), purely local: collide and write
-// f*_i into slot opp(i) of the same cell (the "revert" of Sec. 3).
+// f*_i into slot opp(i) of the same cell (the "revert" of Sec. 3).  Planes
+// z0 .. z0 + gridDim.z - 1.
 // ---------------------------------------------------------------------------
 template <class S, bool FORCE>
-__global__ void __launch_bounds__(128) k_aa_even(Geom<typename S::R> g, typename S::T *__restrict__ f)
+__global__ void __launch_bounds__(128) k_aa_even(Geom<typename S::R> g, Dirs<typename S::T> f, int z0)
 {
     using R = typename S::R;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z + z0;
     if (x >= g.nx) return;
-    const int64_t c = cell_of(g, x, y, z);
+    const int c = cell32(g, x, y, z);
     R s[Q];
-    load_natural<S>(g, f, x, y, z, s);
+    static_for<Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        s[i] = decode<S, i>(f.p[i][c]);
+    });
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
     bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
     if (interior(g, x, y, z)) {
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;
-            f[opp(i) * g.slot + c] = encode<S, opp(i)>(s[i]);
+            f.p[opp(i)][c] = encode<S, opp(i)>(s[i]);
         });
     } else {
+        const Faces fc = faces_of(g, x, y, z);
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;
-            int tx, ty, tz;
-            bool lid;
+            constexpr unsigned m = face_mask(cx(i), cy(i), cz(i));
             R v = s[i];
-            if (!link(g, x, y, z, cx(i), cy(i), cz(i), tx, ty, tz, lid) && lid) v = radd(v, g.L[opp(i)]);
-            f[opp(i) * g.slot + c] = encode<S, opp(i)>(v);
+            if ((fc.wall & m) && (fc.lid & m)) v = radd(v, g.L[opp(i)]);
+            f.p[opp(i)][c] = encode<S, opp(i)>(v);
         });
     }
 }
@@ -220,20 +291,23 @@ __global__ void __launch_bounds__(128) k_aa_even(Geom<typename S::R> g, typename
 // K3: AA odd step (A parity -> natural): gather the streamed values, collide,
 // scatter to the neighbours (the "swap_stream" of Sec. 3).  Cell x reads
 // (x - c_k, opp(k)) and writes (x + c_i, i); no other cell touches those
-// locations in this sweep, so the update is race-free in place.
+// locations in this sweep, so the update is race-free in place.  Planes
+// z0 .. z0 + gridDim.z - 1.
 // ---------------------------------------------------------------------------
 template <class S, bool FORCE>
-__global__ void __launch_bounds__(128) k_aa_odd(Geom<typename S::R> g, typename S::T *__restrict__ f)
+__global__ void __launch_bounds__(128) k_aa_odd(Geom<typename S::R> g, Dirs<typename S::T> f, int z0)
 {
     using R = typename S::R;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    using T = typename S::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z + z0;
     if (x >= g.nx) return;
+    const int c = cell32(g, x, y, z);
     R s[Q];
-    load_aparity<S>(g, f, x, y, z, s);
+    load_aparity_d<S>(g, reinterpret_cast<const Dirs<const T> &>(f), x, y, z, c, s);
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
     bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
-    push_store<S>(g, f, x, y, z, s);
+    push_store_d<S>(g, f, x, y, z, c, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -4,6 +4,7 @@
 
 #include "kernels.cuh"
 #include "merged.cuh"
+#include "wavefront.cuh"
 
 #include <string.h>
 
@@ -24,24 +25,45 @@ struct Launch {
         k_init_eq<S><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (T *)f, rho, u, dtype);
         return cudaGetLastError();
     }
+    static int64_t slot_of(const HostGeom &h, int64_t pitch) { return pitch * h.ny * h.nz; }
     static cudaError_t two_lattice(const HostGeom &h, int64_t pitch, bool force, const void *src, void *dst,
                                    cudaStream_t st)
     {
-        if (force) k_two_lattice<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (const T *)src, (T *)dst);
-        else k_two_lattice<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (const T *)src, (T *)dst);
+        const Geom<R> g = make_geom<R>(h, pitch);
+        const Dirs<const T> a = make_dirs((const T *)src, slot_of(h, pitch));
+        const Dirs<T> b = make_dirs((T *)dst, slot_of(h, pitch));
+        if (force) k_two_lattice<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b);
+        else k_two_lattice<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b);
+        return cudaGetLastError();
+    }
+    // planes [z0, z1) only
+    static cudaError_t aa_even_range(const HostGeom &h, int64_t pitch, bool force, void *f, int z0, int z1,
+                                     cudaStream_t st)
+    {
+        const Geom<R> g = make_geom<R>(h, pitch);
+        const Dirs<T> d = make_dirs((T *)f, slot_of(h, pitch));
+        const dim3 grid((h.nx + CELL_BLOCK - 1) / CELL_BLOCK, h.ny, z1 - z0);
+        if (force) k_aa_even<S, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+        else k_aa_even<S, false><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+        return cudaGetLastError();
+    }
+    static cudaError_t aa_odd_range(const HostGeom &h, int64_t pitch, bool force, void *f, int z0, int z1,
+                                    cudaStream_t st)
+    {
+        const Geom<R> g = make_geom<R>(h, pitch);
+        const Dirs<T> d = make_dirs((T *)f, slot_of(h, pitch));
+        const dim3 grid((h.nx + CELL_BLOCK - 1) / CELL_BLOCK, h.ny, z1 - z0);
+        if (force) k_aa_odd<S, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+        else k_aa_odd<S, false><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
         return cudaGetLastError();
     }
     static cudaError_t aa_even(const HostGeom &h, int64_t pitch, bool force, void *f, cudaStream_t st)
     {
-        if (force) k_aa_even<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (T *)f);
-        else k_aa_even<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (T *)f);
-        return cudaGetLastError();
+        return aa_even_range(h, pitch, force, f, 0, h.nz, st);
     }
     static cudaError_t aa_odd(const HostGeom &h, int64_t pitch, bool force, void *f, cudaStream_t st)
     {
-        if (force) k_aa_odd<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (T *)f);
-        else k_aa_odd<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(make_geom<R>(h, pitch), (T *)f);
-        return cudaGetLastError();
+        return aa_odd_range(h, pitch, force, f, 0, h.nz, st);
     }
     static cudaError_t moments(const HostGeom &h, int64_t pitch, bool force, int parity, const void *f, void *rho,
                                void *u, int dtype, cudaStream_t st)
@@ -127,17 +149,18 @@ struct Launch {
         const size_t smem = MergedSmem<TX, TY, T, R>::bytes;
         const dim3 grid(ti.ntx, ti.nty), block(TX, TY);
         const Geom<R> g = make_geom<R>(h, pitch);
+        const Dirs<T> fd = make_dirs((T *)f, slot_of(h, pitch));
         CUtensorMap map;
         memcpy(&map, tmap, sizeof(map));
         cudaError_t e;
         if (force) {
             e = cudaFuncSetAttribute(k_merged<S, true, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            k_merged<S, true, TX, TY><<<grid, block, smem, st>>>(map, g, (T *)f, (const R *)G, ti, status);
+            k_merged<S, true, TX, TY><<<grid, block, smem, st>>>(map, g, fd, (const R *)G, ti, status);
         } else {
             e = cudaFuncSetAttribute(k_merged<S, false, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            k_merged<S, false, TX, TY><<<grid, block, smem, st>>>(map, g, (T *)f, (const R *)G, ti, status);
+            k_merged<S, false, TX, TY><<<grid, block, smem, st>>>(map, g, fd, (const R *)G, ti, status);
         }
         return cudaGetLastError();
     }
@@ -157,6 +180,25 @@ struct Launch {
             else return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
         }
+    }
+    static cudaError_t wavefront(const HostGeom &h, int64_t pitch, bool force, void *f, const void *sched, int grid,
+                                 cudaStream_t st)
+    {
+        const Geom<R> g = make_geom<R>(h, pitch);
+        const Dirs<T> d = make_dirs((T *)f, slot_of(h, pitch));
+        WaveSchedule ws;
+        memcpy(&ws, sched, sizeof(ws));
+        if (force) k_wavefront<S, true><<<grid, WF_THREADS, 0, st>>>(g, d, ws);
+        else k_wavefront<S, false><<<grid, WF_THREADS, 0, st>>>(g, d, ws);
+        return cudaGetLastError();
+    }
+    static int wavefront_blocks_per_sm(bool force)
+    {
+        int n = 0;
+        const cudaError_t e = force
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_wavefront<S, true>, WF_THREADS, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_wavefront<S, false>, WF_THREADS, 0);
+        return e == cudaSuccess ? n : 0;
     }
     static cudaError_t adjoint(const HostGeom &h, int64_t pitch, bool force, const void *f, const void *lam_in,
                                void *lam_out, double *gF, cudaStream_t st)
@@ -197,10 +239,14 @@ StorageOps make_ops()
     o.real_size = sizeof(typename S::R);
     o.max_tile_y = L::merged_smem(16) ? 16 : (L::merged_smem(8) ? 8 : 4);
     o.merged_smem = &L::merged_smem;
+    o.wavefront = &L::wavefront;
+    o.wavefront_blocks_per_sm = &L::wavefront_blocks_per_sm;
     o.init_eq = &L::init_eq;
     o.two_lattice = &L::two_lattice;
     o.aa_even = &L::aa_even;
     o.aa_odd = &L::aa_odd;
+    o.aa_even_range = &L::aa_even_range;
+    o.aa_odd_range = &L::aa_odd_range;
     o.moments = &L::moments;
     o.export_pop = &L::export_pop;
     o.import_pop = &L::import_pop;

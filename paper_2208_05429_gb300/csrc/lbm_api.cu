@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -12,6 +13,7 @@
 #include "d3q19.cuh"
 #include "lbm.h"
 #include "ops.h"
+#include "wavefront.cuh"
 
 using namespace lbm;
 
@@ -31,7 +33,9 @@ struct lbm_handle {
     void *G;       // shell snapshot (MERGED)
     TileInfo ti;
     CUtensorMap tmap;  // TMA descriptor of f (MERGED)
-    int *status;       // device status word: bit 2 = a bounded wait gave up
+    int *status;       // device status word: bits 2 / 4 = a bounded wait gave up
+    int *wf_words;     // WAVEFRONT schedule (device): entries, ticket, done flags
+    int wf_nentries, wf_rb, wf_nrb, wf_grid, wf_ahead;
     double *partial;
     double *red_out;
     int *flag;
@@ -113,8 +117,41 @@ int64_t ghost_elems(const lbm_config &c)
 }
 
 struct Layout {
-    size_t f, f2, G, partial, red_out, flag, status, total;
+    size_t f, f2, G, wf, partial, red_out, flag, status, total;
 };
+
+// WAVEFRONT schedule words: entries (2 nz + 4), ticket, done[nz * ny] (at
+// most ny row blocks per plane).
+constexpr int WF_AHEAD_DEFAULT = 4;  // planes by which even steps lead odd steps
+
+int64_t wf_ints(const lbm_config &c)
+{
+    return c.variant == LBM_VARIANT_WAVEFRONT ? 2 * c.nz + 4 + 1 + c.nz * c.ny : 0;
+}
+
+// Order of the even (2p) and odd (2p+1) steps of the planes for a lookahead
+// of `ahead` planes.
+int wf_entries(const lbm_config &c, int ahead, int *out)
+{
+    const int nz = (int)c.nz;
+    int n = 0;
+    bool *issued = new (std::nothrow) bool[nz]();
+    if (!issued) return -1;
+    auto even = [&](int p) {
+        if (p >= 0 && p < nz && !issued[p]) {
+            issued[p] = true;
+            out[n++] = 2 * p;
+        }
+    };
+    if (c.face_bc[4] == LBM_BC_PERIODIC) even(nz - 1);
+    for (int p = 0; p <= ahead; ++p) even(p);
+    for (int q = 0; q < nz; ++q) {
+        even(q + ahead + 1);
+        out[n++] = 2 * q + 1;
+    }
+    delete[] issued;
+    return n;
+}
 
 Layout layout_of(const lbm_config &c)
 {
@@ -125,6 +162,7 @@ Layout layout_of(const lbm_config &c)
     L.f = off; off += pop;
     L.f2 = off; if (c.variant == LBM_VARIANT_TWO_LATTICE) off += pop;
     L.G = off; off += align_up((size_t)ghost_elems(c) * real_size_of(c.storage));
+    L.wf = off; off += align_up((size_t)wf_ints(c) * sizeof(int));
     L.partial = off; off += align_up(sizeof(double) * 5 * RED_BLOCKS_MAX);
     L.red_out = off; off += align_up(sizeof(double) * 5);
     L.flag = off; off += align_up(sizeof(int));
@@ -276,7 +314,8 @@ int lbm_validate(const lbm_config *c)
     if (!(ul < 0.3)) return LBM_EINVAL;
     if (!(c->rho_wall > 0.0) || !isfinite(c->rho_wall)) return LBM_EINVAL;
     if (c->storage < LBM_STORAGE_F64 || c->storage > LBM_STORAGE_BF16S) return LBM_EINVAL;
-    if (c->variant < LBM_VARIANT_TWO_LATTICE || c->variant > LBM_VARIANT_MERGED) return LBM_EINVAL;
+    if (c->variant < LBM_VARIANT_TWO_LATTICE || c->variant > LBM_VARIANT_WAVEFRONT) return LBM_EINVAL;
+    if ((double)((c->nx + 15) / 16 * 16) * (double)c->ny * (double)c->nz > 2147483647.0) return LBM_EINVAL;
     if (c->force_mode < LBM_FORCE_NONE || c->force_mode > LBM_FORCE_FIELD) return LBM_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (!isfinite(c->force_uniform[a])) return LBM_EINVAL;
@@ -292,6 +331,38 @@ int lbm_required_bytes(const lbm_config *cfg, size_t *bytes)
     if (v != LBM_OK) return v;
     if (!bytes) return LBM_EINVAL;
     *bytes = layout_of(*cfg).total;
+    return LBM_OK;
+}
+
+// Schedule of the WAVEFRONT sweep: entry order for the lookahead, row blocks
+// of about 4096 cells, one CTA per resident slot on the device.
+static int wf_setup(lbm_handle *h, int ahead)
+{
+    const lbm_config &c = h->cfg;
+    int *ent = new (std::nothrow) int[2 * c.nz + 4];
+    if (!ent) return LBM_ENOMEM;
+    const int n = wf_entries(c, ahead, ent);
+    if (n < 0) { delete[] ent; return LBM_ENOMEM; }
+    const cudaError_t e = cudaMemcpyAsync(h->wf_words, ent, sizeof(int) * n, cudaMemcpyHostToDevice, h->stream);
+    const cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    delete[] ent;
+    if (e != cudaSuccess || e2 != cudaSuccess) return LBM_ECUDA;
+    h->wf_nentries = n;
+    h->wf_ahead = ahead;
+    int64_t item_cells = 4096;  // tunable through LBM_WAVEFRONT_ITEM_CELLS
+    if (const char *env = getenv("LBM_WAVEFRONT_ITEM_CELLS")) {
+        const long v = atol(env);
+        if (v >= 32 && v <= (1L << 22)) item_cells = v;
+    }
+    const int64_t want = item_cells / c.nx;
+    h->wf_rb = (int)(want < 1 ? 1 : (want > c.ny ? c.ny : want));
+    h->wf_nrb = (int)((c.ny + h->wf_rb - 1) / h->wf_rb);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) return LBM_ECUDA;
+    const int per = h->ops->wavefront_blocks_per_sm(h->force);
+    if (per <= 0) return LBM_ECUDA;
+    const int64_t items = (int64_t)n * h->wf_nrb;
+    h->wf_grid = (int)(items < (int64_t)sms * per ? items : (int64_t)sms * per);
     return LBM_OK;
 }
 
@@ -340,6 +411,7 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
     h->red_out = (double *)(b + L.red_out);
     h->flag = (int *)(b + L.flag);
     h->status = (int *)(b + L.status);
+    h->wf_words = cfg->variant == LBM_VARIANT_WAVEFRONT ? (int *)(b + L.wf) : nullptr;
     const int64_t n = cfg->nx * cfg->ny * cfg->nz;
     int64_t nb = (n + 255) / 256;
     h->red_blocks = (int)(nb < RED_BLOCKS_MAX ? nb : RED_BLOCKS_MAX);
@@ -350,6 +422,22 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
         delete h->rec_kind;
         delete h;
         return LBM_ECUDA;
+    }
+    if (cfg->variant == LBM_VARIANT_WAVEFRONT) {
+        // lookahead (planes) of the even steps, tunable through LBM_WAVEFRONT_AHEAD
+        int ahead = WF_AHEAD_DEFAULT;
+        if (const char *env = getenv("LBM_WAVEFRONT_AHEAD")) {
+            const int v = atoi(env);
+            if (v >= 1 && v <= 64) ahead = v;
+        }
+        const int rc = wf_setup(h, ahead);
+        if (rc != LBM_OK) {
+            if (own) cudaFree(buf);
+            delete h->ev_pool;
+            delete h->rec_kind;
+            delete h;
+            return rc;
+        }
     }
     *out = h;
     return LBM_OK;
@@ -449,6 +537,31 @@ int lbm_step(lbm_handle *h, int64_t n)
                 h->parity = PARITY_NATURAL;
             }
             n -= 1; h->t += 1;
+            break;
+        case LBM_VARIANT_WAVEFRONT:
+            if (h->parity == PARITY_A) {
+                CK(timed(h, LBM_KERNEL_AA_ODD, [&] { return o.aa_odd(h->hg, h->nxp, h->force, h->f, h->stream); }));
+                h->parity = PARITY_NATURAL;
+                n -= 1; h->t += 1;
+            } else if (n >= 2) {
+                WaveSchedule ws;
+                ws.entries = h->wf_words;
+                ws.nentries = h->wf_nentries;
+                ws.rb = h->wf_rb;
+                ws.nrb = h->wf_nrb;
+                ws.ticket = h->wf_words + 2 * h->cfg.nz + 4;
+                ws.done = ws.ticket + 1;
+                ws.status = h->status;
+                CK(cudaMemsetAsync(ws.ticket, 0, sizeof(int) * (1 + h->cfg.nz * h->wf_nrb), h->stream));
+                CK(timed(h, LBM_KERNEL_WAVEFRONT, [&] {
+                    return o.wavefront(h->hg, h->nxp, h->force, h->f, &ws, h->wf_grid, h->stream);
+                }));
+                n -= 2; h->t += 2;
+            } else {
+                CK(timed(h, LBM_KERNEL_AA_EVEN, [&] { return o.aa_even(h->hg, h->nxp, h->force, h->f, h->stream); }));
+                h->parity = PARITY_A;
+                n -= 1; h->t += 1;
+            }
             break;
         default:  // MERGED
             if (h->parity == PARITY_A) {

@@ -229,7 +229,7 @@ struct MergedCta {
 
     const CUtensorMap *tmap;
     const Geom<R> &g;
-    T *__restrict__ f;
+    const Dirs<T> &fd;
     const R *__restrict__ G;
     const TileInfo &ti;
     T *stage;
@@ -240,9 +240,9 @@ struct MergedCta {
         dupy, edge, timed_out;
     R rest_c, rest_n, zp1, zp0, zp_n, zm_prev, zm_n;  // rest and pure-z populations carried in registers
 
-    __device__ __forceinline__ MergedCta(const CUtensorMap *tmap_, const Geom<R> &g_, T *f_, const R *G_,
+    __device__ __forceinline__ MergedCta(const CUtensorMap *tmap_, const Geom<R> &g_, const Dirs<T> &fd_, const R *G_,
                                          const TileInfo &ti_, unsigned char *smem)
-        : tmap(tmap_), g(g_), f(f_), G(G_), ti(ti_)
+        : tmap(tmap_), g(g_), fd(fd_), G(G_), ti(ti_)
     {
         stage = reinterpret_cast<T *>(smem + L::stage_off);
         ringm = reinterpret_cast<R *>(smem + L::ringm_off);
@@ -465,7 +465,7 @@ struct MergedCta {
         R Fx, Fy, Fz;
         force_at<R, FORCE>(g, canon(g, x, y, k), ncanon(g), Fx, Fy, Fz);
         bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
-        push_store<S>(g, f, x, y, k, s);
+        push_store_d<S>(g, fd, x, y, k, cell32(g, x, y, k), s);
     }
 
     __device__ __forceinline__ void rotate()
@@ -479,14 +479,14 @@ struct MergedCta {
 
 template <class S, bool FORCE, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY, 1) k_merged(const __grid_constant__ CUtensorMap tmap,
-                                                       Geom<typename S::R> g, typename S::T *__restrict__ f,
+                                                       Geom<typename S::R> g, Dirs<typename S::T> fd,
                                                        const typename S::R *__restrict__ G, TileInfo ti,
                                                        int *__restrict__ status)
 {
     using C = MergedCta<S, FORCE, TX, TY>;
     extern __shared__ __align__(128) unsigned char smem[];
     int *abort_flag = reinterpret_cast<int *>(smem + C::L::flag_off);
-    C c(&tmap, g, f, G, ti, smem);
+    C c(&tmap, g, fd, G, ti, smem);
     const int nz = g.nz;
 
     if (c.tid == 0) {

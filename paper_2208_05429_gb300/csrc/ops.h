@@ -43,6 +43,9 @@ struct StorageOps {
                                cudaStream_t);
     cudaError_t (*aa_even)(const HostGeom &, int64_t pitch, bool force, void *f, cudaStream_t);
     cudaError_t (*aa_odd)(const HostGeom &, int64_t pitch, bool force, void *f, cudaStream_t);
+    // the same on planes [z0, z1) only
+    cudaError_t (*aa_even_range)(const HostGeom &, int64_t pitch, bool force, void *f, int z0, int z1, cudaStream_t);
+    cudaError_t (*aa_odd_range)(const HostGeom &, int64_t pitch, bool force, void *f, int z0, int z1, cudaStream_t);
     cudaError_t (*moments)(const HostGeom &, int64_t pitch, bool force, int parity, const void *f, void *rho,
                            void *u, int dtype, cudaStream_t);
     cudaError_t (*export_pop)(const HostGeom &, int64_t pitch, int parity, const void *f, void *out, int dtype,
@@ -59,6 +62,11 @@ struct StorageOps {
     cudaError_t (*merged)(const HostGeom &, int64_t pitch, bool force, void *f, const void *G, const TileInfo &,
                           const void *tmap, int *status, cudaStream_t);
     size_t (*merged_smem)(int tile_y);  // dynamic shared memory of the merged kernel (0 = not built)
+    // persistent plane-wavefront sweep (two time steps); sched points to a
+    // WaveSchedule (device pointers inside), grid = number of CTAs
+    cudaError_t (*wavefront)(const HostGeom &, int64_t pitch, bool force, void *f, const void *sched, int grid,
+                             cudaStream_t);
+    int (*wavefront_blocks_per_sm)(bool force);
     // lam_* are arrays of the compute type with the given pitch
     cudaError_t (*adjoint)(const HostGeom &, int64_t pitch, bool force, const void *f, const void *lam_in,
                            void *lam_out, double *gF, cudaStream_t);

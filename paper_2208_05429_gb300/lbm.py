@@ -24,16 +24,18 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ESTATE, LBM_ENONFINITE, LBM_ETIME
     0, -1, -2, -3, -4, -5, -6, -7
 LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_LID = 0, 1, 2
 LBM_STORAGE_F64, LBM_STORAGE_F32, LBM_STORAGE_F32S, LBM_STORAGE_F16S, LBM_STORAGE_BF16S = 0, 1, 2, 3, 4
-LBM_VARIANT_TWO_LATTICE, LBM_VARIANT_AA, LBM_VARIANT_MERGED = 0, 1, 2
+LBM_VARIANT_TWO_LATTICE, LBM_VARIANT_AA, LBM_VARIANT_MERGED, LBM_VARIANT_WAVEFRONT = 0, 1, 2, 3
 LBM_FORCE_NONE, LBM_FORCE_UNIFORM, LBM_FORCE_FIELD = 0, 1, 2
 LBM_DTYPE_F32, LBM_DTYPE_F64 = 0, 1
-LBM_KERNEL_TWO_LATTICE, LBM_KERNEL_AA_EVEN, LBM_KERNEL_AA_ODD, LBM_KERNEL_SNAPSHOT, LBM_KERNEL_MERGED = 0, 1, 2, 3, 4
+LBM_KERNEL_TWO_LATTICE, LBM_KERNEL_AA_EVEN, LBM_KERNEL_AA_ODD, LBM_KERNEL_SNAPSHOT, LBM_KERNEL_MERGED, \
+    LBM_KERNEL_WAVEFRONT = 0, 1, 2, 3, 4, 5
 KERNELS = {"two_lattice": LBM_KERNEL_TWO_LATTICE, "aa_even": LBM_KERNEL_AA_EVEN, "aa_odd": LBM_KERNEL_AA_ODD,
-           "snapshot": LBM_KERNEL_SNAPSHOT, "merged": LBM_KERNEL_MERGED}
+           "snapshot": LBM_KERNEL_SNAPSHOT, "merged": LBM_KERNEL_MERGED, "wavefront": LBM_KERNEL_WAVEFRONT}
 
 STORAGE = {"f64": LBM_STORAGE_F64, "f32": LBM_STORAGE_F32, "f32s": LBM_STORAGE_F32S,
            "f16s": LBM_STORAGE_F16S, "bf16s": LBM_STORAGE_BF16S}
-VARIANT = {"two_lattice": LBM_VARIANT_TWO_LATTICE, "aa": LBM_VARIANT_AA, "merged": LBM_VARIANT_MERGED}
+VARIANT = {"two_lattice": LBM_VARIANT_TWO_LATTICE, "aa": LBM_VARIANT_AA, "merged": LBM_VARIANT_MERGED,
+           "wavefront": LBM_VARIANT_WAVEFRONT}
 BC = {"periodic": LBM_BC_PERIODIC, "wall": LBM_BC_WALL, "lid": LBM_BC_LID}
 
 _PKG = os.path.dirname(os.path.abspath(__file__))

@@ -38,7 +38,7 @@ def test_default_config_valid(cuda_lib):
 
 @pytest.mark.parametrize("field,value", [
     ("nx", 0), ("ny", -3), ("nz", 70000), ("tau", 0.5), ("tau", float("nan")), ("rho_wall", 0.0),
-    ("storage", 9), ("variant", 3), ("force_mode", 5), ("tile_x", 16), ("tile_y", 5),
+    ("storage", 9), ("variant", 4), ("force_mode", 5), ("tile_x", 16), ("tile_y", 5),
 ])
 def test_invalid_configs_rejected(cuda_lib, field, value):
     cfg = lbm.lbm_config_default()

@@ -17,7 +17,7 @@ from helpers import relmax
 pytestmark = pytest.mark.gpu
 
 CASES = cases()
-VARIANTS = ["two_lattice", "aa", "merged"]
+VARIANTS = ["two_lattice", "aa", "merged", "wavefront"]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -99,15 +99,16 @@ def test_reduce_flags_nonfinite(gpu):
     assert np.all(np.isfinite(lat2.reduce()))
 
 
-def test_sampled_step_at_bench_size(gpu):
-    """256^3 cavity (the benchmark workload, FP32, MERGED, default tiles):
+@pytest.mark.parametrize("variant", ["merged", "wavefront"])
+def test_sampled_step_at_bench_size(gpu, variant):
+    """256^3 cavity (the benchmark workload, FP32, default launch shapes):
     after 20 steps, one more GPU step is checked on 400 sampled cells against
     the oracle stepping those cells alone from the GPU's own state."""
     import torch
     from paper_2208_05429_gb300 import inputs
     n = 256
     cfg = oracle.cavity(n, 0.55)
-    lat = make_gpu(cfg, "f32", "merged")
+    lat = make_gpu(cfg, "f32", variant)
     lat.init_equilibrium()
     lat.step(20)
     f20 = gpu_state(lat)                       # oracle order, float64
@@ -124,11 +125,12 @@ def test_sampled_step_at_bench_size(gpu):
     del f20
 
 
-def test_mass_conservation_bench_size(gpu):
+@pytest.mark.parametrize("variant", ["merged", "wavefront"])
+def test_mass_conservation_bench_size(gpu, variant):
     """Exact mass conservation of the cavity holds at 256^3 (FP64 sums of an
     FP32 lattice: drift only from storage rounding)."""
     cfg = oracle.cavity(256, 0.55)
-    lat = make_gpu(cfg, "f32s", "merged")
+    lat = make_gpu(cfg, "f32s", variant)
     lat.init_equilibrium()
     m0 = lat.reduce()[0]
     lat.step(100)

@@ -27,7 +27,7 @@ def test_schedules_bitwise_equal(gpu, storage, name, nsteps):
     f0 = start_state(cfg, seed=3)
     ref = None
     tiles = [(32, 4)] + ([] if storage == "f64" else [(32, 8), (32, 16)])
-    runs = [("two_lattice", (0, 0)), ("aa", (0, 0))] + [("merged", t) for t in tiles]
+    runs = [("two_lattice", (0, 0)), ("aa", (0, 0)), ("wavefront", (0, 0))] + [("merged", t) for t in tiles]
     for variant, tile in runs:
         lat = make_gpu(cfg, storage, variant, tile=tile)
         load_state(lat, f0)
@@ -59,11 +59,15 @@ def test_mixed_step_sequences(gpu, storage):
     load_state(t, f0)
     for _ in range(9):
         t.step(1)
-    assert m.time == a.time == t.time == 9
-    ra, rm, rt = _raw(a), _raw(m), _raw(t)
-    assert torch.equal(ra, rm) and torch.equal(ra, rt)
+    w = make_gpu(cfg, storage, "wavefront")
+    load_state(w, f0)
+    for k in (2, 1, 4, 2):
+        w.step(k)
+    assert m.time == a.time == t.time == w.time == 9
+    ra, rm, rt, rw = _raw(a), _raw(m), _raw(t), _raw(w)
+    assert torch.equal(ra, rm) and torch.equal(ra, rt) and torch.equal(ra, rw)
     # moments agree at both parities (a is at the odd parity after 9 steps)
-    for lat in (a, m, t):
+    for lat in (a, m, t, w):
         rho, u = lat.moments(torch.float64)
         r0, u0 = a.moments(torch.float64)
         assert torch.equal(rho, r0) and torch.equal(u, u0)
