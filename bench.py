@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--size", type=int, default=256)
     p.add_argument("--storage", default="f32", choices=sorted(ELEM))
-    p.add_argument("--variant", default="merged", choices=["merged", "wavefront", "aa", "two_lattice"])
+    p.add_argument("--variant", default="aa", choices=["merged", "wavefront", "aa", "two_lattice"])
     p.add_argument("--tile-y", type=int, default=0)
     p.add_argument("--no-extras", action="store_true", help="skip the per-variant, adjoint and CPU legs")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle baseline")
@@ -270,7 +270,7 @@ def adjoint_leg():
     NX, NY, NZ, T, K = 128, 64, 64, 200, 20
     F = torch.tensor(inputs.channel_force(NX, NY, NZ), device="cuda")
     bc = ("periodic", "periodic", "wall", "wall", "wall", "wall")
-    lat = Lattice((NX, NY, NZ), 0.6, bc=bc, storage="f32", variant="merged", force=F)
+    lat = Lattice((NX, NY, NZ), 0.6, bc=bc, storage="f32", variant="aa", force=F)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     st = lat.stream
     res = {}

@@ -4,6 +4,7 @@
 
 #include "kernels.cuh"
 #include "merged.cuh"
+#include "merged3.cuh"
 #include "wavefront.cuh"
 
 #include <string.h>
@@ -181,6 +182,36 @@ struct Launch {
         default: return cudaErrorInvalidValue;
         }
     }
+    // band height of the shadow-shell sweep: 32 x 14 tiles (one per SM on a
+    // 256^2 plane) for 4-byte and 2-byte storage, 32 x 6 for FP64 (registers)
+    static constexpr int M3_TY = sizeof(R) == 8 ? 6 : 14;
+    static cudaError_t shell_gather(const HostGeom &h, int64_t pitch, const void *f, void *G, const ShellInfo &si,
+                                    cudaStream_t st)
+    {
+        const int64_t tot = (int64_t)si.ntx * si.nty * M3<M3_TY>::NSP * h.nz;
+        const unsigned blocks = (unsigned)((tot + 255) / 256);
+        k_shell_gather<S, M3_TY><<<blocks, 256, 0, st>>>(make_geom<R>(h, pitch),
+                                                         make_dirs((const T *)f, slot_of(h, pitch)), (T *)G, si);
+        return cudaGetLastError();
+    }
+    template <bool F>
+    static cudaError_t merged3_f(const HostGeom &h, int64_t pitch, void *f, const void *Gc, void *Gn,
+                                 const ShellInfo &si, cudaStream_t st)
+    {
+        using L3 = M3<M3_TY>;
+        constexpr size_t smem = L3::template smem<R>();
+        cudaError_t e = cudaFuncSetAttribute(k_merged3<S, F, M3_TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        k_merged3<S, F, M3_TY><<<dim3(si.ntx, si.nty), L3::THREADS, smem, st>>>(
+            make_geom<R>(h, pitch), make_dirs((T *)f, slot_of(h, pitch)), (const T *)Gc, (T *)Gn, si);
+        return cudaGetLastError();
+    }
+    static cudaError_t merged3(const HostGeom &h, int64_t pitch, bool force, void *f, const void *Gc, void *Gn,
+                               const ShellInfo &si, cudaStream_t st)
+    {
+        return force ? merged3_f<true>(h, pitch, f, Gc, Gn, si, st) : merged3_f<false>(h, pitch, f, Gc, Gn, si, st);
+    }
     static cudaError_t wavefront(const HostGeom &h, int64_t pitch, bool force, void *f, const void *sched, int grid,
                                  cudaStream_t st)
     {
@@ -254,6 +285,10 @@ StorageOps make_ops()
     o.reduce = &L::reduce;
     o.snapshot = &L::snapshot;
     o.merged = &L::merged;
+    o.m3_ty = L::M3_TY;
+    o.m3_nsp = M3<L::M3_TY>::NSP;
+    o.shell_gather = &L::shell_gather;
+    o.merged3 = &L::merged3;
     o.adjoint = &L::adjoint;
     o.adjoint_seed = &L::adjoint_seed;
     o.canon_to_pitched = &L::canon_to_pitched;

@@ -30,8 +30,13 @@ struct lbm_handle {
     size_t bytes;
     void *f;       // populations
     void *f2;      // second lattice (TWO_LATTICE)
-    void *G;       // shell snapshot (MERGED)
+    void *G;       // shell snapshot (MERGED with explicit tile or periodic z)
     TileInfo ti;
+    bool m3;           // MERGED runs the shadow-shell sweep
+    ShellInfo si;
+    void *G3[2];       // shadow of the tile shells: current / next
+    int g3cur;
+    bool g3fresh;      // G3[g3cur] mirrors the shell cells of f
     CUtensorMap tmap;  // TMA descriptor of f (MERGED)
     int *status;       // device status word: bits 2 / 4 = a bounded wait gave up
     int *wf_words;     // WAVEFRONT schedule (device): entries, ticket, done flags
@@ -109,15 +114,36 @@ TileInfo tile_info(const lbm_config &c)
     return ti;
 }
 
+// The shadow-shell sweep serves MERGED with automatic tiles when z is not
+// periodic; an explicit tile height or a periodic z selects the snapshot
+// sweep (merged.cuh).
+bool uses_m3(const lbm_config &c)
+{
+    return c.variant == LBM_VARIANT_MERGED && c.tile_y == 0 && c.face_bc[4] != LBM_BC_PERIODIC;
+}
+
+ShellInfo shell_info(const lbm_config &c)
+{
+    ShellInfo si;
+    memset(&si, 0, sizeof(si));
+    const StorageOps *o = ops_for(c.storage);
+    si.ntx = (int)((c.nx + 31) / 32);
+    si.nty = (int)((c.ny + o->m3_ty - 1) / o->m3_ty);
+    si.hb = (int)(c.ny / si.nty);
+    si.rem = (int)(c.ny % si.nty);
+    si.gplane = (int64_t)si.ntx * si.nty * Q * o->m3_nsp;
+    return si;
+}
+
 int64_t ghost_elems(const lbm_config &c)
 {
-    if (c.variant != LBM_VARIANT_MERGED) return 0;
+    if (c.variant != LBM_VARIANT_MERGED || uses_m3(c)) return 0;
     const TileInfo ti = tile_info(c);
     return (int64_t)Q * (ti.gy_slot + ti.gx_slot + ti.gz_slot);
 }
 
 struct Layout {
-    size_t f, f2, G, wf, partial, red_out, flag, status, total;
+    size_t f, f2, G, G3, wf, partial, red_out, flag, status, total;
 };
 
 // WAVEFRONT schedule words: entries (2 nz + 4), ticket, done[nz * ny] (at
@@ -162,6 +188,8 @@ Layout layout_of(const lbm_config &c)
     L.f = off; off += pop;
     L.f2 = off; if (c.variant == LBM_VARIANT_TWO_LATTICE) off += pop;
     L.G = off; off += align_up((size_t)ghost_elems(c) * real_size_of(c.storage));
+    L.G3 = off;
+    if (uses_m3(c)) off += 2 * align_up((size_t)(shell_info(c).gplane * c.nz) * es);
     L.wf = off; off += align_up((size_t)wf_ints(c) * sizeof(int));
     L.partial = off; off += align_up(sizeof(double) * 5 * RED_BLOCKS_MAX);
     L.red_out = off; off += align_up(sizeof(double) * 5);
@@ -407,6 +435,15 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
     h->f = b + L.f;
     h->f2 = cfg->variant == LBM_VARIANT_TWO_LATTICE ? b + L.f2 : nullptr;
     h->G = cfg->variant == LBM_VARIANT_MERGED ? b + L.G : nullptr;
+    h->m3 = uses_m3(*cfg);
+    if (h->m3) {
+        h->si = shell_info(*cfg);
+        const size_t gbytes = align_up((size_t)(h->si.gplane * cfg->nz) * elem_size_of(cfg->storage));
+        h->G3[0] = b + L.G3;
+        h->G3[1] = b + L.G3 + gbytes;
+    }
+    h->g3cur = 0;
+    h->g3fresh = false;
     h->partial = (double *)(b + L.partial);
     h->red_out = (double *)(b + L.red_out);
     h->flag = (int *)(b + L.flag);
@@ -415,7 +452,7 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
     const int64_t n = cfg->nx * cfg->ny * cfg->nz;
     int64_t nb = (n + 255) / 256;
     h->red_blocks = (int)(nb < RED_BLOCKS_MAX ? nb : RED_BLOCKS_MAX);
-    if ((cfg->variant == LBM_VARIANT_MERGED && !make_tmap(*cfg, h->ti, h->f, &h->tmap)) ||
+    if ((cfg->variant == LBM_VARIANT_MERGED && !h->m3 && !make_tmap(*cfg, h->ti, h->f, &h->tmap)) ||
         cudaMemsetAsync(buf, 0, L.total, h->stream) != cudaSuccess) {
         if (own) cudaFree(buf);
         delete h->ev_pool;
@@ -499,6 +536,7 @@ int lbm_init_equilibrium(lbm_handle *h, const void *rho, const void *u, int32_t 
     if (!g.ok) return LBM_ECUDA;
     CK(h->ops->init_eq(h->hg, h->nxp, h->f, rho, u, dtype, h->stream));
     h->parity = PARITY_NATURAL;
+    h->g3fresh = false;
     h->t = 0;
     h->adj_ready = false;
     return LBM_OK;
@@ -532,9 +570,11 @@ int lbm_step(lbm_handle *h, int64_t n)
             if (h->parity == PARITY_NATURAL) {
                 CK(timed(h, LBM_KERNEL_AA_EVEN, [&] { return o.aa_even(h->hg, h->nxp, h->force, h->f, h->stream); }));
                 h->parity = PARITY_A;
+                h->g3fresh = false;
             } else {
                 CK(timed(h, LBM_KERNEL_AA_ODD, [&] { return o.aa_odd(h->hg, h->nxp, h->force, h->f, h->stream); }));
                 h->parity = PARITY_NATURAL;
+                h->g3fresh = false;
             }
             n -= 1; h->t += 1;
             break;
@@ -542,6 +582,7 @@ int lbm_step(lbm_handle *h, int64_t n)
             if (h->parity == PARITY_A) {
                 CK(timed(h, LBM_KERNEL_AA_ODD, [&] { return o.aa_odd(h->hg, h->nxp, h->force, h->f, h->stream); }));
                 h->parity = PARITY_NATURAL;
+                h->g3fresh = false;
                 n -= 1; h->t += 1;
             } else if (n >= 2) {
                 WaveSchedule ws;
@@ -560,6 +601,7 @@ int lbm_step(lbm_handle *h, int64_t n)
             } else {
                 CK(timed(h, LBM_KERNEL_AA_EVEN, [&] { return o.aa_even(h->hg, h->nxp, h->force, h->f, h->stream); }));
                 h->parity = PARITY_A;
+                h->g3fresh = false;
                 n -= 1; h->t += 1;
             }
             break;
@@ -567,7 +609,21 @@ int lbm_step(lbm_handle *h, int64_t n)
             if (h->parity == PARITY_A) {
                 CK(timed(h, LBM_KERNEL_AA_ODD, [&] { return o.aa_odd(h->hg, h->nxp, h->force, h->f, h->stream); }));
                 h->parity = PARITY_NATURAL;
+                h->g3fresh = false;
                 n -= 1; h->t += 1;
+            } else if (n >= 2 && h->m3) {
+                if (!h->g3fresh) {
+                    CK(timed(h, LBM_KERNEL_SNAPSHOT, [&] {
+                        return o.shell_gather(h->hg, h->nxp, h->f, h->G3[h->g3cur], h->si, h->stream);
+                    }));
+                    h->g3fresh = true;
+                }
+                CK(timed(h, LBM_KERNEL_MERGED, [&] {
+                    return o.merged3(h->hg, h->nxp, h->force, h->f, h->G3[h->g3cur], h->G3[h->g3cur ^ 1], h->si,
+                                     h->stream);
+                }));
+                h->g3cur ^= 1;
+                n -= 2; h->t += 2;
             } else if (n >= 2) {
                 CK(timed(h, LBM_KERNEL_SNAPSHOT, [&] { return o.snapshot(h->hg, h->nxp, h->force, h->f, h->G, h->ti, h->stream); }));
                 CK(timed(h, LBM_KERNEL_MERGED, [&] {
@@ -577,6 +633,7 @@ int lbm_step(lbm_handle *h, int64_t n)
             } else {
                 CK(timed(h, LBM_KERNEL_AA_EVEN, [&] { return o.aa_even(h->hg, h->nxp, h->force, h->f, h->stream); }));
                 h->parity = PARITY_A;
+                h->g3fresh = false;
                 n -= 1; h->t += 1;
             }
             break;
@@ -619,6 +676,7 @@ int lbm_init_populations(lbm_handle *h, const void *f_in, int32_t dtype)
     if (!g.ok) return LBM_ECUDA;
     CK(h->ops->import_pop(h->hg, h->nxp, h->f, f_in, dtype, h->stream));
     h->parity = PARITY_NATURAL;
+    h->g3fresh = false;
     h->t = 0;
     h->adj_ready = false;
     return LBM_OK;
@@ -753,6 +811,7 @@ int lbm_adjoint_forward(lbm_handle *h, int64_t T, int64_t K, void *work, size_t 
     CK(cudaMemcpyAsync(w + (A.nck - 1) * A.state, cur, sb, cudaMemcpyDeviceToDevice, h->stream));
     CK(cudaMemcpyAsync(h->f, cur, sb, cudaMemcpyDeviceToDevice, h->stream));
     h->parity = PARITY_NATURAL;
+    h->g3fresh = false;
     h->t += T;
     h->adj_ready = true;
     h->adj_T = T;

@@ -29,6 +29,15 @@ struct TileInfo {
     int64_t gx_slot, gy_slot, gz_slot;
 };
 
+// Tiles of the shadow-shell merged sweep: 32 cells wide along x, bands of
+// near-equal height along y; its shadow G[z][tile][q][nsp] (tile = by * ntx
+// + bx) holds the stored populations of every tile-boundary cell.
+struct ShellInfo {
+    int ntx, nty;      // tiles along x and y
+    int hb, rem;       // band heights: hb + 1 for the first rem bands, else hb
+    int64_t gplane;    // elements of one z-plane of G
+};
+
 enum { PARITY_NATURAL = 0, PARITY_A = 1 };
 
 // Launchers of one storage format.  `pitch` is the row pitch (elements) of
@@ -62,6 +71,13 @@ struct StorageOps {
     cudaError_t (*merged)(const HostGeom &, int64_t pitch, bool force, void *f, const void *G, const TileInfo &,
                           const void *tmap, int *status, cudaStream_t);
     size_t (*merged_smem)(int tile_y);  // dynamic shared memory of the merged kernel (0 = not built)
+    // shadow-shell merged sweep: band height limit and shell slots per tile
+    // of this storage's instantiation; G* arrays hold stored elements
+    int m3_ty, m3_nsp;
+    cudaError_t (*shell_gather)(const HostGeom &, int64_t pitch, const void *f, void *G, const ShellInfo &,
+                                cudaStream_t);
+    cudaError_t (*merged3)(const HostGeom &, int64_t pitch, bool force, void *f, const void *Gcur, void *Gnext,
+                           const ShellInfo &, cudaStream_t);
     // persistent plane-wavefront sweep (two time steps); sched points to a
     // WaveSchedule (device pointers inside), grid = number of CTAs
     cudaError_t (*wavefront)(const HostGeom &, int64_t pitch, bool force, void *f, const void *sched, int grid,

@@ -17,7 +17,14 @@ from helpers import relmax
 pytestmark = pytest.mark.gpu
 
 CASES = cases()
-VARIANTS = ["two_lattice", "aa", "merged", "wavefront"]
+VARIANTS = ["two_lattice", "aa", "merged", "merged_snapshot", "wavefront"]
+
+
+def _variant(v):
+    """(variant, tile): "merged" takes the automatic tiles (the shadow-shell
+    sweep where z is not periodic), "merged_snapshot" an explicit 32 x 4 tile
+    (the snapshot sweep)."""
+    return ("merged", (32, 4)) if v == "merged_snapshot" else (v, (0, 0))
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -26,7 +33,8 @@ def test_cavity_32_fp64_100_steps(gpu, variant):
     cfg = oracle.cavity(32, 0.6)
     ref = oracle.run(cfg, oracle.init_equilibrium(cfg), 100)
     rho_r, u_r = oracle.moments(cfg, ref)
-    lat = make_gpu(cfg, "f64", variant)
+    v, tile = _variant(variant)
+    lat = make_gpu(cfg, "f64", v, tile=tile)
     lat.init_equilibrium()
     lat.step(100)
     assert relmax(gpu_state(lat), ref) <= 1e-12
@@ -41,7 +49,10 @@ def test_cavity_32_fp32_100_steps(gpu, storage, variant):
     cfg = oracle.cavity(32, 0.6)
     ref = oracle.run(cfg, oracle.init_equilibrium(cfg), 100)
     _, u_r = oracle.moments(cfg, ref)
-    lat = make_gpu(cfg, storage, variant)
+    v, tile = _variant(variant)
+    if storage != "f64" and v == "merged" and tile != (0, 0):
+        tile = (32, 16)
+    lat = make_gpu(cfg, storage, v, tile=tile)
     lat.init_equilibrium()
     lat.step(100)
     _, u = gpu_moments(lat)
@@ -55,7 +66,8 @@ def test_fp64_cases(gpu, name, variant, nsteps):
     cfg = oracle_force_as_f32(CASES[name])
     f0 = start_state(cfg, seed=nsteps)
     ref = oracle.run(cfg, f0, nsteps)
-    lat = make_gpu(cfg, "f64", variant, tile=(32, 4))
+    v, tile = _variant(variant)
+    lat = make_gpu(cfg, "f64", v, tile=tile)
     load_state(lat, f0)
     lat.step(nsteps)
     assert lat.time == nsteps

@@ -1,7 +1,8 @@
-"""The three schedules agree bit for bit (the paper verifies its two-step
-solvers against the single-step ones, Sec. 5.1; here the check is exact):
-TWO_LATTICE == AA == MERGED for every storage format, every MERGED tile
-shape, odd and even step counts and mixed step(n) sequences."""
+"""The schedules agree bit for bit (the paper verifies its two-step solvers
+against the single-step ones, Sec. 5.1; here the check is exact):
+TWO_LATTICE == AA == WAVEFRONT == MERGED for every storage format, the
+shadow-shell MERGED sweep (automatic tiles) and the snapshot sweep (explicit
+tiles), odd and even step counts and mixed step(n) sequences."""
 import numpy as np
 import pytest
 
@@ -27,7 +28,8 @@ def test_schedules_bitwise_equal(gpu, storage, name, nsteps):
     f0 = start_state(cfg, seed=3)
     ref = None
     tiles = [(32, 4)] + ([] if storage == "f64" else [(32, 8), (32, 16)])
-    runs = [("two_lattice", (0, 0)), ("aa", (0, 0)), ("wavefront", (0, 0))] + [("merged", t) for t in tiles]
+    runs = [("two_lattice", (0, 0)), ("aa", (0, 0)), ("wavefront", (0, 0)), ("merged", (0, 0))] + \
+        [("merged", t) for t in tiles]
     for variant, tile in runs:
         lat = make_gpu(cfg, storage, variant, tile=tile)
         load_state(lat, f0)
@@ -63,14 +65,38 @@ def test_mixed_step_sequences(gpu, storage):
     load_state(w, f0)
     for k in (2, 1, 4, 2):
         w.step(k)
-    assert m.time == a.time == t.time == w.time == 9
-    ra, rm, rt, rw = _raw(a), _raw(m), _raw(t), _raw(w)
-    assert torch.equal(ra, rm) and torch.equal(ra, rt) and torch.equal(ra, rw)
+    # shadow-shell sweep: consecutive sweeps reuse the shadow, a single step
+    # in between invalidates it
+    s3 = make_gpu(cfg, storage, "merged")
+    load_state(s3, f0)
+    for k in (2, 2, 1, 3, 1):
+        s3.step(k)
+    assert m.time == a.time == t.time == w.time == s3.time == 9
+    ra, rm, rt, rw, r3 = _raw(a), _raw(m), _raw(t), _raw(w), _raw(s3)
+    assert torch.equal(ra, rm) and torch.equal(ra, rt) and torch.equal(ra, rw) and torch.equal(ra, r3)
     # moments agree at both parities (a is at the odd parity after 9 steps)
-    for lat in (a, m, t, w):
+    for lat in (a, m, t, w, s3):
         rho, u = lat.moments(torch.float64)
         r0, u0 = a.moments(torch.float64)
         assert torch.equal(rho, r0) and torch.equal(u, u0)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16s"])
+def test_shadow_refreshed_after_new_state(gpu, storage):
+    """A state installed between shadow-shell sweeps replaces the shadow:
+    sweeps, a new state, sweeps again == AA on the new state."""
+    import torch
+    cfg = oracle_force_as_f32(CASES["mixed_33x40x9"])
+    m = make_gpu(cfg, storage, "merged")
+    load_state(m, start_state(cfg, seed=4))
+    m.step(4)
+    f1 = start_state(cfg, seed=5)
+    load_state(m, f1)
+    m.step(4)
+    a = make_gpu(cfg, storage, "aa")
+    load_state(a, f1)
+    a.step(4)
+    assert torch.equal(_raw(m), _raw(a))
 
 
 def test_equilibrium_init_matches_oracle(gpu):
