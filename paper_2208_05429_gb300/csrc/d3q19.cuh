@@ -190,31 +190,87 @@ __device__ __forceinline__ Mom<R> moments_of(const R (&s)[Q], R Fx, R Fy, R Fz)
     return m;
 }
 
-// In-place BGK + Guo collision of one cell's shifted populations.
-// omega = 1/tau, kf = 1 - omega/2.
+__device__ __forceinline__ float rrcp(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double rrcp(double a) { return __drcp_rn(a); }
+
+// In-place BGK + Guo collision of one cell's shifted populations s_i =
+// f_i - w_i.  omega = 1/tau, kf = 1 - omega/2.
+//
+// Opposite directions i and i+9 (i = 1..9) share w_i and |c_i . u|, so the
+// shifted equilibrium seq_i = feq_i - w_i splits into a part common to the
+// pair and a part of opposite sign, seq = sym +- anti with
+//   sym  = w (rho (4.5 (c.u)^2 - 1.5 u.u) + (rho - 1)),
+//   anti = 3 w rho (c.u),
+// and likewise the Guo source, S = w (9 (c.u)(c.F) - 3 u.F) +- 3 w c.F.
+// The relaxation keeps the form s + omega (seq - s) (the non-equilibrium
+// part is formed first, which keeps the rounding relative to it).  Every
+// schedule collides through this function, which is what keeps them
+// bit-identical to each other.
 template <class R, bool FORCE>
 __device__ __forceinline__ void bgk_collide(R (&s)[Q], R omega, R kf, R Fx, R Fy, R Fz)
 {
-    const Mom<R> m = moments_of<R, FORCE>(s, Fx, Fy, Fz);
-    const R usq = rfma(m.ux, m.ux, rfma(m.uy, m.uy, rmul(m.uz, m.uz)));
-    const R base = rmul(R(-1.5), usq);
+    // moments from pair sums and differences
+    R dif[10];
+    R drho = s[0];
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        drho = radd(drho, radd(s[i], s[i + 9]));
+        dif[i] = rsub(s[i], s[i + 9]);
+    });
+    R jx = R(0), jy = R(0), jz = R(0);
+    bool fx = true, fy = true, fz = true;
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        auto acc = [&](R &j, bool &first, int c) {
+            if (c == 0) return;
+            if (first) { j = c > 0 ? dif[i] : -dif[i]; first = false; }
+            else j = c > 0 ? radd(j, dif[i]) : rsub(j, dif[i]);
+        };
+        acc(jx, fx, cx(i));
+        acc(jy, fy, cy(i));
+        acc(jz, fz, cz(i));
+    });
+    const R rho = radd(R(1), drho);
+    if constexpr (FORCE) {
+        jx = rfma(R(0.5), Fx, jx);
+        jy = rfma(R(0.5), Fy, jy);
+        jz = rfma(R(0.5), Fz, jz);
+    }
+    const R inv = rrcp(rho);
+    const R ux = rmul(jx, inv), uy = rmul(jy, inv), uz = rmul(jz, inv);
+    const R ux2 = rmul(ux, ux), uy2 = rmul(uy, uy), uz2 = rmul(uz, uz);
+    const R m15 = rmul(R(-1.5), radd(radd(ux2, uy2), uz2));
+    // per weight class: A = w rho, C = w (rho (-1.5 u.u) + drho)
+    const R C0 = rfma(rmul(R(1.0 / 3.0), rho), m15, rmul(R(1.0 / 3.0), drho));
+    const R A1 = rmul(R(1.0 / 18.0), rho), A2 = rmul(R(1.0 / 36.0), rho);
+    const R C1 = rfma(A1, m15, rmul(R(1.0 / 18.0), drho)), C2 = rfma(A2, m15, rmul(R(1.0 / 36.0), drho));
+    const R D1 = rmul(R(4.5), A1), D2 = rmul(R(4.5), A2);
+    const R E1 = rmul(R(3), A1), E2 = rmul(R(3), A2);
     R uF = R(0);
-    if constexpr (FORCE) uF = rfma(m.ux, Fx, rfma(m.uy, Fy, rmul(m.uz, Fz)));
-    static_for<Q>([&](auto K) {
-        constexpr int i = decltype(K)::value;
-        const R cu = cdot<i, R>(m.ux, m.uy, m.uz);
-        // 3 c.u + 4.5 (c.u)^2 - 1.5 u.u
-        const R P = (i == 0) ? base : rfma(cu, rfma(R(4.5), cu, R(3)), base);
-        // feq_i - w_i
-        const R seq = rmul(R(wgt(i)), rfma(m.rho, P, m.drho));
-        R out = rfma(omega, rsub(seq, s[i]), s[i]);
+    if constexpr (FORCE) uF = rfma(ux, Fx, rfma(uy, Fy, rmul(uz, Fz)));
+    s[0] = rfma(omega, rsub(C0, s[0]), s[0]);
+    if constexpr (FORCE) s[0] = rfma(kf, -uF, s[0]);  // w_0 S_0 = -3 w_0 u.F = -u.F
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        constexpr bool face = csq(i) == 1;
+        const R cu = cdot<i, R>(ux, uy, uz);
+        R t;
+        if constexpr (face) t = cx(i) != 0 ? ux2 : (cy(i) != 0 ? uy2 : uz2);
+        else t = rmul(cu, cu);
+        const R sym = rfma(face ? D1 : D2, t, face ? C1 : C2);
+        const R anti = rmul(face ? E1 : E2, cu);
+        R a = rfma(omega, rsub(radd(sym, anti), s[i]), s[i]);
+        R b = rfma(omega, rsub(rsub(sym, anti), s[i + 9]), s[i + 9]);
         if constexpr (FORCE) {
+            constexpr double w = wgt(i);
             const R cF = cdot<i, R>(Fx, Fy, Fz);
-            // S_i = w_i (3 (c.F - u.F) + 9 (c.u)(c.F))
-            const R S = rmul(R(wgt(i)), rfma(rmul(R(9), cu), cF, rmul(R(3), rsub(cF, uF))));
-            out = rfma(kf, S, out);
+            const R ssym = rfma(rmul(R(9 * w), cu), cF, rmul(R(-3 * w), uF));
+            const R santi = rmul(R(3 * w), cF);
+            a = rfma(kf, radd(ssym, santi), a);
+            b = rfma(kf, rsub(ssym, santi), b);
         }
-        s[i] = out;
+        s[i] = a;
+        s[i + 9] = b;
     });
 }
 

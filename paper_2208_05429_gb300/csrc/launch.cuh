@@ -183,8 +183,11 @@ struct Launch {
         }
     }
     // band height of the shadow-shell sweep: 32 x 14 tiles (one per SM on a
-    // 256^2 plane) for 4-byte and 2-byte storage, 32 x 6 for FP64 (registers)
-    static constexpr int M3_TY = sizeof(R) == 8 ? 6 : 14;
+    // 256^2 plane) for 4-byte and 2-byte storage, 32 x 4 for FP64 (shared
+    // memory)
+    static constexpr int M3_TY = sizeof(R) == 8 ? 4 : 14;
+    using M3L = M3Smem<M3_TY, T, R>;
+    static_assert(M3L::bytes <= 232448, "shadow-shell sweep shared memory");
     static cudaError_t shell_gather(const HostGeom &h, int64_t pitch, const void *f, void *G, const ShellInfo &si,
                                     cudaStream_t st)
     {
@@ -196,21 +199,23 @@ struct Launch {
     }
     template <bool F>
     static cudaError_t merged3_f(const HostGeom &h, int64_t pitch, void *f, const void *Gc, void *Gn,
-                                 const ShellInfo &si, cudaStream_t st)
+                                 const ShellInfo &si, const void *tmap, int *status, cudaStream_t st)
     {
-        using L3 = M3<M3_TY>;
-        constexpr size_t smem = L3::template smem<R>();
+        constexpr size_t smem = M3L::bytes;
         cudaError_t e = cudaFuncSetAttribute(k_merged3<S, F, M3_TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        k_merged3<S, F, M3_TY><<<dim3(si.ntx, si.nty), L3::THREADS, smem, st>>>(
-            make_geom<R>(h, pitch), make_dirs((T *)f, slot_of(h, pitch)), (const T *)Gc, (T *)Gn, si);
+        CUtensorMap map;
+        memcpy(&map, tmap, sizeof(map));
+        k_merged3<S, F, M3_TY><<<dim3(si.ntx, si.nty), M3<M3_TY>::THREADS, smem, st>>>(
+            map, make_geom<R>(h, pitch), make_dirs((T *)f, slot_of(h, pitch)), (const T *)Gc, (T *)Gn, si, status);
         return cudaGetLastError();
     }
     static cudaError_t merged3(const HostGeom &h, int64_t pitch, bool force, void *f, const void *Gc, void *Gn,
-                               const ShellInfo &si, cudaStream_t st)
+                               const ShellInfo &si, const void *tmap, int *status, cudaStream_t st)
     {
-        return force ? merged3_f<true>(h, pitch, f, Gc, Gn, si, st) : merged3_f<false>(h, pitch, f, Gc, Gn, si, st);
+        return force ? merged3_f<true>(h, pitch, f, Gc, Gn, si, tmap, status, st)
+                     : merged3_f<false>(h, pitch, f, Gc, Gn, si, tmap, status, st);
     }
     static cudaError_t wavefront(const HostGeom &h, int64_t pitch, bool force, void *f, const void *sched, int grid,
                                  cudaStream_t st)

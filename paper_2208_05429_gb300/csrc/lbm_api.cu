@@ -262,8 +262,8 @@ EncodeTiledFn encode_tiled()
 }
 
 // 4D map over f[q][z][y][x] (x extent nx, row pitch nxp) with a box of one
-// tile plane and all 19 directions.
-bool make_tmap(const lbm_config &c, const TileInfo &ti, void *f, CUtensorMap *map)
+// tile plane (tx x ty) and bq directions.
+bool make_tmap(const lbm_config &c, int tx, int ty, int bq, void *f, CUtensorMap *map)
 {
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return false;
@@ -277,7 +277,7 @@ bool make_tmap(const lbm_config &c, const TileInfo &ti, void *f, CUtensorMap *ma
     const cuuint64_t es = elem_size_of(c.storage), nxp = (cuuint64_t)pitch_of(c);
     const cuuint64_t dims[4] = {(cuuint64_t)c.nx, (cuuint64_t)c.ny, (cuuint64_t)c.nz, (cuuint64_t)Q};
     const cuuint64_t strides[3] = {nxp * es, nxp * (cuuint64_t)c.ny * es, nxp * (cuuint64_t)c.ny * (cuuint64_t)c.nz * es};
-    const cuuint32_t box[4] = {(cuuint32_t)ti.TX, (cuuint32_t)ti.TY, 1u, (cuuint32_t)Q};
+    const cuuint32_t box[4] = {(cuuint32_t)tx, (cuuint32_t)ty, 1u, (cuuint32_t)bq};
     const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
     return fn(map, dt, 4, f, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -452,7 +452,10 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
     const int64_t n = cfg->nx * cfg->ny * cfg->nz;
     int64_t nb = (n + 255) / 256;
     h->red_blocks = (int)(nb < RED_BLOCKS_MAX ? nb : RED_BLOCKS_MAX);
-    if ((cfg->variant == LBM_VARIANT_MERGED && !h->m3 && !make_tmap(*cfg, h->ti, h->f, &h->tmap)) ||
+    const bool tmap_ok = cfg->variant != LBM_VARIANT_MERGED ||
+                         (h->m3 ? make_tmap(*cfg, 32, h->ops->m3_ty, 1, h->f, &h->tmap)
+                                : make_tmap(*cfg, h->ti.TX, h->ti.TY, Q, h->f, &h->tmap));
+    if (!tmap_ok ||
         cudaMemsetAsync(buf, 0, L.total, h->stream) != cudaSuccess) {
         if (own) cudaFree(buf);
         delete h->ev_pool;
@@ -620,7 +623,7 @@ int lbm_step(lbm_handle *h, int64_t n)
                 }
                 CK(timed(h, LBM_KERNEL_MERGED, [&] {
                     return o.merged3(h->hg, h->nxp, h->force, h->f, h->G3[h->g3cur], h->G3[h->g3cur ^ 1], h->si,
-                                     h->stream);
+                                     &h->tmap, h->status, h->stream);
                 }));
                 h->g3cur ^= 1;
                 n -= 2; h->t += 2;

@@ -7,14 +7,18 @@
 // threads' sub-domains meet safe by handling them apart (the intersection
 // layers of Alg. 3, Sec. 4.2).  Here:
 //
-//  * A CTA owns a column of 32 x TH cells (TH <= TY, the rows of the plane
-//    split into bands of near-equal height) and marches it along z.  At
-//    iteration k it performs the even (local) half of the AA pair on plane
-//    k+1 and the odd half on plane k.  Post-collision values move between
-//    threads through shared-memory rings (one per z-group of directions,
-//    sized to how long the values live) covering the tile and a one-cell
-//    halo ring; the rest population and the pure-z directions stay in
-//    registers.  One __syncthreads per plane.
+//  * A CTA owns a column of 32 x TH cells (TH <= TY; the rows of the plane
+//    are split into bands of near-equal height) and marches it along z.
+//    Its warps are specialised: "even" warps (one per tile row) collide
+//    plane k+2 and hand the post-collision values to shared-memory rings,
+//    "odd" warps (one per tile row) gather plane k from the rings, collide
+//    and scatter into f, and halo warps re-collide the one-cell halo ring
+//    and stage the inputs.  Even and odd warps work in the same interval
+//    between two __syncthreads, two planes apart, so twice as many warps
+//    hide each other's latencies.
+//  * Inputs of a plane arrive in a two-slot stage: one TMA tensor copy per
+//    direction for the 32 x TY tile, and cp.async copies for the tile's own
+//    shell cells and its halo cells, all completing on the slot's mbarrier.
 //  * Cells on a tile's boundary ring ("shell" cells) are read by up to four
 //    CTAs: the owner and the neighbours whose halo they are.  Every shell
 //    cell also lives in a double-buffered shadow G: a sweep takes shell and
@@ -23,15 +27,10 @@
 //    cell to G_next as well as to f.  No CTA reads what another CTA writes
 //    during the sweep, so tiles need no synchronisation at all, and f stays
 //    the complete state after every sweep.
-//  * The halo ring is collided again by dedicated halo warps from G_cur
-//    (2 x 34 + 2 x TY cells, three warps for TY = 14), so the tile warps
-//    run without divergent halo code.
-//  * Inputs are loaded straight into registers one plane ahead (coalesced
-//    32-wide rows of f; G rows of the tile's shell slots).
 //
 // HBM traffic per two steps: every population read and written once, plus
 // the shell shadow (read once by its owner, written once): 2 x 19 x
-// sizeof(T) x (1 + NS/cells-per-tile) bytes per cell.
+// sizeof(T) x (1 + NS / (32 TY)) bytes per cell.
 #pragma once
 
 #include "merged.cuh"
@@ -42,15 +41,44 @@ template <int TY>
 struct M3 {
     static constexpr int TX = 32, W = TX + 2, H = TY + 2, NPOS = W * H;
     static constexpr int NT = TX * TY;
-    static constexpr int NH = 2 * W + 2 * TY;  // halo ring cells
-    static constexpr int NHW = (NH + 31) / 32;  // halo warps
-    static constexpr int THREADS = NT + 32 * NHW;
-    static constexpr int NS = 2 * TX + 2 * (TY - 2);  // shell slots of a full tile
+    static constexpr int NH = 2 * W + 2 * TY;          // halo ring cells
+    static constexpr int NHW = (NH + 31) / 32;          // halo warps
+    static constexpr int NHT = 32 * NHW;                // halo threads
+    static constexpr int NWARPS = 2 * TY + NHW;
+    static constexpr int THREADS = 32 * NWARPS;
+    static constexpr int NS = 2 * TX + 2 * (TY - 2);    // shell slots of a full tile
     static constexpr int NSP = (NS + 7) / 8 * 8;
-    static constexpr int NRING = SLM * NDM + SL0 * ND0 + SLP * NDP;
-    template <class R>
-    static constexpr size_t smem() { return (size_t)NRING * NPOS * sizeof(R) + (size_t)NPOS * sizeof(int); }
+    // ring slots per z-group (planes alive at once with even warps two
+    // planes ahead of odd warps) and the small rings of the rest and pure-z
+    // populations
+    static constexpr int RSM = 3, RS0 = 3, RSP = 4;
+    static constexpr int NRING = RSM * NDM + RS0 * ND0 + RSP * NDP;
+    static constexpr int SREST = 3, SZP = 4, SZM = 3;
     static_assert(TY >= 2, "bands of at least two rows");
+    static_assert(THREADS <= 1024, "one CTA");
+};
+
+// Shared-memory layout of one CTA for stored type T and compute type R.
+template <int TY, class T, class R>
+struct M3Smem {
+    using L = M3<TY>;
+    static constexpr int EPU = sizeof(T) >= 4 ? 1 : 4 / (int)sizeof(T);  // elements per copy unit
+    static constexpr int CP = (int)sizeof(T) * EPU;                         // bytes per copy unit
+    static constexpr int DST = (L::NT + L::NSP + 128 / (int)sizeof(T) - 1) / (128 / (int)sizeof(T)) *
+                               (128 / (int)sizeof(T));                      // tile-block stride per direction
+    static constexpr size_t tile_bytes = (size_t)Q * DST * sizeof(T);
+    static constexpr size_t halo_bytes = (size_t)Q * L::NHT * CP;
+    static constexpr size_t slot_bytes = (tile_bytes + halo_bytes + 127) / 128 * 128;
+    static constexpr size_t stage_off = 0;
+    static constexpr size_t ring_off = 2 * slot_bytes;
+    static constexpr size_t small_off = ring_off + (size_t)L::NRING * L::NPOS * sizeof(R);
+    static constexpr size_t gtab_off = small_off + (size_t)(L::SREST + L::SZP + L::SZM) * L::NT * sizeof(R);
+    static constexpr size_t bar_off = (gtab_off + (size_t)L::NPOS * sizeof(int) + 15) / 16 * 16;
+    static constexpr size_t flag_off = bar_off + 2 * sizeof(uint64_t);
+    static constexpr size_t bytes = flag_off + 16;
+    static constexpr unsigned tma_bytes = (unsigned)(Q * L::NT * sizeof(T));
+    static constexpr int CHUNKS = L::NSP * (int)sizeof(T) / 16;  // 16-byte chunks of one direction's shell row
+    static_assert(L::NSP * sizeof(T) % 16 == 0, "shell rows in 16-byte chunks");
 };
 
 // Shell slot of local cell (lx, ly) of a tw x th tile, or -1 inside:
@@ -125,46 +153,74 @@ __global__ void __launch_bounds__(256) k_shell_gather(Geom<typename S::R> g, Dir
     });
 }
 
+
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t *bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Directions with c_z = -1 / +1 (wall links on the z = 0 / nz-1 planes).
+__host__ __device__ constexpr unsigned z_bits(int sign)
+{
+    unsigned m = 0u;
+    for (int i = 0; i < Q; ++i)
+        if (cz(i) == sign) m |= 1u << i;
+    return m;
+}
+
 template <class S, bool FORCE, int TY>
-struct Merged3Cta {
+struct M3Cta {
     using R = typename S::R;
     using T = typename S::T;
     using L = M3<TY>;
-    static constexpr int W = L::W, NPOS = L::NPOS, NSP = L::NSP;
+    using SM = M3Smem<TY, T, R>;
+    static constexpr int W = L::W, NPOS = L::NPOS, NSP = L::NSP, NT = L::NT, NHT = L::NHT;
+    static constexpr int DST = SM::DST, EPU = SM::EPU, CP = SM::CP;
+    static constexpr unsigned CZM = z_bits(-1), CZP = z_bits(1);
+    enum { EVEN = 0, ODD = 1, HALO = 2 };
 
     const Geom<R> &g;
     const Dirs<T> &fd;
     const T *__restrict__ Gc;
     T *__restrict__ Gn;
     const ShellInfo &si;
-    R *ringm, *ring0, *ringp;
+    const CUtensorMap *tmap;
+    unsigned char *smem;
+    R *ringm, *ring0, *ringp, *srest, *szp, *szm;
     int *gtab;
-    int x0, y0, tw, th, lx, ly, x, y, pos, nx, ny, nz, goff, cxy;
-    unsigned gmask;
-    bool tile_thr, active, perx, pery, wxl, wxh, wyl, wyh, xybnd;
-    R rest_c, rest_n, zp1, zp0, zp_n, zm_prev, zm_n;
+    uint64_t *bar;
+    int role, x0, y0, tw, th, lx, ly, x, y, pos, tc, hidx, nx, ny, nz, goff, cxy, inoff, sub;
+    unsigned gmask, wxy, lxy;
+    bool active, perx, pery, xybnd, timed_out;
 
-    __device__ __forceinline__ Merged3Cta(const Geom<R> &g_, const Dirs<T> &fd_, const T *Gc_, T *Gn_,
-                                          const ShellInfo &si_, unsigned char *smem)
-        : g(g_), fd(fd_), Gc(Gc_), Gn(Gn_), si(si_)
+    __device__ __forceinline__ M3Cta(const Geom<R> &g_, const Dirs<T> &fd_, const T *Gc_, T *Gn_, const ShellInfo &si_,
+                                     const CUtensorMap *tmap_, unsigned char *smem_)
+        : g(g_), fd(fd_), Gc(Gc_), Gn(Gn_), si(si_), tmap(tmap_), smem(smem_)
     {
-        ringm = reinterpret_cast<R *>(smem);
-        ring0 = ringm + SLM * NDM * NPOS;
-        ringp = ring0 + SL0 * ND0 * NPOS;
-        gtab = reinterpret_cast<int *>(ringp + SLP * NDP * NPOS);
+        ringm = reinterpret_cast<R *>(smem + SM::ring_off);
+        ring0 = ringm + L::RSM * NDM * NPOS;
+        ringp = ring0 + L::RS0 * ND0 * NPOS;
+        srest = reinterpret_cast<R *>(smem + SM::small_off);
+        szp = srest + L::SREST * NT;
+        szm = szp + L::SZP * NT;
+        gtab = reinterpret_cast<int *>(smem + SM::gtab_off);
+        bar = reinterpret_cast<uint64_t *>(smem + SM::bar_off);
         nx = g.nx; ny = g.ny; nz = g.nz;
         perx = g.per[0] != 0; pery = g.per[1] != 0;
         x0 = 32 * blockIdx.x;
         tw = min(32, nx - x0);
         band_of(si, blockIdx.y, y0, th);
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        tile_thr = warp < TY;
-        if (tile_thr) {
-            lx = lane; ly = warp;
+        role = warp < TY ? EVEN : (warp < 2 * TY ? ODD : HALO);
+        hidx = 0;
+        if (role != HALO) {
+            lx = lane;
+            ly = role == EVEN ? warp : warp - TY;
             active = lx < tw && ly < th;
         } else {
             // halo ring: row -1, row th, column -1, column tw
-            const int h = (warp - TY) * 32 + lane;
+            const int h = (warp - 2 * TY) * 32 + lane;
+            hidx = h;
             active = true;
             if (h < W) { lx = h - 1; ly = -1; active = lx <= tw; }
             else if (h < 2 * W) { lx = h - W - 1; ly = th; active = lx <= tw; }
@@ -173,18 +229,31 @@ struct Merged3Cta {
             else { lx = 0; ly = 0; active = false; }
         }
         pos = (ly + 1) * W + (lx + 1);
+        tc = role == HALO ? 0 : ly * 32 + lx;
         x = x0 + lx; y = y0 + ly;
-        if (!tile_thr && active) {  // wrap the halo cell into the domain, or drop it (wall)
+        if (role == HALO && active) {  // wrap the halo cell into the domain, or drop it (wall)
             if (x < 0 || x >= nx) { if (perx) x = x < 0 ? x + nx : x - nx; else active = false; }
             if (y < 0 || y >= ny) { if (pery) y = y < 0 ? y + ny : y - ny; else active = false; }
         }
-        wxl = tile_thr && x == 0 && !perx; wxh = tile_thr && x == nx - 1 && !perx;
-        wyl = tile_thr && y == 0 && !pery; wyh = tile_thr && y == ny - 1 && !pery;
         xybnd = x == 0 || x == nx - 1 || y == 0 || y == ny - 1;
         cxy = active ? y * (int)g.nxp + x : 0;
-        rest_c = rest_n = zp1 = zp0 = zp_n = zm_prev = zm_n = R(0);
         goff = -1;
-        gmask = 0u;
+        inoff = 0;
+        sub = 0;
+        gmask = wxy = lxy = 0u;
+        timed_out = false;
+        // wall links through the x and y faces, and those ending on a lid
+        if (active) {
+            static_for<Q>([&](auto K) {
+                constexpr int i = decltype(K)::value;
+                bool wall = false, lid = false;
+                const int tx = x + cx(i), ty = y + cy(i);
+                if ((tx < 0 || tx >= nx) && !perx) { wall = true; lid |= g.lid[tx < 0 ? 0 : 1] != 0; }
+                if ((ty < 0 || ty >= ny) && !pery) { wall = true; lid |= g.lid[ty < 0 ? 2 : 3] != 0; }
+                if (wall) wxy |= 1u << i;
+                if (wall && lid) lxy |= 1u << i;
+            });
+        }
     }
 
     // Shadow offsets of every ring and halo position (one table per CTA).
@@ -204,86 +273,127 @@ struct Merged3Cta {
         }
     }
 
-    // After fill_gtab and a barrier: own shadow offset and, for tile
-    // threads, the directions whose (non-wall) target is a shell cell.
-    __device__ __forceinline__ void setup_masks()
+    // After fill_gtab and a barrier.
+    __device__ __forceinline__ void setup()
     {
         if (!active) return;
         goff = gtab[pos];
-        if (!tile_thr) return;
-        static_for<Q>([&](auto K) {
-            constexpr int i = decltype(K)::value;
-            if (gtab[pos + cx(i) + cy(i) * W] >= 0) gmask |= 1u << i;
-        });
+        if (role == EVEN) {
+            const int s = shell_slot<TY>(lx, ly, tw, th);
+            inoff = s >= 0 ? NT + s : ly * 32 + lx;
+        } else if (role == HALO) {
+            sub = goff & (EPU - 1);
+        } else {
+            static_for<Q>([&](auto K) {
+                constexpr int i = decltype(K)::value;
+                if (gtab[pos + cx(i) + cy(i) * W] >= 0) gmask |= 1u << i;
+            });
+        }
     }
 
     __device__ __forceinline__ static int slot(int plane, int n) { return (plane + n) % n; }
     template <int GG>
     __device__ __forceinline__ R *ring_at(int plane, int gi) const
     {
-        if constexpr (GG == GRP_M) return ringm + (slot(plane, SLM) * NDM + gi) * NPOS;
-        else if constexpr (GG == GRP_0) return ring0 + (slot(plane, SL0) * ND0 + gi) * NPOS;
-        else return ringp + (slot(plane, SLP) * NDP + gi) * NPOS;
+        if constexpr (GG == GRP_M) return ringm + (slot(plane, L::RSM) * NDM + gi) * NPOS;
+        else if constexpr (GG == GRP_0) return ring0 + (slot(plane, L::RS0) * ND0 + gi) * NPOS;
+        else return ringp + (slot(plane, L::RSP) * NDP + gi) * NPOS;
+    }
+    __device__ __forceinline__ T *tile_block(int q) const { return reinterpret_cast<T *>(smem + (q & 1) * SM::slot_bytes); }
+    __device__ __forceinline__ unsigned char *halo_block(int q) const
+    {
+        return smem + (q & 1) * SM::slot_bytes + SM::tile_bytes;
     }
 
-    // Stored inputs of plane z: the shadow for shell and halo cells, f for
-    // the inside of the tile.
-    __device__ __forceinline__ void load(int z, T (&raw)[Q]) const
+    // Halo warps: start the copies of plane q into its stage slot.
+    __device__ __forceinline__ void issue_stage(int q)
     {
-        if (!active) return;
-        if (goff >= 0) {
-            const T *p = Gc + z * si.gplane + goff;
+        uint64_t *b = &bar[q & 1];
+        T *tb = tile_block(q);
+        if (hidx == 0) {
+            mbar_arrive_expect_tx(b, SM::tma_bytes);
+            for (int d = 0; d < Q; ++d) tma_load_4d(tb + d * DST, tmap, x0, y0, q, d, b);
+        }
+        // the tile's own shell cells: 16-byte chunks of its shadow rows
+        const T *gs = Gc + q * si.gplane + (int64_t)(blockIdx.y * si.ntx + blockIdx.x) * Q * NSP;
+        for (int ch = hidx; ch < Q * SM::CHUNKS; ch += NHT) {
+            const int d = ch / SM::CHUNKS, j = ch - d * SM::CHUNKS;
+            cp_async<16>(reinterpret_cast<unsigned char *>(tb + d * DST + NT) + 16 * j,
+                         reinterpret_cast<const unsigned char *>(gs + d * NSP) + 16 * j);
+        }
+        // this thread's halo cell: the copy unit holding each direction
+        if (active) {
+            const T *hs = Gc + q * si.gplane + (goff - sub);
+            unsigned char *hb = halo_block(q) + hidx * CP;
             static_for<Q>([&](auto K) {
                 constexpr int i = decltype(K)::value;
-                raw[i] = p[i * NSP];
-            });
-        } else {
-            const int c = cxy + z * (int)g.plane;
-            static_for<Q>([&](auto K) {
-                constexpr int i = decltype(K)::value;
-                raw[i] = fd.p[i][c];
+                cp_async<CP>(hb + i * NHT * CP, hs + i * NSP);
             });
         }
+        cp_async_mbar_arrive(b);
     }
 
-    // Even step of plane q: collide and hand every value to its ring.
-    __device__ __forceinline__ void produce(int q, const T (&raw)[Q])
+    __device__ __forceinline__ void wait_stage(int q)
+    {
+        if (!mbar_wait_bounded(&bar[q & 1], (unsigned)((q >> 1) & 1))) timed_out = true;
+    }
+
+    // Even step of plane q (even and halo warps): collide, hand every value
+    // to its ring.
+    __device__ __forceinline__ void produce(int q)
     {
         if (!active) return;
         R s[Q];
-        static_for<Q>([&](auto K) {
-            constexpr int i = decltype(K)::value;
-            s[i] = decode<S, i>(raw[i]);
-        });
+        if (role == EVEN) {
+            const T *in = tile_block(q) + inoff;
+            static_for<Q>([&](auto K) {
+                constexpr int i = decltype(K)::value;
+                s[i] = decode<S, i>(in[i * DST]);
+            });
+        } else {
+            const unsigned char *hb = halo_block(q) + hidx * CP;
+            static_for<Q>([&](auto K) {
+                constexpr int i = decltype(K)::value;
+                s[i] = decode<S, i>(reinterpret_cast<const T *>(hb + i * NHT * CP)[sub]);
+            });
+        }
         R Fx, Fy, Fz;
         force_at<R, FORCE>(g, canon(g, x, y, q), ncanon(g), Fx, Fy, Fz);
         bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
-        outgoing_values<S>(g, x, y, q, s);
-        static_for<Q>([&](auto K) {
-            constexpr int i = decltype(K)::value;
-            s[i] = roundtrip<S, i>(s[i]);
-        });
-        rest_n = s[0];
-        zm_n = s[DIR_ZM];
-        zp_n = s[DIR_ZP];
+        // value that leaves along c_i as the next step reads it: + L_opp(i)
+        // on a wall link that ends on a lid
+        const unsigned lm = lxy | (q == 0 && g.lid[4] ? CZM : 0u) | (q == nz - 1 && g.lid[5] ? CZP : 0u);
+        if (lm) {
+            static_for<Q>([&](auto K) {
+                constexpr int i = decltype(K)::value;
+                if (lm & (1u << i)) s[i] = radd(s[i], g.L[opp(i)]);
+            });
+        }
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;
             constexpr int gg = grp(i);
-            if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P) ring_at<gg>(q, gidx(i))[pos] = s[i];
+            const R v = roundtrip<S, i>(s[i]);
+            if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P) ring_at<gg>(q, gidx(i))[pos] = v;
+            else if (role == EVEN) {
+                if constexpr (i == 0) srest[slot(q, L::SREST) * NT + tc] = v;
+                else if constexpr (i == DIR_ZP) szp[slot(q, L::SZP) * NT + tc] = v;
+                else szm[slot(q, L::SZM) * NT + tc] = v;
+            }
         });
     }
 
-    // Odd step of plane k: gather, collide, scatter into f and, for targets
-    // on a shell, into the next shadow.
+    // Odd step of plane k (odd warps): gather, collide, scatter into f and,
+    // for targets on a shell, into the next shadow.
     __device__ __forceinline__ void consume(int k)
     {
-        if (!active || !tile_thr) return;
+        if (!active) return;
         const bool zlo = k == 0, zhi = k == nz - 1;
+        const unsigned wm = wxy | (zlo ? CZM : 0u) | (zhi ? CZP : 0u);
         R s[Q];
-        s[0] = rest_c;
-        s[DIR_ZP] = zlo ? zm_prev : zp1;
-        s[DIR_ZM] = zhi ? zp0 : zm_n;
-        if (!(wxl || wxh || wyl || wyh || zlo || zhi)) {
+        s[0] = srest[slot(k, L::SREST) * NT + tc];
+        s[DIR_ZP] = zlo ? szm[slot(k, L::SZM) * NT + tc] : szp[slot(k - 1, L::SZP) * NT + tc];
+        s[DIR_ZM] = zhi ? szp[slot(k, L::SZP) * NT + tc] : szm[slot(k + 1, L::SZM) * NT + tc];
+        if (!wm) {
             static_for<Q>([&](auto K) {
                 constexpr int i = decltype(K)::value;
                 constexpr int gg = grp(i);
@@ -295,10 +405,8 @@ struct Merged3Cta {
                 constexpr int i = decltype(K)::value;
                 constexpr int gg = grp(i);
                 if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P) {
-                    const bool wall = (cx(i) == 1 && wxl) || (cx(i) == -1 && wxh) || (cy(i) == 1 && wyl) ||
-                                      (cy(i) == -1 && wyh) || (cz(i) == 1 && zlo) || (cz(i) == -1 && zhi);
-                    if (!wall) s[i] = ring_at<gg>(k - cz(i), gidx(i))[pos - cx(i) - cy(i) * W];
-                    else s[i] = ring_at<grp(opp(i))>(k, gidx(opp(i)))[pos];
+                    if (wm & (1u << opp(i))) s[i] = ring_at<grp(opp(i))>(k, gidx(opp(i)))[pos];
+                    else s[i] = ring_at<gg>(k - cz(i), gidx(i))[pos - cx(i) - cy(i) * W];
                 }
             });
         }
@@ -308,17 +416,16 @@ struct Merged3Cta {
         scatter(k, s);
     }
 
-    __device__ __forceinline__ T *gnext(int z) const { return Gn + z * si.gplane; }
-
     __device__ __forceinline__ void scatter(int k, const R (&s)[Q]) const
     {
         const int c = cxy + k * (int)g.plane;
+        T *const gk = Gn + k * si.gplane;
         if (!xybnd && k > 0 && k < nz - 1) {
             static_for<Q>([&](auto K) {
                 constexpr int i = decltype(K)::value;
                 const T e = encode<S, i>(s[i]);
                 fd.p[i][c + g.noff[i]] = e;
-                if (gmask & (1u << i)) gnext(k + cz(i))[gtab[pos + cx(i) + cy(i) * W] + i * NSP] = e;
+                if (gmask & (1u << i)) gk[cz(i) * si.gplane + gtab[pos + cx(i) + cy(i) * W] + i * NSP] = e;
             });
         } else {
             const Faces fc = faces_of(g, x, y, k);
@@ -330,58 +437,67 @@ struct Merged3Cta {
                     if (fc.lid & m) v = radd(v, g.L[opp(i)]);
                     const T e = encode<S, opp(i)>(v);
                     fd.p[opp(i)][c] = e;
-                    if (goff >= 0) gnext(k)[goff + opp(i) * NSP] = e;
+                    if (goff >= 0) gk[goff + opp(i) * NSP] = e;
                 } else {
                     const T e = encode<S, i>(s[i]);
                     fd.p[i][c + step_offset<cx(i), cy(i), cz(i)>(g, fc)] = e;
                     const int t = gtab[pos + cx(i) + cy(i) * W];
-                    if (t >= 0) gnext(k + cz(i))[t + i * NSP] = e;
+                    if (t >= 0) gk[cz(i) * si.gplane + t + i * NSP] = e;
                 }
             });
         }
-    }
-
-    __device__ __forceinline__ void rotate()
-    {
-        rest_c = rest_n;
-        zp1 = zp0;
-        zp0 = zp_n;
-        zm_prev = zm_n;
     }
 };
 
 template <class S, bool FORCE, int TY>
 __global__ void __launch_bounds__(M3<TY>::THREADS, 1)
-    k_merged3(Geom<typename S::R> g, Dirs<typename S::T> fd, const typename S::T *__restrict__ Gc,
-              typename S::T *__restrict__ Gn, ShellInfo si)
+    k_merged3(const __grid_constant__ CUtensorMap tmap, Geom<typename S::R> g, Dirs<typename S::T> fd,
+              const typename S::T *__restrict__ Gc, typename S::T *__restrict__ Gn, ShellInfo si,
+              int *__restrict__ status)
 {
-    using C = Merged3Cta<S, FORCE, TY>;
-    using T = typename S::T;
+    using C = M3Cta<S, FORCE, TY>;
+    using SM = typename C::SM;
     extern __shared__ __align__(128) unsigned char smem[];
-    C c(g, fd, Gc, Gn, si, smem);
+    C c(g, fd, Gc, Gn, si, &tmap, smem);
+    int *abort_flag = reinterpret_cast<int *>(smem + SM::flag_off);
     const int nz = g.nz;
+    if (threadIdx.x == 0) {
+        mbar_init(&c.bar[0], 1 + M3<TY>::NHT);
+        mbar_init(&c.bar[1], 1 + M3<TY>::NHT);
+        mbar_fence_init();
+        *abort_flag = 0;
+    }
     c.fill_gtab();
     __syncthreads();
-    c.setup_masks();
-
-    T raw[Q], nxt[Q];
-    c.load(0, raw);
-    if (nz > 1) c.load(1, nxt);
-    c.produce(0, raw);
-    c.rotate();
-    // iteration k: even step of plane k+1, odd step of plane k
-    for (int k = 0; k < nz; ++k) {
-        const int q = k + 1;
-        if (q < nz) {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) raw[i] = nxt[i];
-            if (q + 1 < nz) c.load(q + 1, nxt);
-            c.produce(q, raw);
+    c.setup();
+    if (c.role == C::HALO) c.issue_stage(0);
+    // interval k: even and halo warps collide plane k+2, odd warps plane k;
+    // the halo warps start loading plane k+3 into the slot plane k+1 freed
+    for (int k = -2; k < nz; ++k) {
+        const int q = k + 2;
+        if (c.role == C::HALO && k + 3 < nz) c.issue_stage(k + 3);
+        if (c.role != C::ODD) {
+            if (q < nz) {
+                c.wait_stage(q);
+                if (!c.timed_out) c.produce(q);
+            }
+        } else if (k >= 0) {
+            c.consume(k);
         }
+        if (c.timed_out) *abort_flag = 1;
         __syncthreads();
-        c.consume(k);
-        c.rotate();
+        if (*abort_flag) goto bail;
     }
+    return;
+
+bail:
+    // a stage never completed: record it, drain the copies still in flight
+    // (bounded) and leave without touching the lattice again
+    if (threadIdx.x == 0) {
+        atomicOr(status, 2);
+        for (int s = 0; s < 2; ++s) mbar_wait_bounded(&c.bar[s], 0);
+    }
+    cp_async_wait_all();
 }
 
 }  // namespace lbm

@@ -76,8 +76,9 @@ struct StorageOps {
     int m3_ty, m3_nsp;
     cudaError_t (*shell_gather)(const HostGeom &, int64_t pitch, const void *f, void *G, const ShellInfo &,
                                 cudaStream_t);
+    // tmap: CUtensorMap of f with a box of one direction of a 32 x m3_ty tile
     cudaError_t (*merged3)(const HostGeom &, int64_t pitch, bool force, void *f, const void *Gcur, void *Gnext,
-                           const ShellInfo &, cudaStream_t);
+                           const ShellInfo &, const void *tmap, int *status, cudaStream_t);
     // persistent plane-wavefront sweep (two time steps); sched points to a
     // WaveSchedule (device pointers inside), grid = number of CTAs
     cudaError_t (*wavefront)(const HostGeom &, int64_t pitch, bool force, void *f, const void *sched, int grid,
