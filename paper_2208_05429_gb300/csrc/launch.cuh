@@ -207,8 +207,16 @@ struct Launch {
         if (e != cudaSuccess) return e;
         CUtensorMap map;
         memcpy(&map, tmap, sizeof(map));
-        k_merged3<S, F, M3_TY><<<dim3(si.ntx, si.nty), M3<M3_TY>::THREADS, smem, st>>>(
-            map, make_geom<R>(h, pitch), make_dirs((T *)f, slot_of(h, pitch)), (const T *)Gc, (T *)Gn, si, status);
+        const Geom<R> g = make_geom<R>(h, pitch);
+        const Dirs<T> fd = make_dirs((T *)f, slot_of(h, pitch));
+        Dirs<T> fo = fd, go;
+        for (int i = 0; i < Q; ++i) {
+            fo.p[i] = fd.p[i] + g.noff[i];
+            go.p[i] = (T *)Gn + cz(i) * si.gplane + (int64_t)i * M3<M3_TY>::NSP;
+        }
+        k_merged3<S, F, M3_TY><<<dim3(si.ntx, si.nty), M3<M3_TY>::THREADS, smem, st>>>(map, g, fd, fo, go,
+                                                                                       (const T *)Gc, (T *)Gn, si,
+                                                                                       status);
         return cudaGetLastError();
     }
     static cudaError_t merged3(const HostGeom &h, int64_t pitch, bool force, void *f, const void *Gc, void *Gn,

@@ -117,9 +117,13 @@ TileInfo tile_info(const lbm_config &c)
 // The shadow-shell sweep serves MERGED with automatic tiles when z is not
 // periodic; an explicit tile height or a periodic z selects the snapshot
 // sweep (merged.cuh).
+ShellInfo shell_info(const lbm_config &c);
+
 bool uses_m3(const lbm_config &c)
 {
-    return c.variant == LBM_VARIANT_MERGED && c.tile_y == 0 && c.face_bc[4] != LBM_BC_PERIODIC;
+    if (c.variant != LBM_VARIANT_MERGED || c.tile_y != 0 || c.face_bc[4] == LBM_BC_PERIODIC) return false;
+    // the sweep indexes one shadow copy with 32-bit offsets
+    return (double)shell_info(c).gplane * (double)c.nz < 2147483647.0;
 }
 
 ShellInfo shell_info(const lbm_config &c)

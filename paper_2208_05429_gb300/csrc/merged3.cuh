@@ -181,6 +181,8 @@ struct M3Cta {
 
     const Geom<R> &g;
     const Dirs<T> &fd;
+    const Dirs<T> &fo;  // fd.p[i] + noff[i]: the push target of an interior cell
+    const Dirs<T> &go;  // Gn + cz(i) gplane + i NSP: the shadow target of direction i
     const T *__restrict__ Gc;
     T *__restrict__ Gn;
     const ShellInfo &si;
@@ -193,9 +195,10 @@ struct M3Cta {
     unsigned gmask, wxy, lxy;
     bool active, perx, pery, xybnd, timed_out;
 
-    __device__ __forceinline__ M3Cta(const Geom<R> &g_, const Dirs<T> &fd_, const T *Gc_, T *Gn_, const ShellInfo &si_,
-                                     const CUtensorMap *tmap_, unsigned char *smem_)
-        : g(g_), fd(fd_), Gc(Gc_), Gn(Gn_), si(si_), tmap(tmap_), smem(smem_)
+    __device__ __forceinline__ M3Cta(const Geom<R> &g_, const Dirs<T> &fd_, const Dirs<T> &fo_, const Dirs<T> &go_,
+                                     const T *Gc_, T *Gn_, const ShellInfo &si_, const CUtensorMap *tmap_,
+                                     unsigned char *smem_)
+        : g(g_), fd(fd_), fo(fo_), go(go_), Gc(Gc_), Gn(Gn_), si(si_), tmap(tmap_), smem(smem_)
     {
         ringm = reinterpret_cast<R *>(smem + SM::ring_off);
         ring0 = ringm + L::RSM * NDM * NPOS;
@@ -419,13 +422,14 @@ struct M3Cta {
     __device__ __forceinline__ void scatter(int k, const R (&s)[Q]) const
     {
         const int c = cxy + k * (int)g.plane;
-        T *const gk = Gn + k * si.gplane;
+        const int kg = k * (int)si.gplane;  // shadow sizes stay below 2^31 elements
+        T *const gk = Gn + kg;
         if (!xybnd && k > 0 && k < nz - 1) {
             static_for<Q>([&](auto K) {
                 constexpr int i = decltype(K)::value;
                 const T e = encode<S, i>(s[i]);
-                fd.p[i][c + g.noff[i]] = e;
-                if (gmask & (1u << i)) gk[cz(i) * si.gplane + gtab[pos + cx(i) + cy(i) * W] + i * NSP] = e;
+                fo.p[i][c] = e;
+                if (gmask & (1u << i)) go.p[i][kg + gtab[pos + cx(i) + cy(i) * W]] = e;
             });
         } else {
             const Faces fc = faces_of(g, x, y, k);
@@ -452,13 +456,13 @@ struct M3Cta {
 template <class S, bool FORCE, int TY>
 __global__ void __launch_bounds__(M3<TY>::THREADS, 1)
     k_merged3(const __grid_constant__ CUtensorMap tmap, Geom<typename S::R> g, Dirs<typename S::T> fd,
-              const typename S::T *__restrict__ Gc, typename S::T *__restrict__ Gn, ShellInfo si,
-              int *__restrict__ status)
+              Dirs<typename S::T> fo, Dirs<typename S::T> go, const typename S::T *__restrict__ Gc,
+              typename S::T *__restrict__ Gn, ShellInfo si, int *__restrict__ status)
 {
     using C = M3Cta<S, FORCE, TY>;
     using SM = typename C::SM;
     extern __shared__ __align__(128) unsigned char smem[];
-    C c(g, fd, Gc, Gn, si, &tmap, smem);
+    C c(g, fd, fo, go, Gc, Gn, si, &tmap, smem);
     int *abort_flag = reinterpret_cast<int *>(smem + SM::flag_off);
     const int nz = g.nz;
     if (threadIdx.x == 0) {
