@@ -152,7 +152,7 @@ struct Layout {
 
 // WAVEFRONT schedule words: entries (2 nz + 4), ticket, done[nz * ny] (at
 // most ny row blocks per plane).
-constexpr int WF_AHEAD_DEFAULT = 4;  // planes by which even steps lead odd steps
+constexpr int WF_AHEAD_DEFAULT = 3;  // planes by which even steps lead odd steps
 
 int64_t wf_ints(const lbm_config &c)
 {
@@ -381,7 +381,7 @@ static int wf_setup(lbm_handle *h, int ahead)
     if (e != cudaSuccess || e2 != cudaSuccess) return LBM_ECUDA;
     h->wf_nentries = n;
     h->wf_ahead = ahead;
-    int64_t item_cells = 4096;  // tunable through LBM_WAVEFRONT_ITEM_CELLS
+    int64_t item_cells = 2048;  // tunable through LBM_WAVEFRONT_ITEM_CELLS
     if (const char *env = getenv("LBM_WAVEFRONT_ITEM_CELLS")) {
         const long v = atol(env);
         if (v >= 32 && v <= (1L << 22)) item_cells = v;
@@ -391,8 +391,14 @@ static int wf_setup(lbm_handle *h, int ahead)
     h->wf_nrb = (int)((c.ny + h->wf_rb - 1) / h->wf_rb);
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) return LBM_ECUDA;
-    const int per = h->ops->wavefront_blocks_per_sm(h->force);
+    int per = h->ops->wavefront_blocks_per_sm(h->force);
     if (per <= 0) return LBM_ECUDA;
+    // CTAs per SM (resident items bound the planes in flight), tunable
+    // through LBM_WAVEFRONT_CTAS_PER_SM
+    if (const char *env = getenv("LBM_WAVEFRONT_CTAS_PER_SM")) {
+        const int v = atoi(env);
+        if (v >= 1 && v < per) per = v;
+    }
     const int64_t items = (int64_t)n * h->wf_nrb;
     h->wf_grid = (int)(items < (int64_t)sms * per ? items : (int64_t)sms * per);
     return LBM_OK;

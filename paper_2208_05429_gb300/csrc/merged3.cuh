@@ -216,11 +216,7 @@ struct M3Cta {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         role = warp < TY ? EVEN : (warp < 2 * TY ? ODD : HALO);
         hidx = 0;
-        if (role != HALO) {
-            lx = lane;
-            ly = role == EVEN ? warp : warp - TY;
-            active = lx < tw && ly < th;
-        } else {
+        if (role == HALO) {
             // halo ring: row -1, row th, column -1, column tw
             const int h = (warp - 2 * TY) * 32 + lane;
             hidx = h;
@@ -230,6 +226,22 @@ struct M3Cta {
             else if (h < 2 * W + TY) { lx = -1; ly = h - 2 * W; active = ly < th; }
             else if (h < 2 * W + 2 * TY) { lx = tw; ly = h - 2 * W - TY; active = ly < th; }
             else { lx = 0; ly = 0; active = false; }
+        } else if (role == EVEN || tw < 4 || th < 4) {
+            lx = lane;
+            ly = role == EVEN ? warp : warp - TY;
+            active = lx < tw && ly < th;
+        } else {
+            // odd warps take the cells in band order: the two outer rows on
+            // either side, then the two outer columns of the middle rows
+            // (every cell that can land a value on a shell cell), then the
+            // inner cells, so that whole warps skip the shadow stores
+            const int t = threadIdx.x - 32 * TY;
+            const int nrow = 4 * tw, nband = nrow + 4 * (th - 4);
+            active = t < tw * th;
+            if (!active) { lx = 0; ly = 0; }
+            else if (t < nrow) { const int r = t / tw; lx = t - r * tw; ly = r < 2 ? r : th - 4 + r; }
+            else if (t < nband) { const int u = t - nrow, j = u & 3; ly = 2 + (u >> 2); lx = j < 2 ? j : tw - 4 + j; }
+            else { const int v = t - nband, w = tw - 4; ly = 2 + v / w; lx = 2 + v % w; }
         }
         pos = (ly + 1) * W + (lx + 1);
         tc = role == HALO ? 0 : ly * 32 + lx;
@@ -425,12 +437,19 @@ struct M3Cta {
         const int kg = k * (int)si.gplane;  // shadow sizes stay below 2^31 elements
         T *const gk = Gn + kg;
         if (!xybnd && k > 0 && k < nz - 1) {
-            static_for<Q>([&](auto K) {
-                constexpr int i = decltype(K)::value;
-                const T e = encode<S, i>(s[i]);
-                fo.p[i][c] = e;
-                if (gmask & (1u << i)) go.p[i][kg + gtab[pos + cx(i) + cy(i) * W]] = e;
-            });
+            if (!gmask) {  // inner cells: no shell target
+                static_for<Q>([&](auto K) {
+                    constexpr int i = decltype(K)::value;
+                    fo.p[i][c] = encode<S, i>(s[i]);
+                });
+            } else {
+                static_for<Q>([&](auto K) {
+                    constexpr int i = decltype(K)::value;
+                    const T e = encode<S, i>(s[i]);
+                    fo.p[i][c] = e;
+                    if (gmask & (1u << i)) go.p[i][kg + gtab[pos + cx(i) + cy(i) * W]] = e;
+                });
+            }
         } else {
             const Faces fc = faces_of(g, x, y, k);
             static_for<Q>([&](auto K) {
