@@ -4,9 +4,19 @@
 Workload (the benchmark configuration): lid-driven cavity 256^3, D3Q19 BGK,
 tau = 0.55, lid u = (0.05, 0, 0) on the z+ face, half-way bounce-back on the
 other five faces, fluid at rest at t = 0; FP32 storage and arithmetic; the
-two-step merged single-copy schedule.  One benchmark step = one merged sweep
-= two lattice time steps over all 16.8 M cells.  MLUPS counts every cell as a
-fluid node (million lattice-node updates per second).
+single-copy AA schedule by default (--variant selects the two-step merged
+sweep, the plane wavefront or two lattices; the other schedules and storage
+formats are reported under "variants").  One benchmark step = two lattice
+time steps over all 16.8 M cells (one merged sweep, or an AA even/odd pair).
+MLUPS counts every cell as a fluid node (million lattice-node updates per
+second).
+
+Two further modes print their own JSON line instead of the benchmark line:
+``--sweep`` (cavity cubes 64^3 .. 768^3, FP32 and FP16-shifted storage, AA
+and merged, plus the host oracle at 64^3 and 128^3) and
+``--precision-study`` (periodic Taylor-Green box 512^3, U0 = 0.04, tau =
+0.52: FP32 / FP16 / BF16 storage against an FP64 run of the same case,
+kinetic energy every 100 steps and max-norm velocity error).
 
 Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs an
 independent replica on its own GPU (the update shards only through a halo
@@ -61,6 +71,11 @@ def parse():
     p.add_argument("--tile-y", type=int, default=0)
     p.add_argument("--no-extras", action="store_true", help="skip the per-variant, adjoint and CPU legs")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle baseline")
+    p.add_argument("--sweep", action="store_true", help="cavity size sweep (prints its own JSON line)")
+    p.add_argument("--sweep-sizes", default="64,128,256,512,768")
+    p.add_argument("--precision-study", action="store_true", help="512^3 Taylor-Green precision study")
+    p.add_argument("--study-size", type=int, default=512)
+    p.add_argument("--study-steps", type=int, default=2000)
     return p.parse_args()
 
 
@@ -155,6 +170,24 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max_mhz,
                 "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def slowest_rank_ms(ms, dist_on, device):
+    """The timed region's length on the slowest rank (max over ranks)."""
+    if not dist_on:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world, cells, steps, ms):
+    """Whole-job throughput of `world` independent replicas, each running
+    `steps` bench steps (two time steps each) of a `cells`-cell lattice in the
+    slowest rank's `ms`."""
+    return world * cells * 2 * steps / (ms * 1e3)
 
 
 def sync_all(dist_on):
@@ -367,10 +400,106 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ main
 
+def sweep(args):
+    """Cavity size sweep: MLUPS and fraction of the measured HBM peak per
+    size, storage and schedule (about 500 time steps each, at least ~1 s),
+    and the host oracle at 64^3 and 128^3."""
+    import torch
+    from paper_2208_05429_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    peak, peak_kind = measured_peaks()
+    rows = []
+    for n in [int(v) for v in args.sweep_sizes.split(",")]:
+        cells = n ** 3
+        for st in ("f32", "f16s"):
+            for var in ("aa", "merged"):
+                steps = max(20, min(250, int(2e9 / (cells * 2 * 1.0))))  # ~1-2 s at 30-60k MLUPS
+                try:
+                    ms, prof, lat = time_variant(n, st, var, steps, 3)
+                    ok = abs(lat.reduce()[0] - cells) / cells < 1e-4
+                    del lat
+                    torch.cuda.empty_cache()
+                except Exception as e:  # e.g. out of memory at the largest sizes
+                    rows.append({"n": n, "storage": st, "variant": var, "error": repr(e)[:200]})
+                    continue
+                dk = {"merged": "merged", "aa": "aa_odd"}[var]
+                r = roofline_of(prof, dk, st, cells, peak, peak_kind)
+                rows.append({"n": n, "storage": st, "variant": var, "time_steps": 2 * steps,
+                             "MLUPS": round(cells * 2 * steps / (ms * 1e3), 1),
+                             "kernel": dk, "kernel_frac_of_peak": r["frac"] if r else None,
+                             "kernel_GBs_alg": r["achieved"] if r else None, "mass_conserved": bool(ok)})
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    import oracle
+    oracle.build()
+    cpu = []
+    for n in (64, 128):
+        rate, done, el = oracle_mlups(n, 5.0)
+        cpu.append({"n": n, "MLUPS": round(rate, 2), "time_steps": done, "seconds": round(el, 2),
+                    "threads": omp_threads()})
+    print(json.dumps({"mode": "sweep", "workload": "lid-driven cavity n^3, tau 0.55, lid (0.05,0,0)",
+                      "peak_GBs": peak, "peak_source": peak_kind, "gpu": rows, "cpu_oracle": cpu}), flush=True)
+    return 0
+
+
+def precision_study(args):
+    """Periodic Taylor-Green box: each storage format against an FP64 run of
+    the same case (AA schedule, FP32 arithmetic for the 4- and 2-byte formats)."""
+    import numpy as np
+    import torch
+    from paper_2208_05429_gb300 import build, inputs
+    from paper_2208_05429_gb300.lbm import Lattice
+    build.build()
+    torch.cuda.set_device(0)
+    n, steps, tau, U0 = args.study_size, args.study_steps, 0.52, 0.04
+    u0 = torch.tensor(inputs.taylor_green_velocity(n, n, n, U0), dtype=torch.float32, device="cuda")
+    every = 100
+
+    def run(storage):
+        lat = Lattice((n, n, n), tau, storage=storage, variant="aa")
+        lat.init_equilibrium(None, u0)
+        ke = []
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        for t in range(0, steps, every):
+            ev0.record(lat.stream)
+            lat.step(min(every, steps - t))
+            ev1.record(lat.stream)
+            ev1.synchronize()
+            ms += ev0.elapsed_time(ev1)
+            ke.append(lat.reduce()[4])
+        _, u = lat.moments(torch.float64 if storage == "f64" else torch.float32)
+        del lat
+        torch.cuda.empty_cache()
+        return u, np.array(ke), ms
+
+    u_ref, ke_ref, ms_ref = run("f64")
+    umax = float(u_ref.abs().max())
+    out = {"f64": {"MLUPS": round(n ** 3 * steps / (ms_ref * 1e3), 1), "KE_final": float(ke_ref[-1])}}
+    for st in ("f32", "f16s", "bf16s"):
+        u, ke, ms = run(st)
+        err = float((u.double() - u_ref).abs().max()) / umax
+        out[st] = {"MLUPS": round(n ** 3 * steps / (ms * 1e3), 1), "u_maxnorm_rel_err": err,
+                   "KE_rel_err_final": float(abs(ke[-1] - ke_ref[-1]) / ke_ref[-1]),
+                   "KE_rel_err_max": float(np.max(np.abs(ke - ke_ref) / ke_ref))}
+        del u
+        torch.cuda.empty_cache()
+    out["speedup_f16s_vs_f32"] = round(out["f16s"]["MLUPS"] / out["f32"]["MLUPS"], 3)
+    out["speedup_bf16s_vs_f32"] = round(out["bf16s"]["MLUPS"] / out["f32"]["MLUPS"], 3)
+    print(json.dumps({"mode": "precision_study",
+                      "workload": f"periodic Taylor-Green {n}^3, U0 {U0}, tau {tau}, {steps} steps, AA schedule",
+                      "KE_every": every, "KE_f64": [float(v) for v in ke_ref], "results": out}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return sweep(args)
+    if args.precision_study:
+        return precision_study(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -399,17 +528,13 @@ def main():
     sampler.start()
     ms, prof, lat = time_variant(n, args.storage, args.variant, args.steps, args.warmup, dist_on, args.tile_y)
     clocks = sampler.stop()
-    if dist_on:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = slowest_rank_ms(ms, dist_on, "cuda")
     # mass check of the timed state: a broken kernel shows up here
     mass = lat.reduce()[0]
     ok = abs(mass - cells) / cells < 1e-5
     del lat
 
-    value = world * cells * 2 * args.steps / (ms * 1e3)
+    value = whole_job_mlups(world, cells, args.steps, ms)
     dominant = {"merged": "merged", "wavefront": "wavefront", "aa": "aa_odd"}.get(args.variant, "two_lattice")
     roof = roofline_of(prof, dominant, args.storage, cells, peak, peak_kind)
     launches = sum(v[0] for v in prof.values())
