@@ -414,9 +414,19 @@ def sweep(args):
         cells = n ** 3
         for st in ("f32", "f16s"):
             for var in ("aa", "merged"):
-                steps = max(20, min(250, int(2e9 / (cells * 2 * 1.0))))  # ~1-2 s at 30-60k MLUPS
+                steps = max(64, min(2000, int(4e10 / (cells * 2))))  # ~0.5-1 s at 40-60k MLUPS
                 try:
-                    ms, prof, lat = time_variant(n, st, var, steps, 3)
+                    # kernel fraction from a short profiled run (one launch per call) ...
+                    _, prof, lat = time_variant(n, st, var, 5, 3)
+                    # ... and MLUPS from one step(n) call, which replays captured CUDA graphs
+                    lat.step(64)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(lat.stream)
+                    lat.step(2 * steps)
+                    e1.record(lat.stream)
+                    e1.synchronize()
+                    ms = e0.elapsed_time(e1)
                     ok = abs(lat.reduce()[0] - cells) / cells < 1e-4
                     del lat
                     torch.cuda.empty_cache()

@@ -153,16 +153,15 @@ struct Launch {
         const Dirs<T> fd = make_dirs((T *)f, slot_of(h, pitch));
         CUtensorMap map;
         memcpy(&map, tmap, sizeof(map));
-        cudaError_t e;
-        if (force) {
-            e = cudaFuncSetAttribute(k_merged<S, true, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        static bool attr_set[2] = {false, false};  // once per process: not inside a stream capture
+        if (!attr_set[force]) {
+            const cudaError_t e = cudaFuncSetAttribute(force ? k_merged<S, true, TX, TY> : k_merged<S, false, TX, TY>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            k_merged<S, true, TX, TY><<<grid, block, smem, st>>>(map, g, fd, (const R *)G, ti, status);
-        } else {
-            e = cudaFuncSetAttribute(k_merged<S, false, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            k_merged<S, false, TX, TY><<<grid, block, smem, st>>>(map, g, fd, (const R *)G, ti, status);
+            attr_set[force] = true;
         }
+        if (force) k_merged<S, true, TX, TY><<<grid, block, smem, st>>>(map, g, fd, (const R *)G, ti, status);
+        else k_merged<S, false, TX, TY><<<grid, block, smem, st>>>(map, g, fd, (const R *)G, ti, status);
         return cudaGetLastError();
     }
     static cudaError_t merged(const HostGeom &h, int64_t pitch, bool force, void *f, const void *G,
@@ -202,9 +201,13 @@ struct Launch {
                                  const ShellInfo &si, const void *tmap, int *status, cudaStream_t st)
     {
         constexpr size_t smem = M3L::bytes;
-        cudaError_t e = cudaFuncSetAttribute(k_merged3<S, F, M3_TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
+        static bool attr_set = false;  // once per process: not inside a stream capture
+        if (!attr_set) {
+            const cudaError_t e = cudaFuncSetAttribute(k_merged3<S, F, M3_TY>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
         CUtensorMap map;
         memcpy(&map, tmap, sizeof(map));
         const Geom<R> g = make_geom<R>(h, pitch);

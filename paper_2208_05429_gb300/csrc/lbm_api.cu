@@ -37,6 +37,22 @@ struct lbm_handle {
     void *G3[2];       // shadow of the tile shells: current / next
     int g3cur;
     bool g3fresh;      // G3[g3cur] mirrors the shell cells of f
+    // cached CUDA graph of GRAPH_STEPS time steps from state gfrom to gto,
+    // captured and replayed on an internal stream ordered after / before the
+    // handle's stream with an event (the legacy default stream cannot be
+    // captured)
+    cudaGraphExec_t gexec;
+    cudaStream_t gstream;
+    cudaEvent_t gev;
+    struct StepState {
+        int parity, g3cur;
+        bool g3fresh;
+        void *f, *f2;
+        bool operator==(const StepState &o) const
+        {
+            return parity == o.parity && g3cur == o.g3cur && g3fresh == o.g3fresh && f == o.f && f2 == o.f2;
+        }
+    } gfrom, gto;
     CUtensorMap tmap;  // TMA descriptor of f (MERGED)
     int *status;       // device status word: bits 2 / 4 = a bounded wait gave up
     int *wf_words;     // WAVEFRONT schedule (device): entries, ticket, done flags
@@ -58,6 +74,21 @@ struct lbm_handle {
     void *adj_work;
     size_t adj_bytes;
 };
+
+static void drop_graph(lbm_handle *h)
+{
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+}
+
+static void free_graph_stream(lbm_handle *h)
+{
+    drop_graph(h);
+    if (h->gev) cudaEventDestroy(h->gev);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
+    h->gev = nullptr;
+    h->gstream = nullptr;
+}
 
 namespace {
 
@@ -509,6 +540,8 @@ void lbm_destroy(lbm_handle *h)
     {
         DeviceGuard g(h->device);
         cudaStreamSynchronize(h->stream);
+        if (h->gstream) cudaStreamSynchronize(h->gstream);
+        free_graph_stream(h);
         if (h->owns && h->base) cudaFree(h->base);
         if (h->ev_pool)
             for (cudaEvent_t e : *h->ev_pool) cudaEventDestroy(e);
@@ -561,15 +594,13 @@ int lbm_set_force(lbm_handle *h, const float *F)
     if (h->cfg.force_mode != LBM_FORCE_FIELD) return LBM_ESTATE;
     h->hg.Ff = F;
     h->force_set = true;
+    drop_graph(h);  // captured launches hold the old force pointer
     return LBM_OK;
 }
 
-int lbm_step(lbm_handle *h, int64_t n)
+// Enqueue n time steps with direct launches.
+static int step_units(lbm_handle *h, int64_t n)
 {
-    if (!h || n < 0) return LBM_EINVAL;
-    if (!h->force_set) return LBM_ESTATE;
-    DeviceGuard g(h->device);
-    if (!g.ok) return LBM_ECUDA;
     const StorageOps &o = *h->ops;
     while (n > 0) {
         switch (h->cfg.variant) {
@@ -653,6 +684,95 @@ int lbm_step(lbm_handle *h, int64_t n)
         }
     }
     return LBM_OK;
+}
+
+static lbm_handle::StepState step_state(const lbm_handle *h)
+{
+    lbm_handle::StepState st;
+    st.parity = h->parity;
+    st.g3cur = h->g3cur;
+    st.g3fresh = h->g3fresh;
+    st.f = h->f;
+    st.f2 = h->f2;
+    return st;
+}
+
+static void set_step_state(lbm_handle *h, const lbm_handle::StepState &st)
+{
+    h->parity = st.parity;
+    h->g3cur = st.g3cur;
+    h->g3fresh = st.g3fresh;
+    h->f = st.f;
+    h->f2 = st.f2;
+}
+
+// Time steps per graph replay.  Long step(n) calls replay one captured
+// block of launches instead of launching every kernel from the host.
+constexpr int64_t GRAPH_STEPS = 32;
+
+int lbm_step(lbm_handle *h, int64_t n)
+{
+    if (!h || n < 0) return LBM_EINVAL;
+    if (!h->force_set) return LBM_ESTATE;
+    DeviceGuard g(h->device);
+    if (!g.ok) return LBM_ECUDA;
+    if (n < GRAPH_STEPS || h->prof_on) return step_units(h, n);
+    if (!h->gstream) {
+        if (cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->gev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            free_graph_stream(h);
+            return step_units(h, n);
+        }
+    }
+    // the graph stream starts after everything already on the handle's stream
+    CK(cudaEventRecord(h->gev, h->stream));
+    CK(cudaStreamWaitEvent(h->gstream, h->gev, 0));
+    cudaStream_t user = h->stream;
+    int rc = LBM_OK;
+    while (n >= GRAPH_STEPS) {
+        const lbm_handle::StepState from = step_state(h);
+        if (h->gexec && h->gfrom == from) {
+            if (cudaGraphLaunch(h->gexec, h->gstream) != cudaSuccess) { rc = LBM_ECUDA; break; }
+            set_step_state(h, h->gto);
+            h->t += GRAPH_STEPS;
+            n -= GRAPH_STEPS;
+            continue;
+        }
+        // capture one block on the graph stream; on any failure fall back to
+        // direct launches
+        const int64_t t0 = h->t;
+        if (cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            break;
+        }
+        h->stream = h->gstream;
+        const int urc = step_units(h, GRAPH_STEPS);
+        h->stream = user;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(h->gstream, &graph);
+        cudaGraphExec_t exec = nullptr;
+        if (urc != LBM_OK || ec != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            set_step_state(h, from);
+            h->t = t0;
+            break;
+        }
+        cudaGraphDestroy(graph);
+        const cudaError_t el = cudaGraphLaunch(exec, h->gstream);
+        drop_graph(h);
+        h->gexec = exec;
+        h->gfrom = from;
+        h->gto = step_state(h);
+        if (el != cudaSuccess) { rc = LBM_ECUDA; break; }
+        n -= GRAPH_STEPS;
+    }
+    // the handle's stream continues after the replays
+    CK(cudaEventRecord(h->gev, h->gstream));
+    CK(cudaStreamWaitEvent(h->stream, h->gev, 0));
+    if (rc != LBM_OK) return rc;
+    return step_units(h, n);
 }
 
 int lbm_time(const lbm_handle *h, int64_t *t)

@@ -54,6 +54,7 @@ struct M3 {
     static constexpr int RSM = 3, RS0 = 3, RSP = 4;
     static constexpr int NRING = RSM * NDM + RS0 * ND0 + RSP * NDP;
     static constexpr int SREST = 3, SZP = 4, SZM = 3;
+    static constexpr int NTS = 33 * TY;  // small-ring slot size (pitch 33)
     static_assert(TY >= 2, "bands of at least two rows");
     static_assert(THREADS <= 1024, "one CTA");
 };
@@ -72,7 +73,7 @@ struct M3Smem {
     static constexpr size_t stage_off = 0;
     static constexpr size_t ring_off = 2 * slot_bytes;
     static constexpr size_t small_off = ring_off + (size_t)L::NRING * L::NPOS * sizeof(R);
-    static constexpr size_t gtab_off = small_off + (size_t)(L::SREST + L::SZP + L::SZM) * L::NT * sizeof(R);
+    static constexpr size_t gtab_off = small_off + (size_t)(L::SREST + L::SZP + L::SZM) * L::NTS * sizeof(R);
     static constexpr size_t bar_off = (gtab_off + (size_t)L::NPOS * sizeof(int) + 15) / 16 * 16;
     static constexpr size_t flag_off = bar_off + 2 * sizeof(uint64_t);
     static constexpr size_t bytes = flag_off + 16;
@@ -204,8 +205,8 @@ struct M3Cta {
         ring0 = ringm + L::RSM * NDM * NPOS;
         ringp = ring0 + L::RS0 * ND0 * NPOS;
         srest = reinterpret_cast<R *>(smem + SM::small_off);
-        szp = srest + L::SREST * NT;
-        szm = szp + L::SZP * NT;
+        szp = srest + L::SREST * L::NTS;
+        szm = szp + L::SZP * L::NTS;
         gtab = reinterpret_cast<int *>(smem + SM::gtab_off);
         bar = reinterpret_cast<uint64_t *>(smem + SM::bar_off);
         nx = g.nx; ny = g.ny; nz = g.nz;
@@ -226,9 +227,22 @@ struct M3Cta {
             else if (h < 2 * W + TY) { lx = -1; ly = h - 2 * W; active = ly < th; }
             else if (h < 2 * W + 2 * TY) { lx = tw; ly = h - 2 * W - TY; active = ly < th; }
             else { lx = 0; ly = 0; active = false; }
-        } else if (role == EVEN || tw < 4 || th < 4) {
+        } else if (role == EVEN) {
+            // even warps: the shell cells in shadow-slot order (their inputs
+            // sit side by side in the stage), then the inner cells row by row
+            const int t = threadIdx.x;
+            if (t < L::NS) {
+                active = shell_cell<TY>(t, tw, th, lx, ly);
+                if (!active) { lx = 0; ly = 0; }
+            } else {
+                const int v = t - L::NS, w = tw - 2;
+                active = w > 0 && th > 2 && v < w * (th - 2);
+                if (active) { ly = 1 + v / w; lx = 1 + v % w; }
+                else { lx = 0; ly = 0; }
+            }
+        } else if (tw < 4 || th < 4) {
             lx = lane;
-            ly = role == EVEN ? warp : warp - TY;
+            ly = warp - TY;
             active = lx < tw && ly < th;
         } else {
             // odd warps take the cells in band order: the two outer rows on
@@ -244,7 +258,7 @@ struct M3Cta {
             else { const int v = t - nband, w = tw - 4; ly = 2 + v / w; lx = 2 + v % w; }
         }
         pos = (ly + 1) * W + (lx + 1);
-        tc = role == HALO ? 0 : ly * 32 + lx;
+        tc = role == HALO ? 0 : ly * 33 + lx;  // pitch 33 spreads a column over the banks
         x = x0 + lx; y = y0 + ly;
         if (role == HALO && active) {  // wrap the halo cell into the domain, or drop it (wall)
             if (x < 0 || x >= nx) { if (perx) x = x < 0 ? x + nx : x - nx; else active = false; }
@@ -390,9 +404,9 @@ struct M3Cta {
             const R v = roundtrip<S, i>(s[i]);
             if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P) ring_at<gg>(q, gidx(i))[pos] = v;
             else if (role == EVEN) {
-                if constexpr (i == 0) srest[slot(q, L::SREST) * NT + tc] = v;
-                else if constexpr (i == DIR_ZP) szp[slot(q, L::SZP) * NT + tc] = v;
-                else szm[slot(q, L::SZM) * NT + tc] = v;
+                if constexpr (i == 0) srest[slot(q, L::SREST) * L::NTS + tc] = v;
+                else if constexpr (i == DIR_ZP) szp[slot(q, L::SZP) * L::NTS + tc] = v;
+                else szm[slot(q, L::SZM) * L::NTS + tc] = v;
             }
         });
     }
@@ -405,9 +419,9 @@ struct M3Cta {
         const bool zlo = k == 0, zhi = k == nz - 1;
         const unsigned wm = wxy | (zlo ? CZM : 0u) | (zhi ? CZP : 0u);
         R s[Q];
-        s[0] = srest[slot(k, L::SREST) * NT + tc];
-        s[DIR_ZP] = zlo ? szm[slot(k, L::SZM) * NT + tc] : szp[slot(k - 1, L::SZP) * NT + tc];
-        s[DIR_ZM] = zhi ? szp[slot(k, L::SZP) * NT + tc] : szm[slot(k + 1, L::SZM) * NT + tc];
+        s[0] = srest[slot(k, L::SREST) * L::NTS + tc];
+        s[DIR_ZP] = zlo ? szm[slot(k, L::SZM) * L::NTS + tc] : szp[slot(k - 1, L::SZP) * L::NTS + tc];
+        s[DIR_ZM] = zhi ? szp[slot(k, L::SZP) * L::NTS + tc] : szm[slot(k + 1, L::SZM) * L::NTS + tc];
         if (!wm) {
             static_for<Q>([&](auto K) {
                 constexpr int i = decltype(K)::value;
