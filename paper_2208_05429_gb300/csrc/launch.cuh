@@ -196,14 +196,14 @@ struct Launch {
                                                          make_dirs((const T *)f, slot_of(h, pitch)), (T *)G, si);
         return cudaGetLastError();
     }
-    template <bool F>
+    template <bool F, bool PZ>
     static cudaError_t merged3_f(const HostGeom &h, int64_t pitch, void *f, const void *Gc, void *Gn,
-                                 const ShellInfo &si, const void *tmap, int *status, cudaStream_t st)
+                                 const ShellInfo &si, void *zsave, const void *tmap, int *status, cudaStream_t st)
     {
         constexpr size_t smem = M3L::bytes;
         static bool attr_set = false;  // once per process: not inside a stream capture
         if (!attr_set) {
-            const cudaError_t e = cudaFuncSetAttribute(k_merged3<S, F, M3_TY>,
+            const cudaError_t e = cudaFuncSetAttribute(k_merged3<S, F, M3_TY, PZ>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             attr_set = true;
@@ -217,16 +217,17 @@ struct Launch {
             fo.p[i] = fd.p[i] + g.noff[i];
             go.p[i] = (T *)Gn + cz(i) * si.gplane + (int64_t)i * M3<M3_TY>::NSP;
         }
-        k_merged3<S, F, M3_TY><<<dim3(si.ntx, si.nty), M3<M3_TY>::THREADS, smem, st>>>(map, g, fd, fo, go,
-                                                                                       (const T *)Gc, (T *)Gn, si,
-                                                                                       status);
+        k_merged3<S, F, M3_TY, PZ><<<dim3(si.ntx, si.nty), M3<M3_TY>::THREADS, smem, st>>>(
+            map, g, fd, fo, go, (const T *)Gc, (T *)Gn, si, (R *)zsave, status);
         return cudaGetLastError();
     }
     static cudaError_t merged3(const HostGeom &h, int64_t pitch, bool force, void *f, const void *Gc, void *Gn,
-                               const ShellInfo &si, const void *tmap, int *status, cudaStream_t st)
+                               const ShellInfo &si, void *zsave, const void *tmap, int *status, cudaStream_t st)
     {
-        return force ? merged3_f<true>(h, pitch, f, Gc, Gn, si, tmap, status, st)
-                     : merged3_f<false>(h, pitch, f, Gc, Gn, si, tmap, status, st);
+        if (h.per[2]) return force ? merged3_f<true, true>(h, pitch, f, Gc, Gn, si, zsave, tmap, status, st)
+                                   : merged3_f<false, true>(h, pitch, f, Gc, Gn, si, zsave, tmap, status, st);
+        return force ? merged3_f<true, false>(h, pitch, f, Gc, Gn, si, zsave, tmap, status, st)
+                     : merged3_f<false, false>(h, pitch, f, Gc, Gn, si, zsave, tmap, status, st);
     }
     static cudaError_t wavefront(const HostGeom &h, int64_t pitch, bool force, void *f, const void *sched, int grid,
                                  cudaStream_t st)
@@ -303,6 +304,7 @@ StorageOps make_ops()
     o.merged = &L::merged;
     o.m3_ty = L::M3_TY;
     o.m3_nsp = M3<L::M3_TY>::NSP;
+    o.m3_zsave = M3<L::M3_TY>::ZSAVE;
     o.shell_gather = &L::shell_gather;
     o.merged3 = &L::merged3;
     o.adjoint = &L::adjoint;

@@ -35,6 +35,7 @@ struct lbm_handle {
     bool m3;           // MERGED runs the shadow-shell sweep
     ShellInfo si;
     void *G3[2];       // shadow of the tile shells: current / next
+    void *Z3;          // periodic z: per-tile values of the image planes
     int g3cur;
     bool g3fresh;      // G3[g3cur] mirrors the shell cells of f
     // cached CUDA graph of GRAPH_STEPS time steps from state gfrom to gto,
@@ -145,14 +146,15 @@ TileInfo tile_info(const lbm_config &c)
     return ti;
 }
 
-// The shadow-shell sweep serves MERGED with automatic tiles when z is not
-// periodic; an explicit tile height or a periodic z selects the snapshot
-// sweep (merged.cuh).
+// The shadow-shell sweep serves MERGED with automatic tiles (and at least
+// two planes when z is periodic); an explicit tile height selects the
+// snapshot sweep (merged.cuh).
 ShellInfo shell_info(const lbm_config &c);
 
 bool uses_m3(const lbm_config &c)
 {
-    if (c.variant != LBM_VARIANT_MERGED || c.tile_y != 0 || c.face_bc[4] == LBM_BC_PERIODIC) return false;
+    if (c.variant != LBM_VARIANT_MERGED || c.tile_y != 0) return false;
+    if (c.face_bc[4] == LBM_BC_PERIODIC && c.nz < 2) return false;
     // the sweep indexes one shadow copy with 32-bit offsets
     return (double)shell_info(c).gplane * (double)c.nz < 2147483647.0;
 }
@@ -178,7 +180,7 @@ int64_t ghost_elems(const lbm_config &c)
 }
 
 struct Layout {
-    size_t f, f2, G, G3, wf, partial, red_out, flag, status, total;
+    size_t f, f2, G, G3, Z3, wf, partial, red_out, flag, status, total;
 };
 
 // WAVEFRONT schedule words: entries (2 nz + 4), ticket, done[nz * ny] (at
@@ -225,6 +227,11 @@ Layout layout_of(const lbm_config &c)
     L.G = off; off += align_up((size_t)ghost_elems(c) * real_size_of(c.storage));
     L.G3 = off;
     if (uses_m3(c)) off += 2 * align_up((size_t)(shell_info(c).gplane * c.nz) * es);
+    L.Z3 = off;
+    if (uses_m3(c) && c.face_bc[4] == LBM_BC_PERIODIC) {
+        const ShellInfo si = shell_info(c);
+        off += align_up((size_t)si.ntx * si.nty * ops_for(c.storage)->m3_zsave * real_size_of(c.storage));
+    }
     L.wf = off; off += align_up((size_t)wf_ints(c) * sizeof(int));
     L.partial = off; off += align_up(sizeof(double) * 5 * RED_BLOCKS_MAX);
     L.red_out = off; off += align_up(sizeof(double) * 5);
@@ -482,6 +489,7 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
         const size_t gbytes = align_up((size_t)(h->si.gplane * cfg->nz) * elem_size_of(cfg->storage));
         h->G3[0] = b + L.G3;
         h->G3[1] = b + L.G3 + gbytes;
+        h->Z3 = cfg->face_bc[4] == LBM_BC_PERIODIC ? b + L.Z3 : nullptr;
     }
     h->g3cur = 0;
     h->g3fresh = false;
@@ -664,7 +672,7 @@ static int step_units(lbm_handle *h, int64_t n)
                 }
                 CK(timed(h, LBM_KERNEL_MERGED, [&] {
                     return o.merged3(h->hg, h->nxp, h->force, h->f, h->G3[h->g3cur], h->G3[h->g3cur ^ 1], h->si,
-                                     &h->tmap, h->status, h->stream);
+                                     h->Z3, &h->tmap, h->status, h->stream);
                 }));
                 h->g3cur ^= 1;
                 n -= 2; h->t += 2;

@@ -55,6 +55,10 @@ struct M3 {
     static constexpr int NRING = RSM * NDM + RS0 * ND0 + RSP * NDP;
     static constexpr int SREST = 3, SZP = 4, SZM = 3;
     static constexpr int NTS = 33 * TY;  // small-ring slot size (pitch 33)
+    // periodic z: per tile, the values of planes -1 and 0 kept for the end of
+    // the march (16 ring directions at every position, rest and pure z)
+    static constexpr int NXY = 16;
+    static constexpr int ZSAVE = 2 * (NXY * NPOS + 3 * NTS);
     static_assert(TY >= 2, "bands of at least two rows");
     static_assert(THREADS <= 1024, "one CTA");
 };
@@ -169,7 +173,16 @@ __host__ __device__ constexpr unsigned z_bits(int sign)
     return m;
 }
 
-template <class S, bool FORCE, int TY>
+// Index of an xy-moving direction among the 16 (ring directions).
+__host__ __device__ constexpr int xyidx(int i)
+{
+    int n = 0;
+    for (int j = 0; j < i; ++j)
+        if (grp(j) == GRP_M || grp(j) == GRP_0 || grp(j) == GRP_P) ++n;
+    return n;
+}
+
+template <class S, bool FORCE, int TY, bool PERZ>
 struct M3Cta {
     using R = typename S::R;
     using T = typename S::T;
@@ -188,6 +201,7 @@ struct M3Cta {
     T *__restrict__ Gn;
     const ShellInfo &si;
     const CUtensorMap *tmap;
+    R *zsave;  // periodic z: this tile's save area (ZSAVE elements), else null
     unsigned char *smem;
     R *ringm, *ring0, *ringp, *srest, *szp, *szm;
     int *gtab;
@@ -195,9 +209,11 @@ struct M3Cta {
     int role, x0, y0, tw, th, lx, ly, x, y, pos, tc, hidx, nx, ny, nz, goff, cxy, inoff, sub;
     unsigned gmask, wxy, lxy;
     bool active, perx, pery, xybnd, timed_out;
+    static constexpr bool perz = PERZ;
+    static constexpr int zoff = PERZ ? 1 : 0;  // periodic z: the march starts at the image plane -1
 
     __device__ __forceinline__ M3Cta(const Geom<R> &g_, const Dirs<T> &fd_, const Dirs<T> &fo_, const Dirs<T> &go_,
-                                     const T *Gc_, T *Gn_, const ShellInfo &si_, const CUtensorMap *tmap_,
+                                     const T *Gc_, T *Gn_, const ShellInfo &si_, const CUtensorMap *tmap_, R *zs,
                                      unsigned char *smem_)
         : g(g_), fd(fd_), fo(fo_), go(go_), Gc(Gc_), Gn(Gn_), si(si_), tmap(tmap_), smem(smem_)
     {
@@ -211,6 +227,7 @@ struct M3Cta {
         bar = reinterpret_cast<uint64_t *>(smem + SM::bar_off);
         nx = g.nx; ny = g.ny; nz = g.nz;
         perx = g.per[0] != 0; pery = g.per[1] != 0;
+        zsave = PERZ ? zs + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * L::ZSAVE : nullptr;
         x0 = 32 * blockIdx.x;
         tw = min(32, nx - x0);
         band_of(si, blockIdx.y, y0, th);
@@ -328,23 +345,35 @@ struct M3Cta {
         else if constexpr (GG == GRP_0) return ring0 + (slot(plane, L::RS0) * ND0 + gi) * NPOS;
         else return ringp + (slot(plane, L::RSP) * NDP + gi) * NPOS;
     }
-    __device__ __forceinline__ T *tile_block(int q) const { return reinterpret_cast<T *>(smem + (q & 1) * SM::slot_bytes); }
+    // Planes of the march are virtual: with periodic z they run from the
+    // image -1 of plane nz-1 to the image nz of plane 0.  Stage slots count
+    // the loaded planes u = q + zoff.
+    __device__ __forceinline__ int phys(int q) const
+    {
+        if constexpr (PERZ) return q < 0 ? q + nz : (q >= nz ? q - nz : q);
+        else return q;
+    }
+    __device__ __forceinline__ T *tile_block(int q) const
+    {
+        return reinterpret_cast<T *>(smem + ((q + zoff) & 1) * SM::slot_bytes);
+    }
     __device__ __forceinline__ unsigned char *halo_block(int q) const
     {
-        return smem + (q & 1) * SM::slot_bytes + SM::tile_bytes;
+        return smem + ((q + zoff) & 1) * SM::slot_bytes + SM::tile_bytes;
     }
 
     // Halo warps: start the copies of plane q into its stage slot.
     __device__ __forceinline__ void issue_stage(int q)
     {
-        uint64_t *b = &bar[q & 1];
+        uint64_t *b = &bar[(q + zoff) & 1];
         T *tb = tile_block(q);
+        const int pz = phys(q);
         if (hidx == 0) {
             mbar_arrive_expect_tx(b, SM::tma_bytes);
-            for (int d = 0; d < Q; ++d) tma_load_4d(tb + d * DST, tmap, x0, y0, q, d, b);
+            for (int d = 0; d < Q; ++d) tma_load_4d(tb + d * DST, tmap, x0, y0, pz, d, b);
         }
         // the tile's own shell cells: 16-byte chunks of its shadow rows
-        const T *gs = Gc + q * si.gplane + (int64_t)(blockIdx.y * si.ntx + blockIdx.x) * Q * NSP;
+        const T *gs = Gc + pz * si.gplane + (int64_t)(blockIdx.y * si.ntx + blockIdx.x) * Q * NSP;
         for (int ch = hidx; ch < Q * SM::CHUNKS; ch += NHT) {
             const int d = ch / SM::CHUNKS, j = ch - d * SM::CHUNKS;
             cp_async<16>(reinterpret_cast<unsigned char *>(tb + d * DST + NT) + 16 * j,
@@ -352,7 +381,7 @@ struct M3Cta {
         }
         // this thread's halo cell: the copy unit holding each direction
         if (active) {
-            const T *hs = Gc + q * si.gplane + (goff - sub);
+            const T *hs = Gc + pz * si.gplane + (goff - sub);
             unsigned char *hb = halo_block(q) + hidx * CP;
             static_for<Q>([&](auto K) {
                 constexpr int i = decltype(K)::value;
@@ -364,7 +393,8 @@ struct M3Cta {
 
     __device__ __forceinline__ void wait_stage(int q)
     {
-        if (!mbar_wait_bounded(&bar[q & 1], (unsigned)((q >> 1) & 1))) timed_out = true;
+        const int u = q + zoff;
+        if (!mbar_wait_bounded(&bar[u & 1], (unsigned)((u >> 1) & 1))) timed_out = true;
     }
 
     // Even step of plane q (even and halo warps): collide, hand every value
@@ -387,7 +417,7 @@ struct M3Cta {
             });
         }
         R Fx, Fy, Fz;
-        force_at<R, FORCE>(g, canon(g, x, y, q), ncanon(g), Fx, Fy, Fz);
+        force_at<R, FORCE>(g, canon(g, x, y, phys(q)), ncanon(g), Fx, Fy, Fz);
         bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
         // value that leaves along c_i as the next step reads it: + L_opp(i)
         // on a wall link that ends on a lid
@@ -398,12 +428,43 @@ struct M3Cta {
                 if (lm & (1u << i)) s[i] = radd(s[i], g.L[opp(i)]);
             });
         }
+        R *zs = nullptr;
+        if constexpr (PERZ)
+            if (q <= 0) zs = zsave + (q + 1) * (L::NXY * NPOS + 3 * L::NTS);
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;
             constexpr int gg = grp(i);
             const R v = roundtrip<S, i>(s[i]);
-            if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P) ring_at<gg>(q, gidx(i))[pos] = v;
-            else if (role == EVEN) {
+            if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P) {
+                ring_at<gg>(q, gidx(i))[pos] = v;
+                if constexpr (PERZ)
+                    if (zs) zs[xyidx(i) * NPOS + pos] = v;
+            } else if (role == EVEN) {
+                constexpr int sm = i == 0 ? 0 : (i == DIR_ZP ? 1 : 2);
+                if constexpr (i == 0) srest[slot(q, L::SREST) * L::NTS + tc] = v;
+                else if constexpr (i == DIR_ZP) szp[slot(q, L::SZP) * L::NTS + tc] = v;
+                else szm[slot(q, L::SZM) * L::NTS + tc] = v;
+                if constexpr (PERZ)
+                    if (zs) zs[L::NXY * NPOS + sm * L::NTS + tc] = v;
+            }
+        });
+    }
+
+    // Periodic z, planes nz-1 and nz at the end of the march: the values of
+    // their images -1 and 0, computed before any odd step wrote into them.
+    __device__ __forceinline__ void restore(int q)
+    {
+        if constexpr (!PERZ) return;
+        if (!active) return;
+        const R *zs = zsave + (q - nz + 1) * (L::NXY * NPOS + 3 * L::NTS);
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            constexpr int gg = grp(i);
+            if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P) {
+                ring_at<gg>(q, gidx(i))[pos] = zs[xyidx(i) * NPOS + pos];
+            } else if (role == EVEN) {
+                constexpr int sm = i == 0 ? 0 : (i == DIR_ZP ? 1 : 2);
+                const R v = zs[L::NXY * NPOS + sm * L::NTS + tc];
                 if constexpr (i == 0) srest[slot(q, L::SREST) * L::NTS + tc] = v;
                 else if constexpr (i == DIR_ZP) szp[slot(q, L::SZP) * L::NTS + tc] = v;
                 else szm[slot(q, L::SZM) * L::NTS + tc] = v;
@@ -416,7 +477,7 @@ struct M3Cta {
     __device__ __forceinline__ void consume(int k)
     {
         if (!active) return;
-        const bool zlo = k == 0, zhi = k == nz - 1;
+        const bool zlo = !PERZ && k == 0, zhi = !PERZ && k == nz - 1;
         const unsigned wm = wxy | (zlo ? CZM : 0u) | (zhi ? CZP : 0u);
         R s[Q];
         s[0] = srest[slot(k, L::SREST) * L::NTS + tc];
@@ -479,23 +540,23 @@ struct M3Cta {
                     const T e = encode<S, i>(s[i]);
                     fd.p[i][c + step_offset<cx(i), cy(i), cz(i)>(g, fc)] = e;
                     const int t = gtab[pos + cx(i) + cy(i) * W];
-                    if (t >= 0) gk[cz(i) * si.gplane + t + i * NSP] = e;
+                    if (t >= 0) Gn[phys(k + cz(i)) * si.gplane + t + i * NSP] = e;
                 }
             });
         }
     }
 };
 
-template <class S, bool FORCE, int TY>
+template <class S, bool FORCE, int TY, bool PERZ>
 __global__ void __launch_bounds__(M3<TY>::THREADS, 1)
     k_merged3(const __grid_constant__ CUtensorMap tmap, Geom<typename S::R> g, Dirs<typename S::T> fd,
               Dirs<typename S::T> fo, Dirs<typename S::T> go, const typename S::T *__restrict__ Gc,
-              typename S::T *__restrict__ Gn, ShellInfo si, int *__restrict__ status)
+              typename S::T *__restrict__ Gn, ShellInfo si, typename S::R *__restrict__ zsave, int *__restrict__ status)
 {
-    using C = M3Cta<S, FORCE, TY>;
+    using C = M3Cta<S, FORCE, TY, PERZ>;
     using SM = typename C::SM;
     extern __shared__ __align__(128) unsigned char smem[];
-    C c(g, fd, fo, go, Gc, Gn, si, &tmap, smem);
+    C c(g, fd, fo, go, Gc, Gn, si, &tmap, zsave, smem);
     int *abort_flag = reinterpret_cast<int *>(smem + SM::flag_off);
     const int nz = g.nz;
     if (threadIdx.x == 0) {
@@ -507,16 +568,21 @@ __global__ void __launch_bounds__(M3<TY>::THREADS, 1)
     c.fill_gtab();
     __syncthreads();
     c.setup();
-    if (c.role == C::HALO) c.issue_stage(0);
+    // planes loaded from memory: -zoff .. last; with periodic z the planes
+    // nz-1 and nz are restored at the end
+    const int last = nz - 1 - c.zoff;
+    if (c.role == C::HALO) c.issue_stage(-c.zoff);
     // interval k: even and halo warps collide plane k+2, odd warps plane k;
     // the halo warps start loading plane k+3 into the slot plane k+1 freed
-    for (int k = -2; k < nz; ++k) {
+    for (int k = -2 - c.zoff; k < nz; ++k) {
         const int q = k + 2;
-        if (c.role == C::HALO && k + 3 < nz) c.issue_stage(k + 3);
+        if (c.role == C::HALO && q + 1 <= last) c.issue_stage(q + 1);
         if (c.role != C::ODD) {
-            if (q < nz) {
+            if (q <= last) {
                 c.wait_stage(q);
                 if (!c.timed_out) c.produce(q);
+            } else if (PERZ && q <= nz) {
+                c.restore(q);
             }
         } else if (k >= 0) {
             c.consume(k);

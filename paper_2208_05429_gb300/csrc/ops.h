@@ -74,11 +74,13 @@ struct StorageOps {
     // shadow-shell merged sweep: band height limit and shell slots per tile
     // of this storage's instantiation; G* arrays hold stored elements
     int m3_ty, m3_nsp;
+    int m3_zsave;  // compute-type elements per tile saved across a periodic-z march
     cudaError_t (*shell_gather)(const HostGeom &, int64_t pitch, const void *f, void *G, const ShellInfo &,
                                 cudaStream_t);
-    // tmap: CUtensorMap of f with a box of one direction of a 32 x m3_ty tile
+    // tmap: CUtensorMap of f with a box of one direction of a 32 x m3_ty tile;
+    // zsave: m3_zsave elements per tile with periodic z (else unused)
     cudaError_t (*merged3)(const HostGeom &, int64_t pitch, bool force, void *f, const void *Gcur, void *Gnext,
-                           const ShellInfo &, const void *tmap, int *status, cudaStream_t);
+                           const ShellInfo &, void *zsave, const void *tmap, int *status, cudaStream_t);
     // persistent plane-wavefront sweep (two time steps); sched points to a
     // WaveSchedule (device pointers inside), grid = number of CTAs
     cudaError_t (*wavefront)(const HostGeom &, int64_t pitch, bool force, void *f, const void *sched, int grid,

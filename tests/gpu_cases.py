@@ -28,6 +28,8 @@ def cases():
     c["mixed_33x40x9"] = oracle.Config(nx=33, ny=40, nz=9, tau=0.9, bc=(L, W, P, P, W, L), u_lid=(0.0, 0.04, -0.01))
     c["flat_40x35x1"] = oracle.Config(nx=40, ny=35, nz=1, tau=0.65, bc=(W, W, W, L, P, P), u_lid=(0.03, 0.0, 0.0))
     c["line_70x1x1"] = oracle.Config(nx=70, ny=1, nz=1, tau=0.8)
+    c["periodic_33x15x2"] = oracle.Config(nx=33, ny=15, nz=2, tau=0.7, force_mode=FORCE_UNIFORM,
+                                          force_uniform=(0.0, 3e-6, -2e-6))
     return c
 
 
