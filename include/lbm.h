@@ -213,6 +213,15 @@ int lbm_profile(lbm_handle *h, int32_t enable);
  * outputs.  Synchronises on the recorded events. */
 int lbm_profile_read(lbm_handle *h, int32_t kernel, int64_t *launches, double *total_ms);
 
+/* Self-test of the failure detection of a WAVEFRONT handle: runs one sweep
+ * in which only the odd-step items are scheduled, so that every bounded
+ * inter-CTA wait runs out (about a second) and gives up without touching
+ * the lattice; the state and the step count stay unchanged.  Returns
+ * LBM_ETIMEOUT when the give-up was recorded in the status word (which is
+ * cleared again), LBM_OK if nothing was recorded, LBM_ESTATE for another
+ * schedule.  Synchronises the stream. */
+int lbm_selftest_wait_timeout(lbm_handle *h);
+
 /* ---------------- adjoint (reverse-mode) ----------------
  * The reverse of one step f^t -> f^{t+1} of this handle's configuration,
  * derived by hand from the collide and stream rules above (the paper has no

@@ -844,6 +844,41 @@ int lbm_reduce(lbm_handle *h, double *out)
     return bad ? LBM_ENONFINITE : LBM_OK;
 }
 
+int lbm_selftest_wait_timeout(lbm_handle *h)
+{
+    if (!h) return LBM_EINVAL;
+    if (h->cfg.variant != LBM_VARIANT_WAVEFRONT) return LBM_ESTATE;
+    if (!h->force_set) return LBM_ESTATE;
+    DeviceGuard g(h->device);
+    if (!g.ok) return LBM_ECUDA;
+    // a schedule of odd-step entries only: their completion flags never come
+    const int nz = (int)h->cfg.nz;
+    std::vector<int> odd((size_t)nz);
+    for (int p = 0; p < nz; ++p) odd[(size_t)p] = 2 * p + 1;
+    int *ent = nullptr;
+    CK(cudaMallocAsync((void **)&ent, sizeof(int) * (size_t)nz, h->stream));
+    WaveSchedule ws;
+    ws.entries = ent;
+    ws.nentries = nz;
+    ws.rb = h->wf_rb;
+    ws.nrb = h->wf_nrb;
+    ws.ticket = h->wf_words + 2 * h->cfg.nz + 4;
+    ws.done = ws.ticket + 1;
+    ws.status = h->status;
+    int st = 0;
+    const bool ok = cudaMemcpyAsync(ent, odd.data(), sizeof(int) * (size_t)nz, cudaMemcpyHostToDevice, h->stream) ==
+                        cudaSuccess &&
+                    cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) == cudaSuccess &&
+                    cudaMemsetAsync(ws.ticket, 0, sizeof(int) * (1 + h->cfg.nz * h->wf_nrb), h->stream) ==
+                        cudaSuccess &&
+                    h->ops->wavefront(h->hg, h->nxp, h->force, h->f, &ws, h->wf_grid, h->stream) == cudaSuccess &&
+                    cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream) == cudaSuccess &&
+                    cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) == cudaSuccess;
+    cudaFreeAsync(ent, h->stream);
+    if (!ok || cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
+    return st ? LBM_ETIMEOUT : LBM_OK;
+}
+
 int lbm_profile(lbm_handle *h, int32_t enable)
 {
     if (!h) return LBM_EINVAL;

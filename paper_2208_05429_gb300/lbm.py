@@ -85,6 +85,7 @@ _SIGNATURES = {
     "lbm_init_populations": (ctypes.c_int, [_H, _VP, ctypes.c_int32]),
     "lbm_reduce": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double)]),
     "lbm_profile": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "lbm_selftest_wait_timeout": (ctypes.c_int, [_H]),
     "lbm_profile_read": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_double)]),
     "lbm_adjoint_step": (ctypes.c_int, [_H, _VP, _VP, _VP, ctypes.c_int32, _VP]),
@@ -238,6 +239,11 @@ def lbm_profile_read(h, kernel: int) -> Tuple[int, float]:
     ms = ctypes.c_double(0.0)
     _check(library().lbm_profile_read(h, int(kernel), ctypes.byref(n), ctypes.byref(ms)), "lbm_profile_read")
     return n.value, ms.value
+
+
+def lbm_selftest_wait_timeout(h) -> int:
+    """Status code of the wait-timeout self-test (LBM_ETIMEOUT expected)."""
+    return int(library().lbm_selftest_wait_timeout(h))
 
 
 def lbm_adjoint_step(h, f_t, lam_in, lam_out, dtype_code: int, dLdF=None):
@@ -400,6 +406,11 @@ class Lattice:
             if n:
                 out[name] = (n, ms)
         return out
+
+    def selftest_wait_timeout(self) -> int:
+        """WAVEFRONT only: make every bounded inter-CTA wait of one sweep run
+        out and return the recorded status (LBM_ETIMEOUT expected)."""
+        return lbm_selftest_wait_timeout(self.h)
 
     # adjoint --------------------------------------------------------------
     def adjoint_step(self, f_t, lam_in, lam_out, dLdF=None):

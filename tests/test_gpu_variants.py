@@ -158,3 +158,27 @@ def test_graph_rebuilt_after_force_field_change(gpu):
     for _ in range(32):
         b.step(1)
     assert torch.equal(_raw(a), _raw(b))
+
+
+def test_bounded_wait_gives_up_and_reports(gpu):
+    """Failure detection of the inter-CTA waits: a sweep whose odd-step items
+    wait for even-step items that are never scheduled gives up (bounded
+    waits), reports LBM_ETIMEOUT and leaves the state untouched; the handle
+    keeps working afterwards."""
+    import torch
+    from paper_2208_05429_gb300.lbm import LBM_ETIMEOUT, LBM_ESTATE
+    cfg = oracle_force_as_f32(CASES["cavity16"])
+    f0 = start_state(cfg, seed=21)
+    w = make_gpu(cfg, "f32", "wavefront")
+    load_state(w, f0)
+    w.step(2)
+    before = _raw(w)
+    assert w.selftest_wait_timeout() == LBM_ETIMEOUT
+    assert torch.equal(_raw(w), before) and w.time == 2
+    w.step(2)
+    a = make_gpu(cfg, "f32", "aa")
+    load_state(a, f0)
+    a.step(4)
+    assert torch.equal(_raw(w), _raw(a))
+    assert np.all(np.isfinite(w.reduce()))
+    assert make_gpu(cfg, "f32", "aa").selftest_wait_timeout() == LBM_ESTATE
