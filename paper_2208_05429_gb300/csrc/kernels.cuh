@@ -19,6 +19,8 @@
 #include "d3q19.cuh"
 #include "ops.h"
 
+#include <type_traits>
+
 namespace lbm {
 
 // ---------------------------------------------------------------------------
@@ -255,13 +257,26 @@ __global__ void __launch_bounds__(128) k_two_lattice(Geom<typename S::R> g, Dirs
 // f*_i into slot opp(i) of the same cell (the "revert" of Sec. 3).  Planes
 // z0 .. z0 + gridDim.z - 1.
 // ---------------------------------------------------------------------------
+// Post-collision value f*_i of one cell as the even step stores it in slot
+// opp(i): + L_opp(i) when the link along c_i is a wall link ending on a lid.
+template <class S>
+__device__ __forceinline__ void even_outputs(const Geom<typename S::R> &g, int x, int y, int z,
+                                             typename S::R (&s)[Q])
+{
+    if (interior(g, x, y, z)) return;
+    const Faces fc = faces_of(g, x, y, z);
+    static_for<Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        constexpr unsigned m = face_mask(cx(i), cy(i), cz(i));
+        if ((fc.wall & m) && (fc.lid & m)) s[i] = radd(s[i], g.L[opp(i)]);
+    });
+}
+
 template <class S, bool FORCE>
-__global__ void __launch_bounds__(128) k_aa_even(Geom<typename S::R> g, Dirs<typename S::T> f, int z0)
+__device__ __forceinline__ void aa_even_cell(const Geom<typename S::R> &g, const Dirs<typename S::T> &f, int x, int y,
+                                             int z, int c)
 {
     using R = typename S::R;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z + z0;
-    if (x >= g.nx) return;
-    const int c = cell32(g, x, y, z);
     R s[Q];
     static_for<Q>([&](auto K) {
         constexpr int i = decltype(K)::value;
@@ -270,21 +285,79 @@ __global__ void __launch_bounds__(128) k_aa_even(Geom<typename S::R> g, Dirs<typ
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
     bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
-    if (interior(g, x, y, z)) {
-        static_for<Q>([&](auto K) {
-            constexpr int i = decltype(K)::value;
-            f.p[opp(i)][c] = encode<S, opp(i)>(s[i]);
-        });
-    } else {
-        const Faces fc = faces_of(g, x, y, z);
-        static_for<Q>([&](auto K) {
-            constexpr int i = decltype(K)::value;
-            constexpr unsigned m = face_mask(cx(i), cy(i), cz(i));
-            R v = s[i];
-            if ((fc.wall & m) && (fc.lid & m)) v = radd(v, g.L[opp(i)]);
-            f.p[opp(i)][c] = encode<S, opp(i)>(v);
-        });
+    even_outputs<S>(g, x, y, z, s);
+    static_for<Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        f.p[opp(i)][c] = encode<S, opp(i)>(s[i]);
+    });
+}
+
+template <class S, bool FORCE>
+__global__ void __launch_bounds__(128) k_aa_even(Geom<typename S::R> g, Dirs<typename S::T> f, int z0)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z + z0;
+    if (x >= g.nx) return;
+    aa_even_cell<S, FORCE>(g, f, x, y, z, cell32(g, x, y, z));
+}
+
+// The even step for 2-byte storage, two neighbouring cells (x, x+1), x even,
+// per thread: every access of the step is to the cells' own slots, so the
+// pair moves as one 4-byte word per direction and converts with the packed
+// two-element conversions (element-wise the same rounding).
+template <class S>
+struct Pair2 {
+    __device__ static void decode2(uint32_t w, float &a, float &b)
+    {
+        if constexpr (std::is_same<typename S::T, __half>::value) {
+            __half2 h = *reinterpret_cast<__half2 *>(&w);
+            const float2 v = __half22float2(h);
+            a = v.x; b = v.y;
+        } else {
+            __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&w);
+            const float2 v = __bfloat1622float2(h);
+            a = v.x; b = v.y;
+        }
     }
+    __device__ static uint32_t encode2(float a, float b)
+    {
+        if constexpr (std::is_same<typename S::T, __half>::value) {
+            __half2 h = __floats2half2_rn(a, b);
+            return *reinterpret_cast<uint32_t *>(&h);
+        } else {
+            __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            return *reinterpret_cast<uint32_t *>(&h);
+        }
+    }
+};
+
+template <class S, bool FORCE>
+__global__ void __launch_bounds__(128) k_aa_even_pair(Geom<typename S::R> g, Dirs<typename S::T> f, int z0)
+{
+    static_assert(sizeof(typename S::T) == 2 && S::shifted, "2-byte shifted storage");
+    using R = typename S::R;
+    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x), y = blockIdx.y, z = blockIdx.z + z0;
+    if (x >= g.nx) return;
+    const int c = cell32(g, x, y, z);
+    if (x + 1 >= g.nx) {  // odd nx: the last cell alone
+        aa_even_cell<S, FORCE>(g, f, x, y, z, c);
+        return;
+    }
+    R a[Q], b[Q];
+    static_for<Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        Pair2<S>::decode2(*reinterpret_cast<const uint32_t *>(f.p[i] + c), a[i], b[i]);
+    });
+    R Fx, Fy, Fz;
+    force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
+    bgk_collide<R, FORCE>(a, g.omega, g.kf, Fx, Fy, Fz);
+    force_at<R, FORCE>(g, canon(g, x + 1, y, z), ncanon(g), Fx, Fy, Fz);
+    bgk_collide<R, FORCE>(b, g.omega, g.kf, Fx, Fy, Fz);
+    even_outputs<S>(g, x, y, z, a);
+    even_outputs<S>(g, x + 1, y, z, b);
+    static_for<Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        *reinterpret_cast<uint32_t *>(f.p[opp(i)] + c) = Pair2<S>::encode2(a[i], b[i]);
+    });
 }
 
 // ---------------------------------------------------------------------------

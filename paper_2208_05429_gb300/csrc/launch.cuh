@@ -43,9 +43,15 @@ struct Launch {
     {
         const Geom<R> g = make_geom<R>(h, pitch);
         const Dirs<T> d = make_dirs((T *)f, slot_of(h, pitch));
-        const dim3 grid((h.nx + CELL_BLOCK - 1) / CELL_BLOCK, h.ny, z1 - z0);
-        if (force) k_aa_even<S, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
-        else k_aa_even<S, false><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+        if constexpr (sizeof(T) == 2) {  // two cells per thread (packed 4-byte accesses)
+            const dim3 grid((h.nx + 2 * CELL_BLOCK - 1) / (2 * CELL_BLOCK), h.ny, z1 - z0);
+            if (force) k_aa_even_pair<S, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+            else k_aa_even_pair<S, false><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+        } else {
+            const dim3 grid((h.nx + CELL_BLOCK - 1) / CELL_BLOCK, h.ny, z1 - z0);
+            if (force) k_aa_even<S, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+            else k_aa_even<S, false><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+        }
         return cudaGetLastError();
     }
     static cudaError_t aa_odd_range(const HostGeom &h, int64_t pitch, bool force, void *f, int z0, int z1,
