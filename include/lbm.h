@@ -65,7 +65,7 @@ enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_LID = 2 };
 enum { LBM_STORAGE_F64 = 0, LBM_STORAGE_F32 = 1, LBM_STORAGE_F32S = 2,
        LBM_STORAGE_F16S = 3, LBM_STORAGE_BF16S = 4 };
 
-/* Update schedule.  All three give bit-identical populations for the same
+/* Update schedule.  All of them give bit-identical populations for the same
  * storage (Sec. 5.1 of the paper verifies its two-step solvers against the
  * single-step ones the same way).
  *   TWO_LATTICE  fused collide-and-push into a second lattice (reference
@@ -73,11 +73,17 @@ enum { LBM_STORAGE_F64 = 0, LBM_STORAGE_F32 = 1, LBM_STORAGE_F32S = 2,
  *   AA           single copy: even step collides in place into the opposite
  *                slots (the "revert" of Sec. 3), odd step gathers, collides
  *                and scatters (the "swap_stream" half of Sec. 3)
- *   MERGED       single copy, two time steps per sweep (Sec. 4): a tiled
- *                kernel marching z performs the even and the odd step of a
- *                column in one pass; a pre-pass snapshots the tile shells so
- *                that tiles never read what a neighbouring tile has already
- *                overwritten (the role of Stage I of Alg. 3).
+ *   MERGED       single copy of the lattice, two time steps per sweep
+ *                (Sec. 4): one CTA per 32 x 14 column tile marches z, its
+ *                even-step warps collide plane k+2 into shared-memory rings
+ *                while its odd-step warps collide plane k and scatter.  The
+ *                cells on the tile boundaries (read by up to four tiles) are
+ *                also kept in a double-buffered shadow: a sweep reads them
+ *                from the current copy and writes the next one, so tiles
+ *                never read what a neighbour has already overwritten (the
+ *                role of the intersection layers, Stage I of Alg. 3).  With
+ *                an explicit tile_y the older form runs instead: a pre-pass
+ *                snapshots the tile shells every sweep.
  *   WAVEFRONT    single copy, two time steps per DRAM round trip through the
  *                L2 cache (the cache reuse of Sec. 4.1 and 5.2): one
  *                persistent kernel runs the even step of plane p+L+1 and the
@@ -107,7 +113,8 @@ typedef struct lbm_config {
     int32_t variant;          /* LBM_VARIANT_*                                 */
     int32_t force_mode;       /* LBM_FORCE_*                                   */
     double force_uniform[3];  /* the force of LBM_FORCE_UNIFORM                */
-    int32_t tile_x, tile_y;   /* MERGED tile shape; 0 = library default        */
+    int32_t tile_x, tile_y;   /* MERGED: 0 = shadow-shell sweep (32 x 14 tiles),
+                                 else the snapshot sweep with 32 x tile_y tiles */
 } lbm_config;
 
 /* Fill cfg with a 32^3 fully periodic FP32 AA lattice, tau = 0.6. */
@@ -164,8 +171,11 @@ int lbm_init_equilibrium(lbm_handle *h, const void *rho, const void *u, int32_t 
 int lbm_set_force(lbm_handle *h, const float *F);
 
 /* Advance n >= 0 time steps (one step = collide then stream, Sec. 3).  With
- * MERGED, pairs of steps run as one merged sweep (Sec. 4) and an odd
- * remainder as one AA step.  Asynchronous on the handle's stream. */
+ * MERGED and WAVEFRONT, pairs of steps run as one two-step sweep (Sec. 4) and
+ * an odd remainder as one AA step.  Asynchronous on the handle's stream.
+ * Calls with n >= 32 (outside profiling) capture the launches of 32 steps
+ * once into a CUDA graph and replay it, on an internal stream ordered after
+ * and before the handle's stream; a new force field drops the graph. */
 int lbm_step(lbm_handle *h, int64_t n);
 
 /* Time steps taken since the last init (host output). */
