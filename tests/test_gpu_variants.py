@@ -182,3 +182,41 @@ def test_bounded_wait_gives_up_and_reports(gpu):
     assert torch.equal(_raw(w), _raw(a))
     assert np.all(np.isfinite(w.reduce()))
     assert make_gpu(cfg, "f32", "aa").selftest_wait_timeout() == LBM_ESTATE
+
+
+def _random_config(rng):
+    """A random small lattice: ragged against the 32-wide tiles and the
+    14-row bands, random face types (periodic pairs, walls, lids) and force."""
+    import oracle
+    from oracle import BC_LID, BC_PERIODIC, BC_WALL, FORCE_NONE, FORCE_UNIFORM
+    nx, ny, nz = (int(v) for v in rng.integers([1, 1, 2], [80, 48, 24]))
+    bc = []
+    for a in range(3):
+        if rng.random() < 0.4:
+            bc += [BC_PERIODIC, BC_PERIODIC]
+        else:
+            bc += [BC_LID if rng.random() < 0.3 else BC_WALL, BC_LID if rng.random() < 0.3 else BC_WALL]
+    lid = tuple(float(v) for v in rng.uniform(-0.04, 0.04, 3))
+    fm = FORCE_UNIFORM if rng.random() < 0.5 else FORCE_NONE
+    fu = tuple(float(v) for v in rng.uniform(-2e-5, 2e-5, 3)) if fm == FORCE_UNIFORM else (0.0, 0.0, 0.0)
+    return oracle.Config(nx=nx, ny=ny, nz=nz, tau=float(rng.uniform(0.52, 1.2)), bc=tuple(bc), u_lid=lid,
+                         force_mode=fm, force_uniform=fu)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_shapes_merged_and_wavefront_equal_aa(gpu, seed):
+    import torch
+    rng = np.random.default_rng(1000 + seed)
+    cfg = _random_config(rng)
+    storage = ["f64", "f32", "f32s", "f16s", "bf16s"][seed % 5]
+    nsteps = int(rng.integers(2, 9))
+    f0 = start_state(cfg, seed=seed)
+    ref = make_gpu(cfg, storage, "aa")
+    load_state(ref, f0)
+    ref.step(nsteps)
+    want = _raw(ref)
+    for variant in ("merged", "wavefront"):
+        lat = make_gpu(cfg, storage, variant)
+        load_state(lat, f0)
+        lat.step(nsteps)
+        assert torch.equal(_raw(lat), want), (variant, cfg.nx, cfg.ny, cfg.nz, cfg.bc, storage, nsteps)
