@@ -368,19 +368,37 @@ __global__ void __launch_bounds__(128) k_aa_even_pair(Geom<typename S::R> g, Dir
 // z0 .. z0 + gridDim.z - 1.
 // ---------------------------------------------------------------------------
 template <class S, bool FORCE>
-__global__ void __launch_bounds__(128) k_aa_odd(Geom<typename S::R> g, Dirs<typename S::T> f, int z0)
+__global__ void __launch_bounds__(128) k_aa_odd(Geom<typename S::R> g, Dirs<typename S::T> f, Dirs<typename S::T> fin,
+                                                Dirs<typename S::T> fout, int z0)
 {
+    // fin.p[k] = f.p[opp(k)] - noff[k] and fout.p[i] = f.p[i] + noff[i]: the
+    // gather and push addresses of an interior cell, one index away
     using R = typename S::R;
     using T = typename S::T;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z + z0;
     if (x >= g.nx) return;
     const int c = cell32(g, x, y, z);
     R s[Q];
-    load_aparity_d<S>(g, reinterpret_cast<const Dirs<const T> &>(f), x, y, z, c, s);
+    const bool in = interior(g, x, y, z);
+    if (in) {
+        static_for<Q>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            s[k] = decode<S, k>(fin.p[k][c]);
+        });
+    } else {
+        load_aparity_d<S>(g, reinterpret_cast<const Dirs<const T> &>(f), x, y, z, c, s);
+    }
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
     bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
-    push_store_d<S>(g, f, x, y, z, c, s);
+    if (in) {
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            fout.p[i][c] = encode<S, i>(s[i]);
+        });
+    } else {
+        push_store_d<S>(g, f, x, y, z, c, s);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -59,9 +59,14 @@ struct Launch {
     {
         const Geom<R> g = make_geom<R>(h, pitch);
         const Dirs<T> d = make_dirs((T *)f, slot_of(h, pitch));
+        Dirs<T> din, dout;
+        for (int i = 0; i < Q; ++i) {
+            din.p[i] = d.p[opp(i)] - g.noff[i];
+            dout.p[i] = d.p[i] + g.noff[i];
+        }
         const dim3 grid((h.nx + CELL_BLOCK - 1) / CELL_BLOCK, h.ny, z1 - z0);
-        if (force) k_aa_odd<S, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
-        else k_aa_odd<S, false><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+        if (force) k_aa_odd<S, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, din, dout, z0);
+        else k_aa_odd<S, false><<<grid, CELL_BLOCK, 0, st>>>(g, d, din, dout, z0);
         return cudaGetLastError();
     }
     static cudaError_t aa_even(const HostGeom &h, int64_t pitch, bool force, void *f, cudaStream_t st)
