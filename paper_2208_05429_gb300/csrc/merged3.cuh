@@ -159,6 +159,35 @@ __global__ void __launch_bounds__(256) k_shell_gather(Geom<typename S::R> g, Dir
 }
 
 
+// CTA-wide barrier that the warps may reach from different code locations
+// (every thread arrives the same number of times).
+__device__ __forceinline__ void cta_barrier() { asm volatile("barrier.sync 0;" ::: "memory"); }
+
+// Global store that allocates no L1 line: the lattice and the shadow are
+// written once per sweep, and the few kilobytes of L1 next to the shared
+// memory are better left to the halo copies.
+template <class T>
+__device__ __forceinline__ void st_no_l1(T *p, T v)
+{
+    static_assert(sizeof(T) == 2 || sizeof(T) == 4 || sizeof(T) == 8, "stored element");
+    if constexpr (sizeof(T) == 4) {
+        const unsigned u = *reinterpret_cast<const unsigned *>(&v);
+        asm volatile("st.global.L1::no_allocate.b32 [%0], %1;" ::"l"(p), "r"(u));
+    } else if constexpr (sizeof(T) == 2) {
+        const unsigned short u = *reinterpret_cast<const unsigned short *>(&v);
+        asm volatile("st.global.L1::no_allocate.b16 [%0], %1;" ::"l"(p), "h"(u));
+    } else {
+        const unsigned long long u = *reinterpret_cast<const unsigned long long *>(&v);
+        asm volatile("st.global.L1::no_allocate.b64 [%0], %1;" ::"l"(p), "l"(u));
+    }
+}
+
+// 16-byte asynchronous copy that bypasses L1.
+__device__ __forceinline__ void cp_async_cg16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_mbar_arrive(uint64_t *bar)
 {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
@@ -376,8 +405,8 @@ struct M3Cta {
         const T *gs = Gc + pz * si.gplane + (int64_t)(blockIdx.y * si.ntx + blockIdx.x) * Q * NSP;
         for (int ch = hidx; ch < Q * SM::CHUNKS; ch += NHT) {
             const int d = ch / SM::CHUNKS, j = ch - d * SM::CHUNKS;
-            cp_async<16>(reinterpret_cast<unsigned char *>(tb + d * DST + NT) + 16 * j,
-                         reinterpret_cast<const unsigned char *>(gs + d * NSP) + 16 * j);
+            cp_async_cg16(reinterpret_cast<unsigned char *>(tb + d * DST + NT) + 16 * j,
+                      reinterpret_cast<const unsigned char *>(gs + d * NSP) + 16 * j);
         }
         // this thread's halo cell: the copy unit holding each direction
         if (active) {
@@ -472,14 +501,12 @@ struct M3Cta {
         });
     }
 
-    // Odd step of plane k (odd warps): gather, collide, scatter into f and,
-    // for targets on a shell, into the next shadow.
-    __device__ __forceinline__ void consume(int k)
+    // Odd step of plane k (odd warps, active threads): gather and collide;
+    // scatter() writes the result one interval later.
+    __device__ __forceinline__ void consume(int k, R (&s)[Q]) const
     {
-        if (!active) return;
         const bool zlo = !PERZ && k == 0, zhi = !PERZ && k == nz - 1;
         const unsigned wm = wxy | (zlo ? CZM : 0u) | (zhi ? CZP : 0u);
-        R s[Q];
         s[0] = srest[slot(k, L::SREST) * L::NTS + tc];
         s[DIR_ZP] = zlo ? szm[slot(k, L::SZM) * L::NTS + tc] : szp[slot(k - 1, L::SZP) * L::NTS + tc];
         s[DIR_ZM] = zhi ? szp[slot(k, L::SZP) * L::NTS + tc] : szm[slot(k + 1, L::SZM) * L::NTS + tc];
@@ -503,8 +530,10 @@ struct M3Cta {
         R Fx, Fy, Fz;
         force_at<R, FORCE>(g, canon(g, x, y, k), ncanon(g), Fx, Fy, Fz);
         bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
-        scatter(k, s);
     }
+
+    // Push the odd-step result of plane k into f and, for targets on a
+    // shell, into the next shadow.
 
     __device__ __forceinline__ void scatter(int k, const R (&s)[Q]) const
     {
@@ -515,14 +544,19 @@ struct M3Cta {
             if (!gmask) {  // inner cells: no shell target
                 static_for<Q>([&](auto K) {
                     constexpr int i = decltype(K)::value;
-                    fo.p[i][c] = encode<S, i>(s[i]);
+                    st_no_l1(&fo.p[i][c], encode<S, i>(s[i]));
                 });
             } else {
+                // shadow offsets of the 3 x 3 neighbourhood, loaded together
+                // (19 directions share 9 targets in the plane)
+                int gt[9];
+#pragma unroll
+                for (int j = 0; j < 9; ++j) gt[j] = gtab[pos + (j % 3 - 1) + (j / 3 - 1) * W];
                 static_for<Q>([&](auto K) {
                     constexpr int i = decltype(K)::value;
                     const T e = encode<S, i>(s[i]);
-                    fo.p[i][c] = e;
-                    if (gmask & (1u << i)) go.p[i][kg + gtab[pos + cx(i) + cy(i) * W]] = e;
+                    st_no_l1(&fo.p[i][c], e);
+                    if (gmask & (1u << i)) st_no_l1(&go.p[i][kg + gt[(cx(i) + 1) + (cy(i) + 1) * 3]], e);
                 });
             }
         } else {
@@ -571,24 +605,36 @@ __global__ void __launch_bounds__(M3<TY>::THREADS, 1)
     // planes loaded from memory: -zoff .. last; with periodic z the planes
     // nz-1 and nz are restored at the end
     const int last = nz - 1 - c.zoff;
-    if (c.role == C::HALO) c.issue_stage(-c.zoff);
     // interval k: even and halo warps collide plane k+2, odd warps plane k;
-    // the halo warps start loading plane k+3 into the slot plane k+1 freed
+    // the halo warps start loading plane k+3 into the slot plane k+1 freed.
+    // The roles run separate loops over the same intervals (one barrier
+    // each); odd warps store plane k-1 at the start of interval k, so that
+    // its stores drain while they collide plane k, not at the barrier.
+    if (c.role == C::ODD) {
+        typename S::R sk[Q];
+        bool held = false;
+        for (int k = -2 - c.zoff; k < nz; ++k) {
+            if (held) c.scatter(k - 1, sk);
+            held = k >= 0 && c.active;
+            if (held) c.consume(k, sk);
+            cta_barrier();
+            if (*abort_flag) goto bail;
+        }
+        if (held) c.scatter(nz - 1, sk);
+        return;
+    }
+    if (c.role == C::HALO) c.issue_stage(-c.zoff);
     for (int k = -2 - c.zoff; k < nz; ++k) {
         const int q = k + 2;
         if (c.role == C::HALO && q + 1 <= last) c.issue_stage(q + 1);
-        if (c.role != C::ODD) {
-            if (q <= last) {
-                c.wait_stage(q);
-                if (!c.timed_out) c.produce(q);
-            } else if (PERZ && q <= nz) {
-                c.restore(q);
-            }
-        } else if (k >= 0) {
-            c.consume(k);
+        if (q <= last) {
+            c.wait_stage(q);
+            if (!c.timed_out) c.produce(q);
+        } else if (PERZ && q <= nz) {
+            c.restore(q);
         }
         if (c.timed_out) *abort_flag = 1;
-        __syncthreads();
+        cta_barrier();
         if (*abort_flag) goto bail;
     }
     return;
