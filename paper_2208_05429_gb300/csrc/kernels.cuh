@@ -592,17 +592,21 @@ static __global__ void __launch_bounds__(RED_THREADS) k_reduce_final(const doubl
 // ---------------------------------------------------------------------------
 // lam_out(x) = (d f^{t+1}/d f^t)^T lam_in at cell x, gF(x) += (d f^{t+1}/dF(x))^T lam_in.
 // f and lam share the geometry g (pitch g.nxp); gF and the force are canonical.
+// fd.p[i] = f + i slot; lin.p[i] = lam_in + i slot + noff[i], the gather
+// address of an interior cell; lout.p[j] = lam_out + j slot.
 template <class S, bool FORCE>
-__global__ void __launch_bounds__(128) k_adjoint(Geom<typename S::R> g, const typename S::T *__restrict__ f,
-                                                 const typename S::R *__restrict__ lam_in,
-                                                 typename S::R *__restrict__ lam_out, double *__restrict__ gF)
+__global__ void __launch_bounds__(128) k_adjoint(Geom<typename S::R> g, Dirs<const typename S::T> fd,
+                                                 Dirs<const typename S::R> lin,
+                                                 const typename S::R *__restrict__ lam_in, Dirs<typename S::R> lout,
+                                                 double *__restrict__ gF)
 {
     using R = typename S::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     if (x >= g.nx) return;
-    const int64_t n = ncanon(g), cc = canon(g, x, y, z), c = cell_of(g, x, y, z);
+    const int64_t n = ncanon(g), cc = canon(g, x, y, z);
+    const int c = cell32(g, x, y, z);
     R s[Q];
-    load_natural<S>(g, f, x, y, z, s);
+    load_natural_d<S>(fd, c, s);
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, cc, n, Fx, Fy, Fz);
     const Mom<R> m = moments_of<R, FORCE>(s, Fx, Fy, Fz);
@@ -613,8 +617,7 @@ __global__ void __launch_bounds__(128) k_adjoint(Geom<typename S::R> g, const ty
     static_for<Q>([&](auto K) {
         constexpr int i = decltype(K)::value;
         if (in) {
-            const int64_t off = (int64_t)cz(i) * g.plane + (int64_t)cy(i) * g.nxp + cx(i);
-            mu[i] = lam_in[i * g.slot + c + off];
+            mu[i] = lin.p[i][c];
         } else {
             int tx, ty, tz;
             bool lid;
@@ -653,7 +656,7 @@ __global__ void __launch_bounds__(128) k_adjoint(Geom<typename S::R> g, const ty
         constexpr int j = decltype(K)::value;
         const R v = (R(1) - g.omega) * mu[j] + g.omega * a +
                     (ex * (R(cx(j)) - m.ux) + ey * (R(cy(j)) - m.uy) + ez * (R(cz(j)) - m.uz)) * inv;
-        lam_out[j * g.slot + c] = v;
+        lout.p[j][c] = v;
     });
     if (gF) {
         const R h = R(0.5) * inv;

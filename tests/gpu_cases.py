@@ -30,6 +30,9 @@ def cases():
     c["line_70x1x1"] = oracle.Config(nx=70, ny=1, nz=1, tau=0.8)
     c["periodic_33x15x2"] = oracle.Config(nx=33, ny=15, nz=2, tau=0.7, force_mode=FORCE_UNIFORM,
                                           force_uniform=(0.0, 3e-6, -2e-6))
+    # rows made only of x-edge cells (nx = 2, nx = 1)
+    c["narrow_2x21x5"] = oracle.Config(nx=2, ny=21, nz=5, tau=0.75, bc=(W, L, P, P, W, W), u_lid=(0.0, 0.02, 0.01))
+    c["pencil_1x19x4"] = oracle.Config(nx=1, ny=19, nz=4, tau=0.8, bc=(P, P, W, L, W, W), u_lid=(0.02, 0.0, 0.0))
     return c
 
 
