@@ -23,6 +23,25 @@
 
 namespace lbm {
 
+// Global store that allocates no L1 line, for values written once per sweep
+// and not read back by the writing CTA.
+template <class T>
+__device__ __forceinline__ void st_no_l1(T *p, T v)
+{
+    static_assert(sizeof(T) == 2 || sizeof(T) == 4 || sizeof(T) == 8, "stored element");
+    if constexpr (sizeof(T) == 4) {
+        const unsigned u = *reinterpret_cast<const unsigned *>(&v);
+        asm volatile("st.global.L1::no_allocate.b32 [%0], %1;" ::"l"(p), "r"(u));
+    } else if constexpr (sizeof(T) == 2) {
+        const unsigned short u = *reinterpret_cast<const unsigned short *>(&v);
+        asm volatile("st.global.L1::no_allocate.b16 [%0], %1;" ::"l"(p), "h"(u));
+    } else {
+        const unsigned long long u = *reinterpret_cast<const unsigned long long *>(&v);
+        asm volatile("st.global.L1::no_allocate.b64 [%0], %1;" ::"l"(p), "l"(u));
+    }
+}
+
+
 // ---------------------------------------------------------------------------
 // host -> device parameter conversion
 // ---------------------------------------------------------------------------

@@ -247,8 +247,13 @@ struct Launch {
         const Dirs<T> d = make_dirs((T *)f, slot_of(h, pitch));
         WaveSchedule ws;
         memcpy(&ws, sched, sizeof(ws));
-        if (force) k_wavefront<S, true><<<grid, WF_THREADS, 0, st>>>(g, d, ws);
-        else k_wavefront<S, false><<<grid, WF_THREADS, 0, st>>>(g, d, ws);
+        Dirs<T> din, dout;  // odd-step gather and push addresses of an interior cell
+        for (int i = 0; i < Q; ++i) {
+            din.p[i] = d.p[opp(i)] - g.noff[i];
+            dout.p[i] = d.p[i] + g.noff[i];
+        }
+        if (force) k_wavefront<S, true><<<grid, WF_THREADS, 0, st>>>(g, d, din, dout, ws);
+        else k_wavefront<S, false><<<grid, WF_THREADS, 0, st>>>(g, d, din, dout, ws);
         return cudaGetLastError();
     }
     static int wavefront_blocks_per_sm(bool force)

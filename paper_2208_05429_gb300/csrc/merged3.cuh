@@ -163,25 +163,6 @@ __global__ void __launch_bounds__(256) k_shell_gather(Geom<typename S::R> g, Dir
 // (every thread arrives the same number of times).
 __device__ __forceinline__ void cta_barrier() { asm volatile("barrier.sync 0;" ::: "memory"); }
 
-// Global store that allocates no L1 line: the lattice and the shadow are
-// written once per sweep, and the few kilobytes of L1 next to the shared
-// memory are better left to the halo copies.
-template <class T>
-__device__ __forceinline__ void st_no_l1(T *p, T v)
-{
-    static_assert(sizeof(T) == 2 || sizeof(T) == 4 || sizeof(T) == 8, "stored element");
-    if constexpr (sizeof(T) == 4) {
-        const unsigned u = *reinterpret_cast<const unsigned *>(&v);
-        asm volatile("st.global.L1::no_allocate.b32 [%0], %1;" ::"l"(p), "r"(u));
-    } else if constexpr (sizeof(T) == 2) {
-        const unsigned short u = *reinterpret_cast<const unsigned short *>(&v);
-        asm volatile("st.global.L1::no_allocate.b16 [%0], %1;" ::"l"(p), "h"(u));
-    } else {
-        const unsigned long long u = *reinterpret_cast<const unsigned long long *>(&v);
-        asm volatile("st.global.L1::no_allocate.b64 [%0], %1;" ::"l"(p), "l"(u));
-    }
-}
-
 // 16-byte asynchronous copy that bypasses L1.
 __device__ __forceinline__ void cp_async_cg16(void *dst, const void *src)
 {
@@ -469,12 +450,13 @@ struct M3Cta {
                 if constexpr (PERZ)
                     if (zs) zs[xyidx(i) * NPOS + pos] = v;
             } else if (role == EVEN) {
-                constexpr int sm = i == 0 ? 0 : (i == DIR_ZP ? 1 : 2);
                 if constexpr (i == 0) srest[slot(q, L::SREST) * L::NTS + tc] = v;
                 else if constexpr (i == DIR_ZP) szp[slot(q, L::SZP) * L::NTS + tc] = v;
                 else szm[slot(q, L::SZM) * L::NTS + tc] = v;
-                if constexpr (PERZ)
+                if constexpr (PERZ) {
+                    constexpr int sm = i == 0 ? 0 : (i == DIR_ZP ? 1 : 2);
                     if (zs) zs[L::NXY * NPOS + sm * L::NTS + tc] = v;
+                }
             }
         });
     }

@@ -49,6 +49,15 @@ __device__ __forceinline__ void st_release(int *p, int v)
 template <class T>
 __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 
+// Interior stores of the sweep: the 2-byte formats skip L1 allocation (faster
+// for them on a 256^3 cavity, slower for FP32).
+template <class T>
+__device__ __forceinline__ void wf_store(T *p, T v)
+{
+    if constexpr (sizeof(T) == 2) st_no_l1(p, v);
+    else *p = v;
+}
+
 template <class S, bool FORCE>
 __device__ __forceinline__ void wf_even_cell(const Geom<typename S::R> &g, const Dirs<typename S::T> &f, int x,
                                              int y, int z)
@@ -66,7 +75,7 @@ __device__ __forceinline__ void wf_even_cell(const Geom<typename S::R> &g, const
     if (interior(g, x, y, z)) {
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;
-            f.p[opp(i)][c] = encode<S, opp(i)>(s[i]);
+            wf_store(&f.p[opp(i)][c], encode<S, opp(i)>(s[i]));
         });
     } else {
         const Faces fc = faces_of(g, x, y, z);
@@ -81,7 +90,8 @@ __device__ __forceinline__ void wf_even_cell(const Geom<typename S::R> &g, const
 }
 
 template <class S, bool FORCE>
-__device__ __forceinline__ void wf_odd_cell(const Geom<typename S::R> &g, const Dirs<typename S::T> &f, int x,
+__device__ __forceinline__ void wf_odd_cell(const Geom<typename S::R> &g, const Dirs<typename S::T> &f,
+                                            const Dirs<typename S::T> &fin, const Dirs<typename S::T> &fout, int x,
                                             int y, int z)
 {
     using R = typename S::R;
@@ -90,7 +100,7 @@ __device__ __forceinline__ void wf_odd_cell(const Geom<typename S::R> &g, const 
     if (interior(g, x, y, z)) {
         static_for<Q>([&](auto K) {
             constexpr int k = decltype(K)::value;
-            s[k] = decode<S, k>(ldcg(f.p[opp(k)] + (c - g.noff[k])));
+            s[k] = decode<S, k>(ldcg(fin.p[k] + c));
         });
     } else {
         const Faces fc = faces_of(g, x, y, z);
@@ -103,7 +113,14 @@ __device__ __forceinline__ void wf_odd_cell(const Geom<typename S::R> &g, const 
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
     bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
-    push_store_d<S>(g, f, x, y, z, c, s);
+    if (interior(g, x, y, z)) {
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            wf_store(&fout.p[i][c], encode<S, i>(s[i]));
+        });
+    } else {
+        push_store_d<S>(g, f, x, y, z, c, s);
+    }
 }
 
 // Schedule of one launch (host-built, device pointers):
@@ -119,6 +136,7 @@ struct WaveSchedule {
 
 template <class S, bool FORCE>
 __global__ void __launch_bounds__(WF_THREADS) k_wavefront(Geom<typename S::R> g, Dirs<typename S::T> f,
+                                                          Dirs<typename S::T> fin, Dirs<typename S::T> fout,
                                                           WaveSchedule ws)
 {
     __shared__ int s_item, s_ok;
@@ -169,7 +187,7 @@ __global__ void __launch_bounds__(WF_THREADS) k_wavefront(Geom<typename S::R> g,
         const int ncell = (y1 - y0) * g.nx;
         for (int i = tid; i < ncell; i += WF_THREADS) {
             const int x = i % g.nx, y = y0 + i / g.nx;
-            if (odd) wf_odd_cell<S, FORCE>(g, f, x, y, plane);
+            if (odd) wf_odd_cell<S, FORCE>(g, f, fin, fout, x, y, plane);
             else wf_even_cell<S, FORCE>(g, f, x, y, plane);
         }
         __syncthreads();  // the item's writes are done; s_item may be reused
