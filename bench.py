@@ -11,12 +11,14 @@ time steps over all 16.8 M cells (one merged sweep, or an AA even/odd pair).
 MLUPS counts every cell as a fluid node (million lattice-node updates per
 second).
 
-Two further modes print their own JSON line instead of the benchmark line:
+Three further modes print their own JSON line instead of the benchmark line:
 ``--sweep`` (cavity cubes 64^3 .. 768^3, FP32 and FP16-shifted storage, AA
-and merged, plus the host oracle at 64^3 and 128^3) and
+and merged, plus the host oracle at 64^3 and 128^3),
 ``--precision-study`` (periodic Taylor-Green box 512^3, U0 = 0.04, tau =
 0.52: FP32 / FP16 / BF16 storage against an FP64 run of the same case,
-kinetic energy every 100 steps and max-norm velocity error).
+kinetic energy every 100 steps and max-norm velocity error) and
+``--adjoint-study`` (the adjoint/forward time ratio on the differentiable
+channel 128 x 64 x 64, the same figures as the benchmark line's "adjoint").
 
 Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs an
 independent replica on its own GPU (the update shards only through a halo
@@ -76,6 +78,8 @@ def parse():
     p.add_argument("--precision-study", action="store_true", help="512^3 Taylor-Green precision study")
     p.add_argument("--study-size", type=int, default=512)
     p.add_argument("--study-steps", type=int, default=2000)
+    p.add_argument("--adjoint-study", action="store_true",
+                   help="adjoint/forward time ratio on the differentiable channel alone (prints its own JSON line)")
     return p.parse_args()
 
 
@@ -510,6 +514,13 @@ def main():
         return sweep(args)
     if args.precision_study:
         return precision_study(args)
+    if args.adjoint_study:
+        import torch
+        from paper_2208_05429_gb300 import build
+        torch.cuda.set_device(0)
+        build.build()
+        print(json.dumps({"mode": "adjoint_study", **adjoint_leg()}))
+        return 0
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

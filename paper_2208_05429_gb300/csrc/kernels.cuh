@@ -647,34 +647,51 @@ __global__ void __launch_bounds__(128) k_adjoint(Geom<typename S::R> g, Dirs<con
         }
     });
     // a = sum mu_i dfeq_i/drho; b = sum mu_i dfeq_i/du; sv = sum mu_i dS_i/du;
-    // gv = sum mu_i dS_i/dF|_u
-    R a = R(0), bx = R(0), by = R(0), bz = R(0), sx = R(0), sy = R(0), sz = R(0);
-    R gx = R(0), gy = R(0), gz = R(0);
+    // gv = sum mu_i dS_i/dF|_u.  With wm_i = w_i mu_i and its direction
+    // moments M0 = sum wm_i, M1 = sum wm_i c_i, M2 = sum wm_i c_i c_i^T:
+    //   a = M0 (1 - 1.5 u.u) + 3 M1.u + 4.5 u.M2 u
+    //   gv = 3 M1 + 9 M2 u - 3 u M0,  b = rho gv
+    //   sv = 9 M2 F - 3 F M0
+    // (the c_i are 0 or +-1, so the moments are sums and differences of wm_i).
+    R M0 = R(0), M1x = R(0), M1y = R(0), M1z = R(0);
+    R Mxx = R(0), Myy = R(0), Mzz = R(0), Mxy = R(0), Mxz = R(0), Myz = R(0);
     static_for<Q>([&](auto K) {
         constexpr int i = decltype(K)::value;
         const R wm = R(wgt(i)) * mu[i];
-        const R cu = R(cx(i)) * m.ux + R(cy(i)) * m.uy + R(cz(i)) * m.uz;
-        a += wm * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
-        const R t = R(3) + R(9) * cu;   // (3 c_a + 9 cu c_a) = c_a (3 + 9 cu)
-        bx += wm * m.rho * (R(cx(i)) * t - R(3) * m.ux);
-        by += wm * m.rho * (R(cy(i)) * t - R(3) * m.uy);
-        bz += wm * m.rho * (R(cz(i)) * t - R(3) * m.uz);
-        if constexpr (FORCE) {
-            const R cF = R(cx(i)) * Fx + R(cy(i)) * Fy + R(cz(i)) * Fz;
-            sx += wm * (R(-3) * Fx + R(9) * cF * R(cx(i)));
-            sy += wm * (R(-3) * Fy + R(9) * cF * R(cy(i)));
-            sz += wm * (R(-3) * Fz + R(9) * cF * R(cz(i)));
-        }
-        gx += wm * (R(cx(i)) * t - R(3) * m.ux);
-        gy += wm * (R(cy(i)) * t - R(3) * m.uy);
-        gz += wm * (R(cz(i)) * t - R(3) * m.uz);
+        M0 += wm;
+        if constexpr (cx(i) != 0) { M1x += cx(i) > 0 ? wm : -wm; Mxx += wm; }
+        if constexpr (cy(i) != 0) { M1y += cy(i) > 0 ? wm : -wm; Myy += wm; }
+        if constexpr (cz(i) != 0) { M1z += cz(i) > 0 ? wm : -wm; Mzz += wm; }
+        if constexpr (cx(i) * cy(i) != 0) Mxy += cx(i) * cy(i) > 0 ? wm : -wm;
+        if constexpr (cx(i) * cz(i) != 0) Mxz += cx(i) * cz(i) > 0 ? wm : -wm;
+        if constexpr (cy(i) * cz(i) != 0) Myz += cy(i) * cz(i) > 0 ? wm : -wm;
     });
-    const R ex = g.omega * bx + g.kf * sx, ey = g.omega * by + g.kf * sy, ez = g.omega * bz + g.kf * sz;
+    const R Mux = Mxx * m.ux + Mxy * m.uy + Mxz * m.uz;
+    const R Muy = Mxy * m.ux + Myy * m.uy + Myz * m.uz;
+    const R Muz = Mxz * m.ux + Myz * m.uy + Mzz * m.uz;
+    const R a = M0 * (R(1) - R(1.5) * usq) + R(3) * (M1x * m.ux + M1y * m.uy + M1z * m.uz) +
+                R(4.5) * (m.ux * Mux + m.uy * Muy + m.uz * Muz);
+    const R gx = R(3) * M1x + R(9) * Mux - R(3) * m.ux * M0;
+    const R gy = R(3) * M1y + R(9) * Muy - R(3) * m.uy * M0;
+    const R gz = R(3) * M1z + R(9) * Muz - R(3) * m.uz * M0;
+    R sx = R(0), sy = R(0), sz = R(0);
+    if constexpr (FORCE) {
+        sx = R(9) * (Mxx * Fx + Mxy * Fy + Mxz * Fz) - R(3) * Fx * M0;
+        sy = R(9) * (Mxy * Fx + Myy * Fy + Myz * Fz) - R(3) * Fy * M0;
+        sz = R(9) * (Mxz * Fx + Myz * Fy + Mzz * Fz) - R(3) * Fz * M0;
+    }
+    const R ex = g.omega * (m.rho * gx) + g.kf * sx, ey = g.omega * (m.rho * gy) + g.kf * sy,
+            ez = g.omega * (m.rho * gz) + g.kf * sz;
     const R inv = R(1) / m.rho;
+    // lam_out_j = (1 - omega) mu_j + omega a + e.(c_j - u) / rho
+    const R Ex = ex * inv, Ey = ey * inv, Ez = ez * inv;
+    const R base = g.omega * a - (Ex * m.ux + Ey * m.uy + Ez * m.uz);
     static_for<Q>([&](auto K) {
         constexpr int j = decltype(K)::value;
-        const R v = (R(1) - g.omega) * mu[j] + g.omega * a +
-                    (ex * (R(cx(j)) - m.ux) + ey * (R(cy(j)) - m.uy) + ez * (R(cz(j)) - m.uz)) * inv;
+        R v = (R(1) - g.omega) * mu[j] + base;
+        if constexpr (cx(j) != 0) v = cx(j) > 0 ? v + Ex : v - Ex;
+        if constexpr (cy(j) != 0) v = cy(j) > 0 ? v + Ey : v - Ey;
+        if constexpr (cz(j) != 0) v = cz(j) > 0 ? v + Ez : v - Ez;
         lout.p[j][c] = v;
     });
     if (gF) {
