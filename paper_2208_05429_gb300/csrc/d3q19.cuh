@@ -388,6 +388,21 @@ __device__ __forceinline__ int step_offset(const Geom<R> &g, const Faces &fc)
     return o;
 }
 
+// The periodic-wrap part of step_offset: what a step along (DX, DY, DZ) adds
+// to the plain neighbour offset (0 unless it leaves through a periodic face).
+template <int DX, int DY, int DZ>
+__device__ __forceinline__ int wrap_adj(const Faces &fc)
+{
+    int o = 0;
+    if constexpr (DX < 0) o += fc.adj[0];
+    if constexpr (DX > 0) o += fc.adj[1];
+    if constexpr (DY < 0) o += fc.adj[2];
+    if constexpr (DY > 0) o += fc.adj[3];
+    if constexpr (DZ < 0) o += fc.adj[4];
+    if constexpr (DZ > 0) o += fc.adj[5];
+    return o;
+}
+
 // True when every neighbour of (x,y,z) is an ordinary, unwrapped cell.
 template <class R>
 __device__ __forceinline__ bool interior(const Geom<R> &g, int x, int y, int z)

@@ -615,8 +615,7 @@ static __global__ void __launch_bounds__(RED_THREADS) k_reduce_final(const doubl
 // address of an interior cell; lout.p[j] = lam_out + j slot.
 template <class S, bool FORCE>
 __global__ void __launch_bounds__(128) k_adjoint(Geom<typename S::R> g, Dirs<const typename S::T> fd,
-                                                 Dirs<const typename S::R> lin,
-                                                 const typename S::R *__restrict__ lam_in, Dirs<typename S::R> lout,
+                                                 Dirs<const typename S::R> lin, Dirs<typename S::R> lout,
                                                  double *__restrict__ gF)
 {
     using R = typename S::R;
@@ -632,20 +631,21 @@ __global__ void __launch_bounds__(128) k_adjoint(Geom<typename S::R> g, Dirs<con
     const R usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
     // mu_i = dL/df*_i: the transpose of streaming
     R mu[Q];
-    const bool in = interior(g, x, y, z);
-    static_for<Q>([&](auto K) {
-        constexpr int i = decltype(K)::value;
-        if (in) {
+    if (interior(g, x, y, z)) {
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
             mu[i] = lin.p[i][c];
-        } else {
-            int tx, ty, tz;
-            bool lid;
-            if (link(g, x, y, z, cx(i), cy(i), cz(i), tx, ty, tz, lid))
-                mu[i] = lam_in[i * g.slot + cell_of(g, tx, ty, tz)];
-            else
-                mu[i] = lam_in[opp(i) * g.slot + c];
-        }
-    });
+        });
+    } else {
+        // lin.p[i][c + wrap] is lam_in_i at the (wrapped) target of the push;
+        // lin.p[opp(i)][c + noff[i]] is lam_in_opp(i) of the cell itself
+        const Faces fc = faces_of(g, x, y, z);
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            if (fc.wall & face_mask(cx(i), cy(i), cz(i))) mu[i] = lin.p[opp(i)][c + g.noff[i]];
+            else mu[i] = lin.p[i][c + wrap_adj<cx(i), cy(i), cz(i)>(fc)];
+        });
+    }
     // a = sum mu_i dfeq_i/drho; b = sum mu_i dfeq_i/du; sv = sum mu_i dS_i/du;
     // gv = sum mu_i dS_i/dF|_u.  With wm_i = w_i mu_i and its direction
     // moments M0 = sum wm_i, M1 = sum wm_i c_i, M2 = sum wm_i c_i c_i^T:

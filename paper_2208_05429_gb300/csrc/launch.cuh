@@ -273,8 +273,8 @@ struct Launch {
         const Dirs<R> lout = make_dirs((R *)lam_out, sl);
         Dirs<const R> lin;  // interior gather addresses, one index away
         for (int i = 0; i < Q; ++i) lin.p[i] = (const R *)lam_in + i * sl + g.noff[i];
-        if (force) k_adjoint<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, fd, lin, (const R *)lam_in, lout, gF);
-        else k_adjoint<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, fd, lin, (const R *)lam_in, lout, gF);
+        if (force) k_adjoint<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, fd, lin, lout, gF);
+        else k_adjoint<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, fd, lin, lout, gF);
         return cudaGetLastError();
     }
     static cudaError_t adjoint_seed(const HostGeom &h, int64_t pitch, bool force, const void *f, const void *dLdrho,
