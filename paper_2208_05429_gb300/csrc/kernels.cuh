@@ -255,9 +255,10 @@ __global__ void k_init_eq(Geom<typename S::R> g, typename S::T *__restrict__ f, 
 // ---------------------------------------------------------------------------
 // K1: two-lattice fused collide-and-push (natural -> natural)
 // ---------------------------------------------------------------------------
+// dout.p[i] = dst.p[i] + noff[i]: the push address of an interior cell.
 template <class S, bool FORCE>
 __global__ void __launch_bounds__(128) k_two_lattice(Geom<typename S::R> g, Dirs<const typename S::T> src,
-                                                     Dirs<typename S::T> dst)
+                                                     Dirs<typename S::T> dst, Dirs<typename S::T> dout)
 {
     using R = typename S::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
@@ -268,7 +269,14 @@ __global__ void __launch_bounds__(128) k_two_lattice(Geom<typename S::R> g, Dirs
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
     bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
-    push_store_d<S>(g, dst, x, y, z, c, s);
+    if (interior(g, x, y, z)) {
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            dout.p[i][c] = encode<S, i>(s[i]);
+        });
+    } else {
+        push_store_d<S>(g, dst, x, y, z, c, s);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -33,8 +33,10 @@ struct Launch {
         const Geom<R> g = make_geom<R>(h, pitch);
         const Dirs<const T> a = make_dirs((const T *)src, slot_of(h, pitch));
         const Dirs<T> b = make_dirs((T *)dst, slot_of(h, pitch));
-        if (force) k_two_lattice<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b);
-        else k_two_lattice<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b);
+        Dirs<T> bo;  // push addresses of an interior cell, one index away
+        for (int i = 0; i < Q; ++i) bo.p[i] = b.p[i] + g.noff[i];
+        if (force) k_two_lattice<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo);
+        else k_two_lattice<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo);
         return cudaGetLastError();
     }
     // planes [z0, z1) only
