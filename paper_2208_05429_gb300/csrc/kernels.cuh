@@ -23,6 +23,56 @@
 
 namespace lbm {
 
+// L2 eviction-priority policies and loads/stores that carry one.  The
+// adjoint step streams the recomputed state f^t (evict first) and keeps the
+// adjoint fields lambda and dL/dF, re-read every step, in L2 (evict last):
+// on the 128 x 64 x 64 channel both lambda buffers and dL/dF (93 MB) fit.
+__device__ __forceinline__ uint64_t l2_policy_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+template <class T>
+__device__ __forceinline__ T ld_pol(const T *p, uint64_t pol)
+{
+    T v;
+    if constexpr (sizeof(T) == 4) {
+        unsigned u;
+        asm("ld.global.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(u) : "l"(p), "l"(pol));
+        v = *reinterpret_cast<T *>(&u);
+    } else if constexpr (sizeof(T) == 2) {
+        unsigned short u;
+        asm("ld.global.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(u) : "l"(p), "l"(pol));
+        v = *reinterpret_cast<T *>(&u);
+    } else {
+        unsigned long long u;
+        asm("ld.global.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(u) : "l"(p), "l"(pol));
+        v = *reinterpret_cast<T *>(&u);
+    }
+    return v;
+}
+template <class T>
+__device__ __forceinline__ void st_pol(T *p, T v, uint64_t pol)
+{
+    if constexpr (sizeof(T) == 4) {
+        const unsigned u = *reinterpret_cast<const unsigned *>(&v);
+        asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(u), "l"(pol));
+    } else if constexpr (sizeof(T) == 2) {
+        const unsigned short u = *reinterpret_cast<const unsigned short *>(&v);
+        asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(p), "h"(u), "l"(pol));
+    } else {
+        const unsigned long long u = *reinterpret_cast<const unsigned long long *>(&v);
+        asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(u), "l"(pol));
+    }
+}
+
 // Global store that allocates no L1 line, for values written once per sweep
 // and not read back by the writing CTA.
 template <class T>
@@ -631,8 +681,12 @@ __global__ void __launch_bounds__(128) k_adjoint(Geom<typename S::R> g, Dirs<con
     if (x >= g.nx) return;
     const int64_t n = ncanon(g), cc = canon(g, x, y, z);
     const int c = cell32(g, x, y, z);
+    const uint64_t pf = l2_policy_first(), pl = l2_policy_last();
     R s[Q];
-    load_natural_d<S>(fd, c, s);
+    static_for<Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        s[i] = decode<S, i>(ld_pol(fd.p[i] + c, pf));
+    });
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, cc, n, Fx, Fy, Fz);
     const Mom<R> m = moments_of<R, FORCE>(s, Fx, Fy, Fz);
@@ -642,7 +696,7 @@ __global__ void __launch_bounds__(128) k_adjoint(Geom<typename S::R> g, Dirs<con
     if (interior(g, x, y, z)) {
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;
-            mu[i] = lin.p[i][c];
+            mu[i] = ld_pol(lin.p[i] + c, pl);
         });
     } else {
         // lin.p[i][c + wrap] is lam_in_i at the (wrapped) target of the push;
@@ -650,8 +704,8 @@ __global__ void __launch_bounds__(128) k_adjoint(Geom<typename S::R> g, Dirs<con
         const Faces fc = faces_of(g, x, y, z);
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;
-            if (fc.wall & face_mask(cx(i), cy(i), cz(i))) mu[i] = lin.p[opp(i)][c + g.noff[i]];
-            else mu[i] = lin.p[i][c + wrap_adj<cx(i), cy(i), cz(i)>(fc)];
+            if (fc.wall & face_mask(cx(i), cy(i), cz(i))) mu[i] = ld_pol(lin.p[opp(i)] + c + g.noff[i], pl);
+            else mu[i] = ld_pol(lin.p[i] + c + wrap_adj<cx(i), cy(i), cz(i)>(fc), pl);
         });
     }
     // a = sum mu_i dfeq_i/drho; b = sum mu_i dfeq_i/du; sv = sum mu_i dS_i/du;
@@ -700,13 +754,13 @@ __global__ void __launch_bounds__(128) k_adjoint(Geom<typename S::R> g, Dirs<con
         if constexpr (cx(j) != 0) v = cx(j) > 0 ? v + Ex : v - Ex;
         if constexpr (cy(j) != 0) v = cy(j) > 0 ? v + Ey : v - Ey;
         if constexpr (cz(j) != 0) v = cz(j) > 0 ? v + Ez : v - Ez;
-        lout.p[j][c] = v;
+        st_pol(lout.p[j] + c, v, pl);
     });
     if (gF) {
         const R h = R(0.5) * inv;
-        gF[cc] += (double)(g.kf * gx + ex * h);
-        gF[n + cc] += (double)(g.kf * gy + ey * h);
-        gF[2 * n + cc] += (double)(g.kf * gz + ez * h);
+        st_pol(gF + cc, ld_pol(gF + cc, pl) + (double)(g.kf * gx + ex * h), pl);
+        st_pol(gF + n + cc, ld_pol(gF + n + cc, pl) + (double)(g.kf * gy + ey * h), pl);
+        st_pol(gF + 2 * n + cc, ld_pol(gF + 2 * n + cc, pl) + (double)(g.kf * gz + ez * h), pl);
     }
 }
 
