@@ -14,7 +14,7 @@
 //    "odd" warps (one per tile row) gather plane k from the rings, collide
 //    and scatter into f, and halo warps re-collide the one-cell halo ring
 //    and stage the inputs.  Even and odd warps work in the same interval
-//    between two __syncthreads, two planes apart, so twice as many warps
+//    between two CTA barriers, two planes apart, so twice as many warps
 //    hide each other's latencies.
 //  * Inputs of a plane arrive in a two-slot stage: one TMA tensor copy per
 //    direction for the 32 x TY tile, and cp.async copies for the tile's own
