@@ -74,7 +74,8 @@ enum { LBM_STORAGE_F64 = 0, LBM_STORAGE_F32 = 1, LBM_STORAGE_F32S = 2,
  *                slots (the "revert" of Sec. 3), odd step gathers, collides
  *                and scatters (the "swap_stream" half of Sec. 3)
  *   MERGED       single copy of the lattice, two time steps per sweep
- *                (Sec. 4): one CTA per 32 x 14 column tile marches z, its
+ *                (Sec. 4): one CTA per 32 x 14 column tile (32 x 4 in F64)
+ *                marches z (periodic z included), its
  *                even-step warps collide plane k+2 into shared-memory rings
  *                while its odd-step warps collide plane k and scatter.  The
  *                cells on the tile boundaries (read by up to four tiles) are
@@ -82,8 +83,9 @@ enum { LBM_STORAGE_F64 = 0, LBM_STORAGE_F32 = 1, LBM_STORAGE_F32S = 2,
  *                from the current copy and writes the next one, so tiles
  *                never read what a neighbour has already overwritten (the
  *                role of the intersection layers, Stage I of Alg. 3).  With
- *                an explicit tile_y the older form runs instead: a pre-pass
- *                snapshots the tile shells every sweep.
+ *                an explicit tile_y (or a periodic z with nz = 1) the older
+ *                form runs instead: a pre-pass snapshots the tile shells
+ *                every sweep.
  *   WAVEFRONT    single copy, two time steps per DRAM round trip through the
  *                L2 cache (the cache reuse of Sec. 4.1 and 5.2): one
  *                persistent kernel runs the even step of plane p+L+1 and the
