@@ -74,7 +74,8 @@ __device__ __forceinline__ void st_pol(T *p, T v, uint64_t pol)
 }
 
 // Global store that allocates no L1 line, for values written once per sweep
-// and not read back by the writing CTA.
+// and not read back through the writing SM's L1 (later reads of them go
+// through L2: TMA or cp.async copies, ld.global.cg, or the next launch).
 template <class T>
 __device__ __forceinline__ void st_no_l1(T *p, T v)
 {
