@@ -13,7 +13,8 @@ second).
 
 Three further modes print their own JSON line instead of the benchmark line:
 ``--sweep`` (cavity cubes 64^3 .. 768^3, FP32 and FP16-shifted storage, AA
-and merged, plus the host oracle at 64^3 and 128^3),
+and merged, plus the host oracle at 32^3, 64^3 and 128^3 on all host
+threads and on one),
 ``--precision-study`` (periodic Taylor-Green box 512^3, U0 = 0.04, tau =
 0.52: FP32 / FP16 / BF16 storage against an FP64 run of the same case,
 kinetic energy every 100 steps and max-norm velocity error) and
@@ -338,11 +339,19 @@ def adjoint_leg():
 
 # ------------------------------------------------------------------ CPU legs
 
-def oracle_mlups(n, budget_s, pairs=None):
+def oracle_mlups(n, budget_s, pairs=None, nthreads=None):
     """Time the FP64 oracle (two lattices, OpenMP) on an n^3 cavity: runs
-    `pairs` double steps, or as many as fit in budget_s (at least one)."""
+    `pairs` double steps, or as many as fit in budget_s (at least one), on
+    nthreads host threads (default: as configured)."""
     import numpy as np
     import oracle
+    if nthreads is not None:
+        before = oracle.threads()
+        oracle.threads(nthreads)
+        try:
+            return oracle_mlups(n, budget_s, pairs)
+        finally:
+            oracle.threads(before)
     cfg = oracle.cavity(n, TAU, u_lid=U_LID)
     f = oracle.init_equilibrium(cfg)
     g = np.empty_like(f)
@@ -407,7 +416,7 @@ def run_reference(args):
 def sweep(args):
     """Cavity size sweep: MLUPS and fraction of the measured HBM peak per
     size, storage and schedule (about 500 time steps each, at least ~1 s),
-    and the host oracle at 64^3 and 128^3."""
+    and the host oracle at 32^3, 64^3 and 128^3 on all host threads and on one."""
     import torch
     from paper_2208_05429_gb300 import build
     build.build()
@@ -447,10 +456,11 @@ def sweep(args):
     import oracle
     oracle.build()
     cpu = []
-    for n in (64, 128):
-        rate, done, el = oracle_mlups(n, 5.0)
-        cpu.append({"n": n, "MLUPS": round(rate, 2), "time_steps": done, "seconds": round(el, 2),
-                    "threads": omp_threads()})
+    for n in (32, 64, 128):
+        for nt in (omp_threads(), 1):
+            rate, done, el = oracle_mlups(n, 5.0, nthreads=nt)
+            cpu.append({"n": n, "MLUPS": round(rate, 2), "time_steps": done, "seconds": round(el, 2),
+                        "threads": nt, "nproc": os.cpu_count()})
     print(json.dumps({"mode": "sweep", "workload": "lid-driven cavity n^3, tau 0.55, lid (0.05,0,0)",
                       "peak_GBs": peak, "peak_source": peak_kind, "gpu": rows, "cpu_oracle": cpu}), flush=True)
     return 0

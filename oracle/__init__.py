@@ -97,6 +97,8 @@ def _load():
                 fn = getattr(lib, name)
                 fn.argtypes = argt
                 fn.restype = None
+            lib.orc_threads.argtypes = [ctypes.c_int]
+            lib.orc_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -214,6 +216,12 @@ def step_cells(cfg: Config, f: np.ndarray, cells: np.ndarray) -> np.ndarray:
     lib.orc_step_cells(ctypes.byref(cfg._c()), _ptr(fin), xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                        len(xyz), _ptr(out))
     return out
+
+
+def threads(n: int = 0) -> int:
+    """OpenMP threads of the oracle from now on (n >= 1), or just the number in
+    effect (n = 0).  For host timing only: results do not depend on it."""
+    return int(_load().orc_threads(int(n)))
 
 
 def run(cfg: Config, f: np.ndarray, nsteps: int) -> np.ndarray:

@@ -44,6 +44,9 @@
  * term has no derivative.  It has no counterpart in the paper.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -252,6 +255,20 @@ void orc_step_cells(const orc_cfg *g, const double *f_in, const int64_t *xyz, in
             }
         }
     }
+}
+
+/* Threads of the OpenMP loops from now on (n >= 1; n <= 0 leaves them),
+ * returning the number in effect.  Only the host timing of the oracle sets
+ * it; the results do not depend on it (every cell is computed the same way). */
+int orc_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* nsteps time steps in place on f; tmp is a second lattice of the same size. */

@@ -101,3 +101,19 @@ def test_guo_force_second_moment():
     P = lambda g: np.einsum("q,qa,qb->ab", g, cf, cf)  # noqa: E731
     expected = P(f) - om * (P(f) - P(feq)) + (1.0 - 0.5 * om) * (np.outer(u0, F) + np.outer(F, u0))
     assert np.allclose(P(fs), expected, atol=1e-15)
+
+
+def test_oracle_result_independent_of_threads():
+    """The host timing runs the oracle on one thread and on all of them; every
+    cell is computed the same way, so the states are bitwise equal."""
+    cfg = oracle.cavity(12, 0.6)
+    f0 = oracle.init_equilibrium(cfg)
+    before = oracle.threads()
+    try:
+        oracle.threads(1)
+        one = oracle.run(cfg, f0.copy(), 5)
+        oracle.threads(max(2, before))
+        many = oracle.run(cfg, f0.copy(), 5)
+    finally:
+        oracle.threads(before)
+    assert np.array_equal(one, many)
