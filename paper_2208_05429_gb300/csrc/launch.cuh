@@ -209,20 +209,22 @@ struct Launch {
                                                          make_dirs((const T *)f, slot_of(h, pitch)), (T *)G, si);
         return cudaGetLastError();
     }
-    template <bool F, bool PZ>
+    template <bool F, bool PZ, bool CH>
     static cudaError_t merged3_f(const HostGeom &h, int64_t pitch, void *f, const void *Gc, void *Gn,
-                                 const ShellInfo &si, void *zsave, const void *tmap, int *status, cudaStream_t st)
+                                 const ShellInfo &si, void *zsave, const void *tmap, const void *tmapz, int *status,
+                                 cudaStream_t st)
     {
         constexpr size_t smem = M3L::bytes;
         static bool attr_set = false;  // once per process: not inside a stream capture
         if (!attr_set) {
-            const cudaError_t e = cudaFuncSetAttribute(k_merged3<S, F, M3_TY, PZ>,
+            const cudaError_t e = cudaFuncSetAttribute(k_merged3<S, F, M3_TY, PZ, CH>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             attr_set = true;
         }
-        CUtensorMap map;
+        CUtensorMap map, mapz;
         memcpy(&map, tmap, sizeof(map));
+        memcpy(&mapz, si.nzc > 1 ? tmapz : tmap, sizeof(mapz));
         const Geom<R> g = make_geom<R>(h, pitch);
         const Dirs<T> fd = make_dirs((T *)f, slot_of(h, pitch));
         Dirs<T> fo = fd, go;
@@ -230,17 +232,32 @@ struct Launch {
             fo.p[i] = fd.p[i] + g.noff[i];
             go.p[i] = (T *)Gn + cz(i) * si.gplane + (int64_t)i * M3<M3_TY>::NSP;
         }
-        k_merged3<S, F, M3_TY, PZ><<<dim3(si.ntx, si.nty), M3<M3_TY>::THREADS, smem, st>>>(
-            map, g, fd, fo, go, (const T *)Gc, (T *)Gn, si, (R *)zsave, status);
+        k_merged3<S, F, M3_TY, PZ, CH><<<dim3(si.ntx, si.nty, CH ? si.nzc : 1), M3<M3_TY>::THREADS, smem, st>>>(
+            map, mapz, g, fd, fo, go, (const T *)Gc, (T *)Gn, si, (R *)zsave, status);
         return cudaGetLastError();
     }
     static cudaError_t merged3(const HostGeom &h, int64_t pitch, bool force, void *f, const void *Gc, void *Gn,
-                               const ShellInfo &si, void *zsave, const void *tmap, int *status, cudaStream_t st)
+                               const ShellInfo &si, void *zsave, const void *tmap, const void *tmapz, int *status,
+                               cudaStream_t st)
     {
-        if (h.per[2]) return force ? merged3_f<true, true>(h, pitch, f, Gc, Gn, si, zsave, tmap, status, st)
-                                   : merged3_f<false, true>(h, pitch, f, Gc, Gn, si, zsave, tmap, status, st);
-        return force ? merged3_f<true, false>(h, pitch, f, Gc, Gn, si, zsave, tmap, status, st)
-                     : merged3_f<false, false>(h, pitch, f, Gc, Gn, si, zsave, tmap, status, st);
+        if (h.per[2])
+            return force ? merged3_f<true, true, false>(h, pitch, f, Gc, Gn, si, zsave, tmap, tmapz, status, st)
+                         : merged3_f<false, true, false>(h, pitch, f, Gc, Gn, si, zsave, tmap, tmapz, status, st);
+        if (si.nzc > 1)
+            return force ? merged3_f<true, false, true>(h, pitch, f, Gc, Gn, si, zsave, tmap, tmapz, status, st)
+                         : merged3_f<false, false, true>(h, pitch, f, Gc, Gn, si, zsave, tmap, tmapz, status, st);
+        return force ? merged3_f<true, false, false>(h, pitch, f, Gc, Gn, si, zsave, tmap, tmapz, status, st)
+                     : merged3_f<false, false, false>(h, pitch, f, Gc, Gn, si, zsave, tmap, tmapz, status, st);
+    }
+    static cudaError_t zcopy(const HostGeom &h, int64_t pitch, const void *f, void *zc, const ShellInfo &si,
+                             cudaStream_t st)
+    {
+        if (si.nzc < 2) return cudaSuccess;
+        const int64_t total = (int64_t)Q * 2 * (si.nzc - 1) * h.ny * pitch;
+        const int64_t nb = (total + 255) / 256;
+        k_zcopy<S><<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, st>>>(make_geom<R>(h, pitch), (const T *)f, (T *)zc,
+                                                                      si.nzc);
+        return cudaGetLastError();
     }
     static cudaError_t wavefront(const HostGeom &h, int64_t pitch, bool force, void *f, const void *sched, int grid,
                                  cudaStream_t st)
@@ -330,6 +347,7 @@ StorageOps make_ops()
     o.m3_zsave = M3<L::M3_TY>::ZSAVE;
     o.shell_gather = &L::shell_gather;
     o.merged3 = &L::merged3;
+    o.zcopy = &L::zcopy;
     o.adjoint = &L::adjoint;
     o.adjoint_seed = &L::adjoint_seed;
     o.canon_to_pitched = &L::canon_to_pitched;

@@ -36,6 +36,7 @@ struct lbm_handle {
     ShellInfo si;
     void *G3[2];       // shadow of the tile shells: current / next
     void *Z3;          // periodic z: per-tile values of the image planes
+    void *ZC;          // z split into chunks: copy of the planes next to each chunk boundary
     int g3cur;
     bool g3fresh;      // G3[g3cur] mirrors the shell cells of f
     // cached CUDA graph of GRAPH_STEPS time steps from state gfrom to gto,
@@ -55,6 +56,7 @@ struct lbm_handle {
         }
     } gfrom, gto;
     CUtensorMap tmap;  // TMA descriptor of f (MERGED)
+    CUtensorMap tmapz; // the same over ZC (shadow-shell sweep with si.nzc > 1)
     int *status;       // device status word: bits 2 / 4 = a bounded wait gave up
     int *wf_words;     // WAVEFRONT schedule (device): entries, ticket, done flags
     int wf_nentries, wf_rb, wf_nrb, wf_grid, wf_ahead;
@@ -159,6 +161,24 @@ bool uses_m3(const lbm_config &c)
     return (double)shell_info(c).gplane * (double)c.nz < 2147483647.0;
 }
 
+// Streaming multiprocessors of the current device (152 when it cannot be
+// queried, e.g. on a host without a GPU sizing a buffer).
+int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) {
+            n = v;
+        } else {
+            cudaGetLastError();
+            n = 152;
+        }
+    }
+    return n;
+}
+
 ShellInfo shell_info(const lbm_config &c)
 {
     ShellInfo si;
@@ -169,7 +189,36 @@ ShellInfo shell_info(const lbm_config &c)
     si.hb = (int)(c.ny / si.nty);
     si.rem = (int)(c.ny % si.nty);
     si.gplane = (int64_t)si.ntx * si.nty * Q * o->m3_nsp;
+    // z chunks of at least 4 planes, one CTA per tile and chunk (not with
+    // periodic z, whose march wraps): the count that minimises waves of CTAs
+    // (one per SM) x planes per CTA, a chunk costing about 3 planes more
+    // than its own (the march prologue and the even steps of the planes
+    // next to it); kept at 1 unless that saves 5% or more
+    si.nzc = 1;
+    if (c.face_bc[4] != LBM_BC_PERIODIC) {
+        const int64_t tiles = (int64_t)si.ntx * si.nty, sms = sm_count();
+        auto cost = [&](int64_t n) {
+            return (double)((tiles * n + sms - 1) / sms) * ((double)c.nz / (double)n + (n > 1 ? 3.0 : 0.0));
+        };
+        double best = cost(1);
+        const double one = best;
+        for (int64_t n = 2; n <= c.nz / 4; ++n) {
+            if (cost(n) < best) {
+                best = cost(n);
+                si.nzc = (int)n;
+            }
+        }
+        if (best > 0.95 * one) si.nzc = 1;
+    }
     return si;
+}
+
+// Elements of the chunk-boundary copy: 19 x 2 (nzc - 1) planes.
+int64_t zcopy_elems(const lbm_config &c)
+{
+    if (!uses_m3(c)) return 0;
+    const ShellInfo si = shell_info(c);
+    return si.nzc > 1 ? (int64_t)Q * 2 * (si.nzc - 1) * c.ny * pitch_of(c) : 0;
 }
 
 int64_t ghost_elems(const lbm_config &c)
@@ -180,7 +229,7 @@ int64_t ghost_elems(const lbm_config &c)
 }
 
 struct Layout {
-    size_t f, f2, G, G3, Z3, wf, partial, red_out, flag, status, total;
+    size_t f, f2, G, G3, Z3, ZC, wf, partial, red_out, flag, status, total;
 };
 
 // WAVEFRONT schedule words: entries (2 nz + 4), ticket, done[nz * ny] (at
@@ -232,6 +281,7 @@ Layout layout_of(const lbm_config &c)
         const ShellInfo si = shell_info(c);
         off += align_up((size_t)si.ntx * si.nty * ops_for(c.storage)->m3_zsave * real_size_of(c.storage));
     }
+    L.ZC = off; off += align_up((size_t)zcopy_elems(c) * es);
     L.wf = off; off += align_up((size_t)wf_ints(c) * sizeof(int));
     L.partial = off; off += align_up(sizeof(double) * 5 * RED_BLOCKS_MAX);
     L.red_out = off; off += align_up(sizeof(double) * 5);
@@ -303,10 +353,12 @@ EncodeTiledFn encode_tiled()
     return fn;
 }
 
-// 4D map over f[q][z][y][x] (x extent nx, row pitch nxp) with a box of one
-// tile plane (tx x ty) and bq directions.
-bool make_tmap(const lbm_config &c, int tx, int ty, int bq, void *f, CUtensorMap *map)
+// 4D map over f[q][z][y][x] (x extent nx, row pitch nxp, nzext planes per
+// direction: nz for the lattice) with a box of one tile plane (tx x ty) and
+// bq directions.
+bool make_tmap(const lbm_config &c, int tx, int ty, int bq, void *f, CUtensorMap *map, int64_t nzext = 0)
 {
+    if (nzext <= 0) nzext = c.nz;
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return false;
     CUtensorMapDataType dt;
@@ -317,8 +369,8 @@ bool make_tmap(const lbm_config &c, int tx, int ty, int bq, void *f, CUtensorMap
     default: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; break;
     }
     const cuuint64_t es = elem_size_of(c.storage), nxp = (cuuint64_t)pitch_of(c);
-    const cuuint64_t dims[4] = {(cuuint64_t)c.nx, (cuuint64_t)c.ny, (cuuint64_t)c.nz, (cuuint64_t)Q};
-    const cuuint64_t strides[3] = {nxp * es, nxp * (cuuint64_t)c.ny * es, nxp * (cuuint64_t)c.ny * (cuuint64_t)c.nz * es};
+    const cuuint64_t dims[4] = {(cuuint64_t)c.nx, (cuuint64_t)c.ny, (cuuint64_t)nzext, (cuuint64_t)Q};
+    const cuuint64_t strides[3] = {nxp * es, nxp * (cuuint64_t)c.ny * es, nxp * (cuuint64_t)c.ny * (cuuint64_t)nzext * es};
     const cuuint32_t box[4] = {(cuuint32_t)tx, (cuuint32_t)ty, 1u, (cuuint32_t)bq};
     const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
     return fn(map, dt, 4, f, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -490,6 +542,7 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
         h->G3[0] = b + L.G3;
         h->G3[1] = b + L.G3 + gbytes;
         h->Z3 = cfg->face_bc[4] == LBM_BC_PERIODIC ? b + L.Z3 : nullptr;
+        h->ZC = h->si.nzc > 1 ? b + L.ZC : nullptr;
     }
     h->g3cur = 0;
     h->g3fresh = false;
@@ -502,7 +555,9 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
     int64_t nb = (n + 255) / 256;
     h->red_blocks = (int)(nb < RED_BLOCKS_MAX ? nb : RED_BLOCKS_MAX);
     const bool tmap_ok = cfg->variant != LBM_VARIANT_MERGED ||
-                         (h->m3 ? make_tmap(*cfg, 32, h->ops->m3_ty, 1, h->f, &h->tmap)
+                         (h->m3 ? make_tmap(*cfg, 32, h->ops->m3_ty, 1, h->f, &h->tmap) &&
+                                      (!h->ZC || make_tmap(*cfg, 32, h->ops->m3_ty, 1, h->ZC, &h->tmapz,
+                                                           2 * (int64_t)(h->si.nzc - 1)))
                                 : make_tmap(*cfg, h->ti.TX, h->ti.TY, Q, h->f, &h->tmap));
     if (!tmap_ok ||
         cudaMemsetAsync(buf, 0, L.total, h->stream) != cudaSuccess) {
@@ -670,9 +725,13 @@ static int step_units(lbm_handle *h, int64_t n)
                     }));
                     h->g3fresh = true;
                 }
+                if (h->ZC)
+                    CK(timed(h, LBM_KERNEL_SNAPSHOT, [&] {
+                        return o.zcopy(h->hg, h->nxp, h->f, h->ZC, h->si, h->stream);
+                    }));
                 CK(timed(h, LBM_KERNEL_MERGED, [&] {
                     return o.merged3(h->hg, h->nxp, h->force, h->f, h->G3[h->g3cur], h->G3[h->g3cur ^ 1], h->si,
-                                     h->Z3, &h->tmap, h->status, h->stream);
+                                     h->Z3, &h->tmap, &h->tmapz, h->status, h->stream);
                 }));
                 h->g3cur ^= 1;
                 n -= 2; h->t += 2;

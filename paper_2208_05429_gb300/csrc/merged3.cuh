@@ -159,6 +159,25 @@ __global__ void __launch_bounds__(256) k_shell_gather(Geom<typename S::R> g, Dir
 }
 
 
+// Copies the planes zb-1 and zb of every boundary zb = (b+1) nz / nzc between
+// z chunks b and b+1 into zc[d][2b + s][y][x] (s = 0, 1), before the sweep
+// in which both chunks write them.
+template <class S>
+__global__ void __launch_bounds__(256) k_zcopy(Geom<typename S::R> g, const typename S::T *__restrict__ f,
+                                               typename S::T *__restrict__ zc, int nzc)
+{
+    const int64_t per_plane = (int64_t)g.ny * g.nxp;
+    const int np = 2 * (nzc - 1);
+    const int64_t total = (int64_t)Q * np * per_plane;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = idx % per_plane, t = idx / per_plane;
+        const int p = (int)(t % np), d = (int)(t / np);
+        const int zb = (int)((int64_t)((p >> 1) + 1) * g.nz / nzc);
+        zc[idx] = f[d * g.slot + (int64_t)(zb - 1 + (p & 1)) * per_plane + r];
+    }
+}
+
 // CTA-wide barrier that the warps may reach from different code locations
 // (every thread arrives the same number of times).
 __device__ __forceinline__ void cta_barrier() { asm volatile("barrier.sync 0;" ::: "memory"); }
@@ -192,7 +211,7 @@ __host__ __device__ constexpr int xyidx(int i)
     return n;
 }
 
-template <class S, bool FORCE, int TY, bool PERZ>
+template <class S, bool FORCE, int TY, bool PERZ, bool CHUNK>
 struct M3Cta {
     using R = typename S::R;
     using T = typename S::T;
@@ -211,16 +230,18 @@ struct M3Cta {
     T *__restrict__ Gn;
     const ShellInfo &si;
     const CUtensorMap *tmap;
+    const CUtensorMap *tmapz;  // the z-chunk boundary planes (z split into chunks), else unused
     R *zsave;  // periodic z: this tile's save area (ZSAVE elements), else null
     unsigned char *smem;
     R *ringm, *ring0, *ringp, *srest, *szp, *szm;
     int *gtab;
     uint64_t *bar;
     int role, x0, y0, tw, th, lx, ly, x, y, pos, tc, hidx, nx, ny, nz, goff, cxy, inoff, sub;
+    // z chunk jc of nzc: odd steps of planes [zc0, zc1), loaded planes from qb
+    int jc, nzc, zc0, zc1, qb;
     unsigned gmask, wxy, lxy;
     bool active, perx, pery, xybnd, timed_out;
     static constexpr bool perz = PERZ;
-    static constexpr int zoff = PERZ ? 1 : 0;  // periodic z: the march starts at the image plane -1
 
     __device__ __forceinline__ M3Cta(const Geom<R> &g_, const Dirs<T> &fd_, const Dirs<T> &fo_, const Dirs<T> &go_,
                                      const T *Gc_, T *Gn_, const ShellInfo &si_, const CUtensorMap *tmap_, R *zs,
@@ -357,7 +378,7 @@ struct M3Cta {
     }
     // Planes of the march are virtual: with periodic z they run from the
     // image -1 of plane nz-1 to the image nz of plane 0.  Stage slots count
-    // the loaded planes u = q + zoff.
+    // the loaded planes u = q - qb.
     __device__ __forceinline__ int phys(int q) const
     {
         if constexpr (PERZ) return q < 0 ? q + nz : (q >= nz ? q - nz : q);
@@ -365,22 +386,36 @@ struct M3Cta {
     }
     __device__ __forceinline__ T *tile_block(int q) const
     {
-        return reinterpret_cast<T *>(smem + ((q + zoff) & 1) * SM::slot_bytes);
+        return reinterpret_cast<T *>(smem + ((q - qb) & 1) * SM::slot_bytes);
     }
     __device__ __forceinline__ unsigned char *halo_block(int q) const
     {
-        return smem + ((q + zoff) & 1) * SM::slot_bytes + SM::tile_bytes;
+        return smem + ((q - qb) & 1) * SM::slot_bytes + SM::tile_bytes;
+    }
+
+    // z split into chunks: the two planes on either side of a chunk boundary
+    // are written by both chunks during the sweep, so both read them from a
+    // copy taken before it (planes 2b and 2b+1 of the copy: zb-1 and zb for
+    // the boundary zb between chunks b and b+1); -1 for a plane read from f.
+    __device__ __forceinline__ int zcopy_plane(int q) const
+    {
+        if (jc > 0 && (q == zc0 - 1 || q == zc0)) return 2 * (jc - 1) + (q - zc0 + 1);
+        if (jc < nzc - 1 && (q == zc1 - 1 || q == zc1)) return 2 * jc + (q - zc1 + 1);
+        return -1;
     }
 
     // Halo warps: start the copies of plane q into its stage slot.
     __device__ __forceinline__ void issue_stage(int q)
     {
-        uint64_t *b = &bar[(q + zoff) & 1];
+        uint64_t *b = &bar[(q - qb) & 1];
         T *tb = tile_block(q);
         const int pz = phys(q);
         if (hidx == 0) {
             mbar_arrive_expect_tx(b, SM::tma_bytes);
-            for (int d = 0; d < Q; ++d) tma_load_4d(tb + d * DST, tmap, x0, y0, pz, d, b);
+            const int zq = CHUNK ? zcopy_plane(q) : -1;
+            const CUtensorMap *mp = zq >= 0 ? tmapz : tmap;
+            const int zz = zq >= 0 ? zq : pz;
+            for (int d = 0; d < Q; ++d) tma_load_4d(tb + d * DST, mp, x0, y0, zz, d, b);
         }
         // the tile's own shell cells: 16-byte chunks of its shadow rows
         const T *gs = Gc + pz * si.gplane + (int64_t)(blockIdx.y * si.ntx + blockIdx.x) * Q * NSP;
@@ -403,7 +438,7 @@ struct M3Cta {
 
     __device__ __forceinline__ void wait_stage(int q)
     {
-        const int u = q + zoff;
+        const int u = q - qb;
         if (!mbar_wait_bounded(&bar[u & 1], (unsigned)((u >> 1) & 1))) timed_out = true;
     }
 
@@ -563,16 +598,19 @@ struct M3Cta {
     }
 };
 
-template <class S, bool FORCE, int TY, bool PERZ>
+template <class S, bool FORCE, int TY, bool PERZ, bool CHUNK>
 __global__ void __launch_bounds__(M3<TY>::THREADS, 1)
-    k_merged3(const __grid_constant__ CUtensorMap tmap, Geom<typename S::R> g, Dirs<typename S::T> fd,
-              Dirs<typename S::T> fo, Dirs<typename S::T> go, const typename S::T *__restrict__ Gc,
-              typename S::T *__restrict__ Gn, ShellInfo si, typename S::R *__restrict__ zsave, int *__restrict__ status)
+    k_merged3(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmapz,
+              Geom<typename S::R> g, Dirs<typename S::T> fd, Dirs<typename S::T> fo, Dirs<typename S::T> go,
+              const typename S::T *__restrict__ Gc, typename S::T *__restrict__ Gn, ShellInfo si,
+              typename S::R *__restrict__ zsave, int *__restrict__ status)
 {
-    using C = M3Cta<S, FORCE, TY, PERZ>;
+    static_assert(!(PERZ && CHUNK), "a periodic z march is not split");
+    using C = M3Cta<S, FORCE, TY, PERZ, CHUNK>;
     using SM = typename C::SM;
     extern __shared__ __align__(128) unsigned char smem[];
     C c(g, fd, fo, go, Gc, Gn, si, &tmap, zsave, smem);
+    c.tmapz = &tmapz;
     int *abort_flag = reinterpret_cast<int *>(smem + SM::flag_off);
     const int nz = g.nz;
     if (threadIdx.x == 0) {
@@ -584,9 +622,17 @@ __global__ void __launch_bounds__(M3<TY>::THREADS, 1)
     c.fill_gtab();
     __syncthreads();
     c.setup();
-    // planes loaded from memory: -zoff .. last; with periodic z the planes
-    // nz-1 and nz are restored at the end
-    const int last = nz - 1 - c.zoff;
+    // z chunk blockIdx.z of si.nzc (one chunk with periodic z): odd steps of
+    // planes [zc0, zc1), even steps of the loaded planes qb .. last, one
+    // plane beyond the chunk on either side where it has a neighbour.  With
+    // periodic z the planes -1 .. nz-2 are loaded and nz-1, nz restored.
+    c.nzc = CHUNK ? si.nzc : 1;
+    c.jc = CHUNK ? (int)blockIdx.z : 0;
+    c.zc0 = CHUNK ? (int)((int64_t)c.jc * nz / c.nzc) : 0;
+    c.zc1 = CHUNK ? (int)((int64_t)(c.jc + 1) * nz / c.nzc) : nz;
+    c.qb = PERZ ? -1 : (CHUNK && c.zc0 > 0 ? c.zc0 - 1 : 0);
+    const int last = PERZ ? nz - 2 : (CHUNK && c.zc1 < nz ? c.zc1 : nz - 1);
+    const int kend = CHUNK ? c.zc1 : nz;
     // interval k: even and halo warps collide plane k+2, odd warps plane k;
     // the halo warps start loading plane k+3 into the slot plane k+1 freed.
     // The roles run separate loops over the same intervals (one barrier
@@ -595,18 +641,18 @@ __global__ void __launch_bounds__(M3<TY>::THREADS, 1)
     if (c.role == C::ODD) {
         typename S::R sk[Q];
         bool held = false;
-        for (int k = -2 - c.zoff; k < nz; ++k) {
+        for (int k = c.qb - 2; k < kend; ++k) {
             if (held) c.scatter(k - 1, sk);
-            held = k >= 0 && c.active;
+            held = k >= c.zc0 && c.active;
             if (held) c.consume(k, sk);
             cta_barrier();
             if (*abort_flag) goto bail;
         }
-        if (held) c.scatter(nz - 1, sk);
+        if (held) c.scatter(kend - 1, sk);
         return;
     }
-    if (c.role == C::HALO) c.issue_stage(-c.zoff);
-    for (int k = -2 - c.zoff; k < nz; ++k) {
+    if (c.role == C::HALO) c.issue_stage(c.qb);
+    for (int k = c.qb - 2; k < kend; ++k) {
         const int q = k + 2;
         if (c.role == C::HALO && q + 1 <= last) c.issue_stage(q + 1);
         if (q <= last) {

@@ -36,6 +36,7 @@ struct ShellInfo {
     int ntx, nty;      // tiles along x and y
     int hb, rem;       // band heights: hb + 1 for the first rem bands, else hb
     int64_t gplane;    // elements of one z-plane of G
+    int nzc;           // z chunks marched by separate CTAs (1 with periodic z)
 };
 
 enum { PARITY_NATURAL = 0, PARITY_A = 1 };
@@ -78,9 +79,14 @@ struct StorageOps {
     cudaError_t (*shell_gather)(const HostGeom &, int64_t pitch, const void *f, void *G, const ShellInfo &,
                                 cudaStream_t);
     // tmap: CUtensorMap of f with a box of one direction of a 32 x m3_ty tile;
+    // tmapz: the same over the chunk-boundary copy (nzc > 1, else unused);
     // zsave: m3_zsave elements per tile with periodic z (else unused)
     cudaError_t (*merged3)(const HostGeom &, int64_t pitch, bool force, void *f, const void *Gcur, void *Gnext,
-                           const ShellInfo &, void *zsave, const void *tmap, int *status, cudaStream_t);
+                           const ShellInfo &, void *zsave, const void *tmap, const void *tmapz, int *status,
+                           cudaStream_t);
+    // copy of the planes zb-1 and zb of every z-chunk boundary zb into zc
+    // ([19][2 (nzc-1)][ny][pitch], stored elements)
+    cudaError_t (*zcopy)(const HostGeom &, int64_t pitch, const void *f, void *zc, const ShellInfo &, cudaStream_t);
     // persistent plane-wavefront sweep (two time steps); sched points to a
     // WaveSchedule (device pointers inside), grid = number of CTAs
     cudaError_t (*wavefront)(const HostGeom &, int64_t pitch, bool force, void *f, const void *sched, int grid,

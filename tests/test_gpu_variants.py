@@ -220,3 +220,27 @@ def test_random_shapes_merged_and_wavefront_equal_aa(gpu, seed):
         load_state(lat, f0)
         lat.step(nsteps)
         assert torch.equal(_raw(lat), want), (variant, cfg.nx, cfg.ny, cfg.nz, cfg.bc, storage, nsteps)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+@pytest.mark.parametrize("shape", [(40, 20, 8), (33, 17, 13), (64, 30, 29)])
+def test_merged_z_chunks_equal_aa(gpu, shape, storage):
+    """With fewer tiles than SMs the shadow-shell sweep splits z into chunks
+    (one CTA per tile and chunk; the planes next to a chunk boundary come
+    from a copy taken before the sweep).  On 152 SMs these shapes give
+    two, three and seven chunks of 4 or 5 planes, with a wall and a lid on
+    the z faces."""
+    import torch
+    import oracle
+    from oracle import BC_LID, BC_PERIODIC, BC_WALL, FORCE_UNIFORM
+    nx, ny, nz = shape
+    cfg = oracle.Config(nx=nx, ny=ny, nz=nz, tau=0.7, bc=(BC_WALL, BC_WALL, BC_PERIODIC, BC_PERIODIC, BC_WALL, BC_LID),
+                        u_lid=(0.03, -0.01, 0.0), force_mode=FORCE_UNIFORM, force_uniform=(2e-6, 0.0, -1e-6))
+    f0 = start_state(cfg, seed=nz)
+    ref = make_gpu(cfg, storage, "aa")
+    load_state(ref, f0)
+    ref.step(6)
+    lat = make_gpu(cfg, storage, "merged")
+    load_state(lat, f0)
+    lat.step(6)
+    assert torch.equal(_raw(lat), _raw(ref))
