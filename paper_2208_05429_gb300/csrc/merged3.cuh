@@ -27,6 +27,11 @@
 //    cell to G_next as well as to f.  No CTA reads what another CTA writes
 //    during the sweep, so tiles need no synchronisation at all, and f stays
 //    the complete state after every sweep.
+//  * With fewer tiles than SMs the march is split along z into chunks, one
+//    CTA per tile and chunk (CHUNK = true).  A chunk also collides the
+//    plane beyond each of its ends (even step only); the two planes next to
+//    a chunk boundary, which both chunks write, are loaded from a copy made
+//    before the sweep (k_zcopy).
 //
 // HBM traffic per two steps: every population read and written once, plus
 // the shell shadow (read once by its owner, written once): 2 x 19 x
