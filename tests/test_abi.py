@@ -94,3 +94,26 @@ def test_create_without_gpu_fails_cleanly(cuda_lib):
     cfg = lbm.lbm_config_default()
     with pytest.raises(lbm.LbmError):
         lbm.lbm_create(cfg, 0)
+
+
+def test_required_bytes_merged_z_chunks(cuda_lib):
+    """A 64^3 cavity gives the shadow-shell sweep 10 column tiles (32 x 14),
+    fewer than the 152 SMs of a GB300 (the count assumed without a GPU), so
+    z is split into chunks and the handle also holds the copy of the two
+    planes next to every chunk boundary: 19 x 2 (nzc - 1) planes."""
+    n, es, nsp, sms = 64, 4, 88, 152
+    tiles = ((n + 31) // 32) * ((n + 13) // 14)
+
+    def cost(k):
+        return ((tiles * k + sms - 1) // sms) * (n / k + (3 if k > 1 else 0))
+
+    nzc = min(range(1, n // 4 + 1), key=lambda k: (cost(k), k))
+    if cost(nzc) > 0.95 * cost(1):
+        nzc = 1
+    assert nzc > 1
+    pop = 19 * n ** 3 * es
+    shadow = 2 * tiles * 19 * nsp * n * es
+    zcopy = 19 * 2 * (nzc - 1) * n * n * es
+    mg = lbm.make_config((n, n, n), 0.6, lbm.CAVITY_BC, u_lid=(0.05, 0.0, 0.0), storage="f32", variant="merged")
+    extra = lbm.lbm_required_bytes(mg) - pop - shadow - zcopy
+    assert 0 <= extra < 64 * 1024
