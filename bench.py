@@ -277,9 +277,12 @@ def e2e_leg(n, storage, variant, steps, warmup):
         start.record(st)
         dev_f.copy_(host_f, non_blocking=True)
         lat.init_populations(dev_f)
-        for k in range(steps):
-            lat.step(2)
-            if (k + 1) % every == 0:
+        done = 0
+        while done < steps:  # one step(n) call per reduction interval
+            k = min(every, steps - done)
+            lat.step(2 * k)
+            done += k
+            if k == every:
                 lat.reduce()
                 reads += 1
         rho, u = lat.moments(torch.float32)
