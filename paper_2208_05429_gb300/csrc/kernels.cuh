@@ -604,23 +604,25 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_partial(Geom<typename S:
         R s[Q];
         if constexpr (APAR) load_aparity<S>(g, f, x, y, z, s);
         else load_natural<S>(g, f, x, y, z, s);
-        double dr = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+        // per-cell moments in the compute type (FP64 for FP64 storage), the
+        // sums over cells in FP64; rho = 1 + dr is formed in FP64
+        R dr = R(0), jx = R(0), jy = R(0), jz = R(0);
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;
-            const double v = (double)s[i];
+            const R v = s[i];
             dr += v;
-            if constexpr (cx(i) != 0) jx += cx(i) * v;
-            if constexpr (cy(i) != 0) jy += cy(i) * v;
-            if constexpr (cz(i) != 0) jz += cz(i) * v;
+            if constexpr (cx(i) != 0) jx = cx(i) > 0 ? jx + v : jx - v;
+            if constexpr (cy(i) != 0) jy = cy(i) > 0 ? jy + v : jy - v;
+            if constexpr (cz(i) != 0) jz = cz(i) > 0 ? jz + v : jz - v;
         });
         R Fx, Fy, Fz;
         force_at<R, FORCE>(g, cc, n, Fx, Fy, Fz);
-        const double rho = 1.0 + dr;
-        const double ux = (jx + 0.5 * (double)Fx) / rho, uy = (jy + 0.5 * (double)Fy) / rho,
-                     uz = (jz + 0.5 * (double)Fz) / rho;
-        const double ke = 0.5 * rho * (ux * ux + uy * uy + uz * uz);
+        const R rho = R(1) + dr, inv = R(1) / rho;
+        const R ux = (jx + R(0.5) * Fx) * inv, uy = (jy + R(0.5) * Fy) * inv, uz = (jz + R(0.5) * Fz) * inv;
+        const R ke = R(0.5) * rho * (ux * ux + uy * uy + uz * uz);
         if (!isfinite(rho) || !isfinite(ke)) bad = true;
-        acc[0] += rho; acc[1] += jx; acc[2] += jy; acc[3] += jz; acc[4] += ke;
+        acc[0] += 1.0 + (double)dr; acc[1] += (double)jx; acc[2] += (double)jy; acc[3] += (double)jz;
+        acc[4] += (double)ke;
     }
     if (bad) atomicOr(flag, 1);
     __shared__ double red[5][RED_THREADS / 32];
