@@ -92,7 +92,8 @@ enum { LBM_STORAGE_F64 = 0, LBM_STORAGE_F32 = 1, LBM_STORAGE_F32S = 2,
  *                persistent kernel runs the even step of plane p+L+1 and the
  *                odd step of plane p as ordered work items; the few planes in
  *                flight stay in L2 between their two steps.  The lead L
- *                (default 3 planes) can be set at handle creation with the
+ *                (default 3 planes, 5 with F16S and BF16S storage) can be
+ *                set at handle creation with the
  *                environment variable LBM_WAVEFRONT_AHEAD (1..64), the
  *                cells per work item (default 2048, whole rows) with
  *                LBM_WAVEFRONT_ITEM_CELLS and the resident CTAs per SM
