@@ -76,7 +76,9 @@ enum { LBM_STORAGE_F64 = 0, LBM_STORAGE_F32 = 1, LBM_STORAGE_F32S = 2,
  *   MERGED       single copy of the lattice, two time steps per sweep
  *                (Sec. 4): one CTA per 32 x 14 column tile (32 x 4 in F64)
  *                marches z (periodic z included; with fewer tiles than SMs,
- *                one CTA per tile and z chunk of at least 4 planes), its
+ *                one CTA per tile and z chunk of at least 4 planes; the
+ *                environment variable LBM_MERGED_ZCHUNKS sets the chunk
+ *                count at handle creation), its
  *                even-step warps collide plane k+2 into shared-memory rings
  *                while its odd-step warps collide plane k and scatter.  The
  *                cells on the tile boundaries (read by up to four tiles) are

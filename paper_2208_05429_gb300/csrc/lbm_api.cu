@@ -209,6 +209,11 @@ ShellInfo shell_info(const lbm_config &c)
             }
         }
         if (best > 0.95 * one) si.nzc = 1;
+        // explicit count (tuning): LBM_MERGED_ZCHUNKS, clamped to 1 .. nz / 4
+        if (const char *env = getenv("LBM_MERGED_ZCHUNKS")) {
+            const int64_t v = atoll(env), cap = c.nz / 4 > 1 ? c.nz / 4 : 1;
+            if (v >= 1) si.nzc = (int)(v < cap ? v : cap);
+        }
     }
     return si;
 }
