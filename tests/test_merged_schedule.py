@@ -43,3 +43,124 @@ def test_z_chunk_plane_sources():
                     else:
                         assert all(q not in w for j2, w in written.items() if j2 != j), (nz, nzc, j, q)
             assert odd == list(range(nz))
+
+
+def _shadow_emulation(C, nx, ny, nz, per, TY):
+    """Index rules of k_merged3's shell shadow (z not periodic): every shadow
+    entry of every plane is written exactly once per sweep, every ring and
+    halo access stays in its buffer, and the cells with shell targets are
+    exactly the band cells the odd warps take first."""
+    Q, TX, W, H = 19, 32, 34, TY + 2
+    NPOS, NS = W * H, 2 * TX + 2 * (TY - 2)
+    NSP, NH = (NS + 7) // 8 * 8, 2 * W + 2 * TY
+    opp = [0] + [i + 9 for i in range(1, 10)] + [i - 9 for i in range(10, 19)]
+    ntx, nty = (nx + 31) // 32, (ny + TY - 1) // TY
+    hb, rem = ny // nty, ny % nty
+    gplane = ntx * nty * Q * NSP
+
+    def band_of(by):
+        return by * hb + min(by, rem), hb + (1 if by < rem else 0)
+
+    def band_at(y):
+        big = rem * (hb + 1)
+        return y // (hb + 1) if y < big else rem + (y - big) // hb
+
+    def shell_slot(lx, ly, tw, th):
+        if ly == 0:
+            return lx
+        if ly == th - 1:
+            return 32 + lx
+        if lx == 0:
+            return 64 + ly - 1
+        if lx == tw - 1:
+            return 64 + (TY - 2) + ly - 1
+        return -1
+
+    def shell_offset(x, y):
+        bx, by = x >> 5, band_at(y)
+        y0, th = band_of(by)
+        tw = min(32, nx - 32 * bx)
+        s = shell_slot(x - 32 * bx, y - y0, tw, th)
+        return -1 if s < 0 else (by * ntx + bx) * Q * NSP + s
+
+    def wrap(v, n, p):
+        if 0 <= v < n:
+            return v, True
+        return (v % n, True) if p else (v, False)
+
+    expect = set()
+    for y in range(ny):
+        for x in range(nx):
+            o = shell_offset(x, y)
+            if o >= 0:
+                for i in range(Q):
+                    assert o + i * NSP not in expect and o + i * NSP < gplane
+                    expect.add(o + i * NSP)
+    written = set()
+    for by in range(nty):
+        y0, th = band_of(by)
+        for bx in range(ntx):
+            x0, tw = 32 * bx, min(32, nx - 32 * bx)
+            gtab = [-1] * NPOS
+            for p in range(NPOS):
+                px, py = p % W - 1, p // W - 1
+                if px <= tw and py <= th:
+                    gx, okx = wrap(x0 + px, nx, per[0])
+                    gy, oky = wrap(y0 + py, ny, per[1])
+                    if okx and oky:
+                        gtab[p] = shell_offset(gx, gy)
+            for h in range(32 * ((NH + 31) // 32)):  # halo cells: their shadow rows exist
+                if h < W:
+                    lx, ly, act = h - 1, -1, h - 1 <= tw
+                elif h < 2 * W:
+                    lx, ly, act = h - W - 1, th, h - W - 1 <= tw
+                elif h < 2 * W + TY:
+                    lx, ly, act = -1, h - 2 * W, h - 2 * W < th
+                elif h < NH:
+                    lx, ly, act = tw, h - 2 * W - TY, h - 2 * W - TY < th
+                else:
+                    act = False
+                if act:
+                    _, okx = wrap(x0 + lx, nx, per[0])
+                    _, oky = wrap(y0 + ly, ny, per[1])
+                    if okx and oky:
+                        pos = (ly + 1) * W + lx + 1
+                        assert 0 <= pos < NPOS and gtab[pos] >= 0 and gtab[pos] + 18 * NSP < gplane
+            for ly in range(th):
+                for lx in range(tw):
+                    pos, x, y = (ly + 1) * W + lx + 1, x0 + lx, y0 + ly
+                    assert (gtab[pos] >= 0) == (lx in (0, tw - 1) or ly in (0, th - 1))
+                    has_target = False
+                    for i in range(Q):
+                        cx_, cy_, cz_ = (int(v) for v in C[i])
+                        assert 0 <= pos - cx_ - cy_ * W < NPOS
+                        tx, okx = wrap(x + cx_, nx, per[0])
+                        ty, oky = wrap(y + cy_, ny, per[1])
+                        off = -1
+                        if okx and oky:
+                            off = gtab[pos + cx_ + cy_ * W]
+                            assert off == shell_offset(tx, ty)
+                            has_target |= off >= 0
+                        for k in range(nz):
+                            zt = k + cz_
+                            if not (okx and oky) or zt < 0 or zt >= nz:  # wall link: bounce in the own cell
+                                zt, off2, d2 = k, gtab[pos], opp[i]
+                            else:
+                                off2, d2 = off, i
+                            if off2 >= 0:
+                                key = (zt, off2 + d2 * NSP)
+                                assert key not in written
+                                written.add(key)
+                    if tw >= 4 and th >= 4:
+                        band = ly in (0, 1, th - 2, th - 1) or lx in (0, 1, tw - 2, tw - 1)
+                        assert has_target == band
+    assert written == {(z, e) for z in range(nz) for e in expect}
+
+
+def test_shell_shadow_written_once(cuda_lib):
+    from paper_2208_05429_gb300.lbm import lbm_lattice
+    C, _ = lbm_lattice()
+    for shape, per, ty in [((16, 16, 4), (0, 0), 14), ((37, 19, 5), (1, 1), 14), ((37, 19, 5), (1, 1), 6),
+                           ((33, 40, 4), (0, 1), 14), ((20, 1, 3), (1, 1), 14), ((70, 3, 3), (1, 0), 6),
+                           ((64, 30, 3), (0, 0), 4)]:
+        _shadow_emulation(C, *shape, per, ty)
