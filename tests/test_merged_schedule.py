@@ -164,3 +164,60 @@ def test_shell_shadow_written_once(cuda_lib):
                            ((33, 40, 4), (0, 1), 14), ((20, 1, 3), (1, 1), 14), ((70, 3, 3), (1, 0), 6),
                            ((64, 30, 3), (0, 0), 4)]:
         _shadow_emulation(C, *shape, per, ty)
+
+
+def _shell_cell(s, tw, th, TY):
+    if s < 32:
+        return (s, 0) if s < tw else None
+    if s < 64:
+        return (s - 32, th - 1) if th > 1 and s - 32 < tw else None
+    if s < 64 + (TY - 2):
+        return (0, s - 63) if s - 63 < th - 1 else None
+    if s < 64 + 2 * (TY - 2):
+        ly = s - 64 - (TY - 2) + 1
+        return (tw - 1, ly) if tw > 1 and ly < th - 1 else None
+    return None
+
+
+def test_role_maps_cover_each_tile_once():
+    """The even warps (shell cells in shadow-slot order, then the inner cells)
+    and the odd warps (the two outer rows on either side, the two outer
+    columns of the middle rows, then the inner cells; plain rows for tiles
+    under 4 x 4) each take every cell of every tile shape exactly once."""
+    for TY in (14, 4):
+        NS = 64 + 2 * (TY - 2)
+        for tw in range(1, 33):
+            for th in range(1, TY + 1):
+                cells = sorted((x, y) for y in range(th) for x in range(tw))
+                even = []
+                for t in range(32 * TY):
+                    if t < NS:
+                        c = _shell_cell(t, tw, th, TY)
+                        if c:
+                            even.append(c)
+                    else:
+                        v, w = t - NS, tw - 2
+                        if w > 0 and th > 2 and v < w * (th - 2):
+                            even.append((1 + v % w, 1 + v // w))
+                assert sorted(even) == cells, ("even", TY, tw, th)
+                odd = []
+                for t in range(32 * TY):
+                    if tw < 4 or th < 4:
+                        lx, ly = t & 31, t >> 5
+                        if lx < tw and ly < th:
+                            odd.append((lx, ly))
+                        continue
+                    nrow, nband = 4 * tw, 4 * tw + 4 * (th - 4)
+                    if t >= tw * th:
+                        continue
+                    if t < nrow:
+                        r = t // tw
+                        odd.append((t - r * tw, r if r < 2 else th - 4 + r))
+                    elif t < nband:
+                        u = t - nrow
+                        j = u & 3
+                        odd.append((j if j < 2 else tw - 4 + j, 2 + (u >> 2)))
+                    else:
+                        v, w = t - nband, tw - 4
+                        odd.append((2 + v % w, 2 + v // w))
+                assert sorted(odd) == cells, ("odd", TY, tw, th)
