@@ -137,12 +137,16 @@ int lbm_validate(const lbm_config *cfg);
 /* Device bytes a handle of this configuration uses (populations, second
  * lattice for TWO_LATTICE, tile-shell snapshot for MERGED, work schedule
  * for WAVEFRONT, reduction scratch), each region aligned to 256 bytes.
- * *bytes is a host output. */
+ * *bytes is a host output.  For MERGED the figure depends on the current
+ * device (its SM count sets the z chunks) and on LBM_MERGED_ZCHUNKS, both
+ * read at each call: query with the device and environment the handle will
+ * be created with. */
 int lbm_required_bytes(const lbm_config *cfg, size_t *bytes);
 
-/* Create a handle that allocates its own device memory (cudaMalloc on the
- * current device) and launches on `stream` (a cudaStream_t; NULL = legacy
- * default stream).  Populations start at zero: call lbm_init_equilibrium()
+/* Create a handle that allocates its own device memory (stream-ordered,
+ * cudaMallocAsync on `stream`, current device; released with cudaFreeAsync
+ * on the same stream by lbm_destroy) and launches on `stream` (a
+ * cudaStream_t; NULL = legacy default stream).  Populations start at zero: call lbm_init_equilibrium()
  * or lbm_init_populations() before stepping.  *out receives the handle. */
 int lbm_create(const lbm_config *cfg, void *stream, lbm_handle **out);
 

@@ -151,32 +151,25 @@ TileInfo tile_info(const lbm_config &c)
 // The shadow-shell sweep serves MERGED with automatic tiles (and at least
 // two planes when z is periodic); an explicit tile height selects the
 // snapshot sweep (merged.cuh).
-ShellInfo shell_info(const lbm_config &c);
-
-bool uses_m3(const lbm_config &c)
+// si: the tiles of c (shell_info), computed once per query or creation.
+bool uses_m3(const lbm_config &c, const ShellInfo &si)
 {
     if (c.variant != LBM_VARIANT_MERGED || c.tile_y != 0) return false;
     if (c.face_bc[4] == LBM_BC_PERIODIC && c.nz < 2) return false;
     // the sweep indexes one shadow copy with 32-bit offsets
-    return (double)shell_info(c).gplane * (double)c.nz < 2147483647.0;
+    return (double)si.gplane * (double)c.nz < 2147483647.0;
 }
 
 // Streaming multiprocessors of the current device (152 when it cannot be
 // queried, e.g. on a host without a GPU sizing a buffer).
 int sm_count()
 {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0, v = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) {
-            n = v;
-        } else {
-            cudaGetLastError();
-            n = 152;
-        }
-    }
-    return n;
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+        return v;
+    cudaGetLastError();
+    return 152;
 }
 
 ShellInfo shell_info(const lbm_config &c)
@@ -219,16 +212,15 @@ ShellInfo shell_info(const lbm_config &c)
 }
 
 // Elements of the chunk-boundary copy: 19 x 2 (nzc - 1) planes.
-int64_t zcopy_elems(const lbm_config &c)
+int64_t zcopy_elems(const lbm_config &c, const ShellInfo &si)
 {
-    if (!uses_m3(c)) return 0;
-    const ShellInfo si = shell_info(c);
+    if (!uses_m3(c, si)) return 0;
     return si.nzc > 1 ? (int64_t)Q * 2 * (si.nzc - 1) * c.ny * pitch_of(c) : 0;
 }
 
-int64_t ghost_elems(const lbm_config &c)
+int64_t ghost_elems(const lbm_config &c, const ShellInfo &si)
 {
-    if (c.variant != LBM_VARIANT_MERGED || uses_m3(c)) return 0;
+    if (c.variant != LBM_VARIANT_MERGED || uses_m3(c, si)) return 0;
     const TileInfo ti = tile_info(c);
     return (int64_t)Q * (ti.gy_slot + ti.gx_slot + ti.gz_slot);
 }
@@ -275,7 +267,7 @@ int wf_entries(const lbm_config &c, int ahead, int *out)
     return n;
 }
 
-Layout layout_of(const lbm_config &c)
+Layout layout_of(const lbm_config &c, const ShellInfo &si)
 {
     Layout L;
     const size_t es = elem_size_of(c.storage);
@@ -283,15 +275,14 @@ Layout layout_of(const lbm_config &c)
     size_t off = 0;
     L.f = off; off += pop;
     L.f2 = off; if (c.variant == LBM_VARIANT_TWO_LATTICE) off += pop;
-    L.G = off; off += align_up((size_t)ghost_elems(c) * real_size_of(c.storage));
+    L.G = off; off += align_up((size_t)ghost_elems(c, si) * real_size_of(c.storage));
     L.G3 = off;
-    if (uses_m3(c)) off += 2 * align_up((size_t)(shell_info(c).gplane * c.nz) * es);
+    if (uses_m3(c, si)) off += 2 * align_up((size_t)(si.gplane * c.nz) * es);
     L.Z3 = off;
-    if (uses_m3(c) && c.face_bc[4] == LBM_BC_PERIODIC) {
-        const ShellInfo si = shell_info(c);
+    if (uses_m3(c, si) && c.face_bc[4] == LBM_BC_PERIODIC) {
         off += align_up((size_t)si.ntx * si.nty * ops_for(c.storage)->m3_zsave * real_size_of(c.storage));
     }
-    L.ZC = off; off += align_up((size_t)zcopy_elems(c) * es);
+    L.ZC = off; off += align_up((size_t)zcopy_elems(c, si) * es);
     L.wf = off; off += align_up((size_t)wf_ints(c) * sizeof(int));
     L.partial = off; off += align_up(sizeof(double) * 5 * RED_BLOCKS_MAX);
     L.red_out = off; off += align_up(sizeof(double) * 5);
@@ -462,7 +453,7 @@ int lbm_required_bytes(const lbm_config *cfg, size_t *bytes)
     const int v = lbm_validate(cfg);
     if (v != LBM_OK) return v;
     if (!bytes) return LBM_EINVAL;
-    *bytes = layout_of(*cfg).total;
+    *bytes = layout_of(*cfg, shell_info(*cfg)).total;
     return LBM_OK;
 }
 
@@ -510,7 +501,10 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
     *out = nullptr;
     const int v = lbm_validate(cfg);
     if (v != LBM_OK) return v;
-    const Layout L = layout_of(*cfg);
+    // the merged sweep's tiles and z chunks (current device, environment):
+    // read once, so that the layout and the handle agree
+    const ShellInfo si = shell_info(*cfg);
+    const Layout L = layout_of(*cfg, si);
     lbm_handle *h = new (std::nothrow) lbm_handle;
     if (!h) return LBM_ENOMEM;
     memset((void *)h, 0, sizeof(*h));
@@ -532,7 +526,12 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
         return LBM_ENOMEM;
     }
     if (own) {
-        if (cudaMalloc(&buf, L.total) != cudaSuccess) { delete h->ev_pool; delete h->rec_kind; delete h; return LBM_ENOMEM; }
+        // stream-ordered allocation on the creation stream
+        if (cudaMallocAsync(&buf, L.total, (cudaStream_t)stream) != cudaSuccess) {
+            cudaGetLastError();
+            delete h->ev_pool; delete h->rec_kind; delete h;
+            return LBM_ENOMEM;
+        }
         bytes = L.total;
     } else {
         if (!buf || ((uintptr_t)buf % ALIGN) != 0) { delete h->ev_pool; delete h->rec_kind; delete h; return LBM_EINVAL; }
@@ -545,9 +544,9 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
     h->f = b + L.f;
     h->f2 = cfg->variant == LBM_VARIANT_TWO_LATTICE ? b + L.f2 : nullptr;
     h->G = cfg->variant == LBM_VARIANT_MERGED ? b + L.G : nullptr;
-    h->m3 = uses_m3(*cfg);
+    h->m3 = uses_m3(*cfg, si);
     if (h->m3) {
-        h->si = shell_info(*cfg);
+        h->si = si;
         const size_t gbytes = align_up((size_t)(h->si.gplane * cfg->nz) * elem_size_of(cfg->storage));
         h->G3[0] = b + L.G3;
         h->G3[1] = b + L.G3 + gbytes;
@@ -571,7 +570,7 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
                                 : make_tmap(*cfg, h->ti.TX, h->ti.TY, Q, h->f, &h->tmap));
     if (!tmap_ok ||
         cudaMemsetAsync(buf, 0, L.total, h->stream) != cudaSuccess) {
-        if (own) cudaFree(buf);
+        if (own) cudaFreeAsync(buf, h->stream);
         delete h->ev_pool;
         delete h->rec_kind;
         delete h;
@@ -586,7 +585,7 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
         }
         const int rc = wf_setup(h, ahead);
         if (rc != LBM_OK) {
-            if (own) cudaFree(buf);
+            if (own) cudaFreeAsync(buf, h->stream);
             delete h->ev_pool;
             delete h->rec_kind;
             delete h;
@@ -615,7 +614,10 @@ void lbm_destroy(lbm_handle *h)
         cudaStreamSynchronize(h->stream);
         if (h->gstream) cudaStreamSynchronize(h->gstream);
         free_graph_stream(h);
-        if (h->owns && h->base) cudaFree(h->base);
+        if (h->owns && h->base) {
+            cudaFreeAsync(h->base, h->stream);
+            cudaStreamSynchronize(h->stream);
+        }
         if (h->ev_pool)
             for (cudaEvent_t e : *h->ev_pool) cudaEventDestroy(e);
     }

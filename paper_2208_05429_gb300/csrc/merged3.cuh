@@ -241,6 +241,7 @@ struct M3Cta {
     R *ringm, *ring0, *ringp, *srest, *szp, *szm;
     int *gtab;
     uint64_t *bar;
+    int *issued;  // shared count of the stages whose copies have been started
     int role, x0, y0, tw, th, lx, ly, x, y, pos, tc, hidx, nx, ny, nz, goff, cxy, inoff, sub;
     // z chunk jc of nzc: odd steps of planes [zc0, zc1), loaded planes from qb
     int jc, nzc, zc0, zc1, qb;
@@ -439,6 +440,7 @@ struct M3Cta {
             });
         }
         cp_async_mbar_arrive(b);
+        if (hidx == 0) ++*issued;  // stages issued so far (read when bailing out)
     }
 
     __device__ __forceinline__ void wait_stage(int q)
@@ -617,12 +619,14 @@ __global__ void __launch_bounds__(M3<TY>::THREADS, 1)
     C c(g, fd, fo, go, Gc, Gn, si, &tmap, zsave, smem);
     c.tmapz = &tmapz;
     int *abort_flag = reinterpret_cast<int *>(smem + SM::flag_off);
+    c.issued = abort_flag + 1;
     const int nz = g.nz;
     if (threadIdx.x == 0) {
         mbar_init(&c.bar[0], 1 + M3<TY>::NHT);
         mbar_init(&c.bar[1], 1 + M3<TY>::NHT);
         mbar_fence_init();
         *abort_flag = 0;
+        *c.issued = 0;
     }
     c.fill_gtab();
     __syncthreads();
@@ -674,12 +678,17 @@ __global__ void __launch_bounds__(M3<TY>::THREADS, 1)
 
 bail:
     // a stage never completed: record it, drain the copies still in flight
-    // (bounded) and leave without touching the lattice again
+    // (bounded) and leave without touching the lattice again.  Only the last
+    // two issued stages can still be in flight; stage u completes phase
+    // (u >> 1) & 1 of the mbarrier of slot u & 1, and no later stage has been
+    // issued into either slot.  Every thread drains its own cp.async copies,
+    // which were never committed to a group (they arrive on the mbarrier).
     if (threadIdx.x == 0) {
         atomicOr(status, 2);
-        for (int s = 0; s < 2; ++s) mbar_wait_bounded(&c.bar[s], 0);
+        const int n = *c.issued;
+        for (int u = n - 2 > 0 ? n - 2 : 0; u < n; ++u) mbar_wait_bounded(&c.bar[u & 1], (unsigned)((u >> 1) & 1));
     }
-    cp_async_wait_all();
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 }  // namespace lbm

@@ -29,6 +29,12 @@ def test_lattice_table(cuda_lib):
     assert np.allclose(np.einsum("q,qa,qb->ab", w, c, c), np.eye(3) / 3, atol=1e-16)
 
 
+def test_lattice_table_is_the_one_the_schedule_tests_restate(cuda_lib):
+    from test_merged_schedule import GPU_C
+    c, _ = lbm.lbm_lattice()
+    assert [tuple(int(v) for v in row) for row in c] == GPU_C
+
+
 def test_default_config_valid(cuda_lib):
     cfg = lbm.lbm_config_default()
     assert (cfg.nx, cfg.ny, cfg.nz) == (32, 32, 32)

@@ -160,3 +160,18 @@ def test_channel_gradient_vs_finite_differences(gpu):
           f"FP32 {worst['f32']:.2e}")
     assert worst["f64"] <= 1e-5
     assert worst["f32"] <= 1e-4
+    # Per component, relative 1e-4, for every sampled component above its
+    # noise floor.  FP64: the central differences carry an absolute noise of
+    # about 1.5e-12 (FD minus adjoint on the small y/z components, where the
+    # FP64 and FP32 adjoints agree with each other to 1e-5), so components
+    # with |g| >= 2e-8 are checked one by one.  FP32: the adjoint's own
+    # rounding is about 1e-5 of the largest gradient, so components with
+    # |g| >= 0.1 max|g| are.  The rest stay under the max-norm checks above.
+    floors = {"f64": 2e-8, "f32": 0.1 * float(np.max(np.abs(fds)))}
+    for s, floor in floors.items():
+        a = np.array(adj[s])
+        big = np.abs(fds) >= floor
+        assert big.sum() >= 4, (s, big.sum())
+        rel = np.abs(a[big] - fds[big]) / np.abs(fds[big])
+        print(f"{s}: {int(big.sum())} components above {floor:.1e}, worst relative error {rel.max():.2e}")
+        assert rel.max() <= 1e-4, (s, rel.max())

@@ -4,9 +4,10 @@ periodic Taylor-Green box of the precision study (U0 = 0.04, tau = 0.52), at
 64^3 for 400 steps (the 512^3 x 2000-step case is run by bench.py's precision
 mode); FP32 arithmetic in every format.
 
-Bounds (relative max-norm of u vs FP64): F32 3e-5, F32S 3e-5, F16S 1e-2,
-BF16S 1e-1.  FP16/BF16 parity is not pinned to the oracle beyond this
-measured bound."""
+Bounds (relative max-norm of u vs FP64), about twice the measured errors
+(F32 1.27e-5, F32S 1.24e-5, F16S 1.07e-3, BF16S 5.6e-3): F32 2.5e-5, F32S
+2.5e-5, F16S 2.2e-3, BF16S 1.2e-2.  FP16/BF16 parity is not pinned to the
+oracle beyond this measured bound."""
 import numpy as np
 import pytest
 
@@ -15,7 +16,7 @@ from paper_2208_05429_gb300.lbm import Lattice
 
 pytestmark = pytest.mark.gpu
 
-BOUNDS = {"f32": 3e-5, "f32s": 3e-5, "f16s": 1e-2, "bf16s": 1e-1}
+BOUNDS = {"f32": 2.5e-5, "f32s": 2.5e-5, "f16s": 2.2e-3, "bf16s": 1.2e-2}
 
 
 def _tg(storage, n=64, steps=400, variant="merged"):

@@ -222,25 +222,59 @@ def test_random_shapes_merged_and_wavefront_equal_aa(gpu, seed):
         assert torch.equal(_raw(lat), want), (variant, cfg.nx, cfg.ny, cfg.nz, cfg.bc, storage, nsteps)
 
 
+def _zchunk_config(shape):
+    import oracle
+    from oracle import BC_LID, BC_PERIODIC, BC_WALL, FORCE_UNIFORM
+    nx, ny, nz = shape
+    return oracle.Config(nx=nx, ny=ny, nz=nz, tau=0.7, bc=(BC_WALL, BC_WALL, BC_PERIODIC, BC_PERIODIC, BC_WALL, BC_LID),
+                         u_lid=(0.03, -0.01, 0.0), force_mode=FORCE_UNIFORM, force_uniform=(2e-6, 0.0, -1e-6))
+
+
 @pytest.mark.parametrize("storage", ["f32", "f16s"])
 @pytest.mark.parametrize("shape", [(40, 20, 8), (33, 17, 13), (64, 30, 29)])
 def test_merged_z_chunks_equal_aa(gpu, shape, storage):
     """With fewer tiles than SMs the shadow-shell sweep splits z into chunks
     (one CTA per tile and chunk; the planes next to a chunk boundary come
-    from a copy taken before the sweep).  On 152 SMs these shapes give
-    two, three and seven chunks of 4 or 5 planes, with a wall and a lid on
-    the z faces."""
+    from a copy taken before the sweep).  The automatic chunk count, with a
+    wall and a lid on the z faces."""
     import torch
-    import oracle
-    from oracle import BC_LID, BC_PERIODIC, BC_WALL, FORCE_UNIFORM
-    nx, ny, nz = shape
-    cfg = oracle.Config(nx=nx, ny=ny, nz=nz, tau=0.7, bc=(BC_WALL, BC_WALL, BC_PERIODIC, BC_PERIODIC, BC_WALL, BC_LID),
-                        u_lid=(0.03, -0.01, 0.0), force_mode=FORCE_UNIFORM, force_uniform=(2e-6, 0.0, -1e-6))
-    f0 = start_state(cfg, seed=nz)
+    cfg = _zchunk_config(shape)
+    f0 = start_state(cfg, seed=cfg.nz)
     ref = make_gpu(cfg, storage, "aa")
     load_state(ref, f0)
     ref.step(6)
     lat = make_gpu(cfg, storage, "merged")
     load_state(lat, f0)
     lat.step(6)
+    assert torch.equal(_raw(lat), _raw(ref))
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16s"])
+@pytest.mark.parametrize("shape,nzc", [((64, 30, 29), 2), ((64, 30, 29), 3), ((64, 30, 29), 7),
+                                       ((37, 19, 37), 2), ((37, 19, 37), 5), ((37, 19, 37), 9)])
+def test_merged_explicit_z_chunks_equal_aa(gpu, monkeypatch, shape, nzc, storage):
+    """Explicit chunk counts (LBM_MERGED_ZCHUNKS, read when the handle is
+    created), uneven splits and the largest count nz // 4 included.  That the
+    split is active is checked through the handle's size: it grows by the
+    copy of the 2 (nzc - 1) planes next to the chunk boundaries."""
+    import torch
+    from paper_2208_05429_gb300 import lbm
+    cfg = _zchunk_config(shape)
+    nx, ny, nz = shape
+    es = {"f32": 4, "bf16s": 2}[storage]
+    monkeypatch.setenv("LBM_MERGED_ZCHUNKS", "1")
+    one = lbm.lbm_required_bytes(lbm.make_config(shape, 0.7, cfg.bc, storage=storage, variant="merged"))
+    monkeypatch.setenv("LBM_MERGED_ZCHUNKS", str(nzc))
+    many = lbm.lbm_required_bytes(lbm.make_config(shape, 0.7, cfg.bc, storage=storage, variant="merged"))
+    pitch = (nx + 15) // 16 * 16
+    copy = 19 * 2 * (nzc - 1) * ny * pitch * es
+    assert many - one == (copy + 255) // 256 * 256
+    f0 = start_state(cfg, seed=nzc)
+    lat = make_gpu(cfg, storage, "merged")
+    load_state(lat, f0)
+    lat.step(6)
+    monkeypatch.delenv("LBM_MERGED_ZCHUNKS")
+    ref = make_gpu(cfg, storage, "aa")
+    load_state(ref, f0)
+    ref.step(6)
     assert torch.equal(_raw(lat), _raw(ref))

@@ -157,9 +157,16 @@ def _shadow_emulation(C, nx, ny, nz, per, TY):
     assert written == {(z, e) for z in range(nz) for e in expect}
 
 
-def test_shell_shadow_written_once(cuda_lib):
-    from paper_2208_05429_gb300.lbm import lbm_lattice
-    C, _ = lbm_lattice()
+# The CUDA library's direction numbering (grouped by c_z: rest, then the nine
+# vectors whose first non-zero component is -1, then their opposites); the
+# ABI test checks that lbm_lattice() reports exactly this table.
+GPU_C = [(0, 0, 0), (0, 0, -1), (-1, 0, -1), (0, -1, -1), (-1, 0, 1), (0, -1, 1), (-1, 0, 0), (0, -1, 0),
+         (-1, -1, 0), (-1, 1, 0)]
+GPU_C += [tuple(-v for v in c) for c in GPU_C[1:]]
+
+
+def test_shell_shadow_written_once():
+    C = GPU_C
     for shape, per, ty in [((16, 16, 4), (0, 0), 14), ((37, 19, 5), (1, 1), 14), ((37, 19, 5), (1, 1), 6),
                            ((33, 40, 4), (0, 1), 14), ((20, 1, 3), (1, 1), 14), ((70, 3, 3), (1, 0), 6),
                            ((64, 30, 3), (0, 0), 4)]:
