@@ -217,6 +217,41 @@ int lbm_init_populations(lbm_handle *h, const void *f_in, int32_t dtype);
  * the lattice is then invalid and the flag is cleared. */
 int lbm_reduce(lbm_handle *h, double *out);
 
+/* The sums of lbm_reduce() for a population field the caller holds, computed
+ * without allocating any device memory and without a handle.  The paper has
+ * no counterpart: this is for callers that cannot call cudaMalloc -- a
+ * process whose free device memory is all held by a caching allocator (such
+ * as PyTorch's, where cudaMalloc fails although the pool has room), a
+ * serving or stepping loop that must not take the device-wide
+ * synchronisation of cudaMalloc / cudaFree, or code running inside an
+ * allocator callback.
+ *   cfg    lattice sizes and body force (force_mode, force_uniform); the
+ *          whole config must pass lbm_validate(), so lattices beyond
+ *          2^31 - 1 cells are rejected with LBM_EINVAL; storage, variant
+ *          and tiles are ignored
+ *   f      device, canonical natural-parity populations f[19][z][y][x] of
+ *          element type `dtype` (LBM_DTYPE_F32 or _F64), directions as
+ *          lbm_lattice() -- what lbm_populations() writes
+ *   F      device FP32 [3][z][y][x] when force_mode == LBM_FORCE_FIELD
+ *          (else ignored, may be NULL)
+ *   out    host double[5], as lbm_reduce(): mass, momentum xyz, kinetic energy
+ *   stream cudaStream_t to run on (NULL = legacy default stream); the call
+ *          synchronises it
+ * Scratch: one file-scope device array of 41,088 bytes (1024 x 5 FP64
+ * partial sums, the five results and a flag), present on every GPU that
+ * loads the library until the process exits; enough for every lattice
+ * lbm_validate() accepts.  The first call on a device looks up that array's
+ * device address (once per device, with the device current): make that
+ * first call before any stream capture on the device.  All calls in the
+ * process share the array and it keeps the last call's contents (the flag
+ * is cleared at the start of each call), so calls that overlap on the GPU
+ * -- on two streams, or from two host threads -- race and must be
+ * serialised by the caller.  Returns LBM_ENONFINITE (out still written) as
+ * lbm_reduce() does, LBM_EINVAL for bad arguments, LBM_ECUDA on a CUDA
+ * error, LBM_EUNSUPPORTED for a device ordinal of 64 or more. */
+int lbm_reduce_populations(const lbm_config *cfg, const void *f, int32_t dtype, const float *F, double *out,
+                           void *stream);
+
 /* ---------------- per-kernel timing ----------------
  * Kernel classes launched by lbm_step(). */
 enum { LBM_KERNEL_TWO_LATTICE = 0, LBM_KERNEL_AA_EVEN = 1, LBM_KERNEL_AA_ODD = 2,

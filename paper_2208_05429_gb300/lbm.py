@@ -84,6 +84,8 @@ _SIGNATURES = {
     "lbm_populations": (ctypes.c_int, [_H, _VP, ctypes.c_int32]),
     "lbm_init_populations": (ctypes.c_int, [_H, _VP, ctypes.c_int32]),
     "lbm_reduce": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double)]),
+    "lbm_reduce_populations": (ctypes.c_int, [_CFGP, _VP, ctypes.c_int32, _VP, ctypes.POINTER(ctypes.c_double),
+                                              _VP]),
     "lbm_profile": (ctypes.c_int, [_H, ctypes.c_int32]),
     "lbm_selftest_wait_timeout": (ctypes.c_int, [_H]),
     "lbm_profile_read": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
@@ -227,6 +229,17 @@ def lbm_reduce(h, raise_nonfinite: bool = True) -> np.ndarray:
     rc = library().lbm_reduce(h, out)
     if rc != LBM_OK and (raise_nonfinite or rc != LBM_ENONFINITE):
         raise LbmError(rc, "lbm_reduce")
+    return np.array(out[:], dtype=np.float64)
+
+
+def lbm_reduce_populations(cfg: lbm_config, f, F=None, stream: int = 0, raise_nonfinite: bool = True):
+    """Sums of lbm_reduce() for canonical populations f (a CUDA tensor),
+    without any device allocation (scratch in a fixed device array)."""
+    out = (ctypes.c_double * 5)()
+    rc = library().lbm_reduce_populations(ctypes.byref(cfg), _ptr(f), _dtype_code(f.dtype), _ptr(F), out,
+                                          _VP(stream))
+    if rc != LBM_OK and (raise_nonfinite or rc != LBM_ENONFINITE):
+        raise LbmError(rc, "lbm_reduce_populations")
     return np.array(out[:], dtype=np.float64)
 
 
