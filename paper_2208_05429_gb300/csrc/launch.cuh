@@ -5,6 +5,7 @@
 #include "kernels.cuh"
 #include "merged.cuh"
 #include "merged3.cuh"
+#include "nsweep.cuh"
 #include "wavefront.cuh"
 
 #include <string.h>
@@ -259,6 +260,72 @@ struct Launch {
                                                                       si.nzc);
         return cudaGetLastError();
     }
+    // neighbour-synchronised merged sweep: 4- and 2-byte storage, 32 x 14 tiles
+    static constexpr int NS_TY = 14;
+    static constexpr bool HAS_NS = sizeof(T) < 8;
+    template <bool F>
+    static cudaError_t nsweep_f(const HostGeom &h, int64_t pitch, void *f, const ShellInfo &si, int *prog,
+                                const void *tmap, int *status, cudaStream_t st)
+    {
+        if constexpr (!HAS_NS) {
+            return cudaErrorNotSupported;
+        } else {
+            using NSM = NSSmem<NS_TY, T, R>;
+            static_assert(NSM::bytes <= 232448, "neighbour-synchronised sweep shared memory");
+            constexpr size_t smem = NSM::bytes;
+            static bool attr_set = false;  // once per process: not inside a stream capture
+            if (!attr_set) {
+                const cudaError_t e = cudaFuncSetAttribute(k_nsweep<S, F, NS_TY>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+                attr_set = true;
+            }
+            CUtensorMap map;
+            memcpy(&map, tmap, sizeof(map));
+            const Geom<R> g = make_geom<R>(h, pitch);
+            const Dirs<T> fd = make_dirs((T *)f, slot_of(h, pitch));
+            Dirs<T> fo = fd;
+            for (int i = 0; i < Q; ++i) fo.p[i] = fd.p[i] + g.noff[i];
+            cudaLaunchConfig_t cfg;
+            memset(&cfg, 0, sizeof(cfg));
+            cfg.gridDim = dim3(si.ntx, si.nty, 1);
+            cfg.blockDim = dim3(NSL<NS_TY, T>::THREADS, 1, 1);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            return cudaLaunchKernelEx(&cfg, k_nsweep<S, F, NS_TY>, map, g, fd, fo, si, prog, status);
+        }
+    }
+    static cudaError_t nsweep(const HostGeom &h, int64_t pitch, bool force, void *f, const ShellInfo &si, int *prog,
+                              const void *tmap, int *status, cudaStream_t st)
+    {
+        return force ? nsweep_f<true>(h, pitch, f, si, prog, tmap, status, st)
+                     : nsweep_f<false>(h, pitch, f, si, prog, tmap, status, st);
+    }
+    // CTAs of the sweep one SM holds (0 where it does not exist or fit)
+    static int nsweep_ctas_per_sm(bool force)
+    {
+        if constexpr (!HAS_NS) {
+            return 0;
+        } else {
+            constexpr size_t smem = NSSmem<NS_TY, T, R>::bytes;
+            auto kern = force ? k_nsweep<S, true, NS_TY> : k_nsweep<S, false, NS_TY>;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+                cudaGetLastError();
+                return 0;
+            }
+            int n = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NSL<NS_TY, T>::THREADS, smem) != cudaSuccess) {
+                cudaGetLastError();
+                return 0;
+            }
+            return n;
+        }
+    }
     static cudaError_t wavefront(const HostGeom &h, int64_t pitch, bool force, void *f, const void *sched, int grid,
                                  cudaStream_t st)
     {
@@ -328,6 +395,11 @@ StorageOps make_ops()
     o.max_tile_y = L::merged_smem(16) ? 16 : (L::merged_smem(8) ? 8 : 4);
     o.merged_smem = &L::merged_smem;
     o.wavefront = &L::wavefront;
+    o.nsweep = L::HAS_NS ? &L::nsweep : nullptr;
+    o.nsweep_ctas_per_sm = &L::nsweep_ctas_per_sm;
+    o.ns_ty = L::NS_TY;
+    o.ns_box_w = 32 + 2 * (16 / (int)sizeof(typename S::T));
+    o.ns_margin = 16 / (int)sizeof(typename S::T);
     o.wavefront_blocks_per_sm = &L::wavefront_blocks_per_sm;
     o.init_eq = &L::init_eq;
     o.two_lattice = &L::two_lattice;

@@ -57,6 +57,9 @@ struct lbm_handle {
     } gfrom, gto;
     CUtensorMap tmap;  // TMA descriptor of f (MERGED)
     CUtensorMap tmapz; // the same over ZC (shadow-shell sweep with si.nzc > 1)
+    bool ns;           // MERGED runs the neighbour-synchronised sweep
+    int *prog;         // its progress words, one per tile
+    CUtensorMap tmapns;  // its copy box: tile + halo, all 19 directions
     int *status;       // device status word: bits 2 / 4 = a bounded wait gave up
     int *wf_words;     // WAVEFRONT schedule (device): entries, ticket, done flags
     int wf_nentries, wf_rb, wf_nrb, wf_grid, wf_ahead;
@@ -151,10 +154,37 @@ TileInfo tile_info(const lbm_config &c)
 // The shadow-shell sweep serves MERGED with automatic tiles (and at least
 // two planes when z is periodic); an explicit tile height selects the
 // snapshot sweep (merged.cuh).
+int sm_count();
+
+// The neighbour-synchronised sweep serves MERGED with automatic tiles when
+// every face is a wall or lid, the format has the sweep, all tiles can be
+// resident at once and they are at least half as many as the SMs (fewer
+// tiles leave SMs idle; the shadow-shell sweep splits z for them).  The
+// environment variable LBM_MERGED_SWEEP=shadow selects the shadow-shell
+// sweep instead, LBM_MERGED_SWEEP=neighbour this one whenever it can run
+// (any tile count up to the resident limit).
+bool uses_ns(const lbm_config &c, const ShellInfo &si)
+{
+    if (c.variant != LBM_VARIANT_MERGED || c.tile_y != 0) return false;
+    bool any_count = false;
+    if (const char *e = getenv("LBM_MERGED_SWEEP")) {
+        if (strcmp(e, "shadow") == 0) return false;
+        any_count = strcmp(e, "neighbour") == 0;
+    }
+    for (int k = 0; k < 6; ++k)
+        if (c.face_bc[k] == LBM_BC_PERIODIC) return false;
+    const StorageOps *o = ops_for(c.storage);
+    if (!o->nsweep || o->ns_ty != o->m3_ty) return false;
+    const int64_t tiles = (int64_t)si.ntx * si.nty, sms = sm_count();
+    const int per = o->nsweep_ctas_per_sm(c.force_mode != LBM_FORCE_NONE);
+    return per > 0 && tiles <= (int64_t)per * sms && (any_count || 2 * tiles >= sms);
+}
+
 // si: the tiles of c (shell_info), computed once per query or creation.
 bool uses_m3(const lbm_config &c, const ShellInfo &si)
 {
     if (c.variant != LBM_VARIANT_MERGED || c.tile_y != 0) return false;
+    if (uses_ns(c, si)) return false;
     if (c.face_bc[4] == LBM_BC_PERIODIC && c.nz < 2) return false;
     // the sweep indexes one shadow copy with 32-bit offsets
     return (double)si.gplane * (double)c.nz < 2147483647.0;
@@ -226,7 +256,7 @@ int64_t ghost_elems(const lbm_config &c, const ShellInfo &si)
 }
 
 struct Layout {
-    size_t f, f2, G, G3, Z3, ZC, wf, partial, red_out, flag, status, total;
+    size_t f, f2, G, G3, Z3, ZC, prog, wf, partial, red_out, flag, status, total;
 };
 
 // WAVEFRONT schedule words: entries (2 nz + 4), ticket, done[nz * ny] (at
@@ -283,6 +313,8 @@ Layout layout_of(const lbm_config &c, const ShellInfo &si)
         off += align_up((size_t)si.ntx * si.nty * ops_for(c.storage)->m3_zsave * real_size_of(c.storage));
     }
     L.ZC = off; off += align_up((size_t)zcopy_elems(c, si) * es);
+    L.prog = off;
+    if (uses_ns(c, si)) off += align_up(sizeof(int) * NS_PROG_INTS * (size_t)si.ntx * si.nty);
     L.wf = off; off += align_up((size_t)wf_ints(c) * sizeof(int));
     L.partial = off; off += align_up(sizeof(double) * 5 * RED_BLOCKS_MAX);
     L.red_out = off; off += align_up(sizeof(double) * 5);
@@ -545,6 +577,11 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
     h->f2 = cfg->variant == LBM_VARIANT_TWO_LATTICE ? b + L.f2 : nullptr;
     h->G = cfg->variant == LBM_VARIANT_MERGED ? b + L.G : nullptr;
     h->m3 = uses_m3(*cfg, si);
+    h->ns = uses_ns(*cfg, si);
+    if (h->ns) {
+        h->si = si;
+        h->prog = (int *)(b + L.prog);
+    }
     if (h->m3) {
         h->si = si;
         const size_t gbytes = align_up((size_t)(h->si.gplane * cfg->nz) * elem_size_of(cfg->storage));
@@ -564,7 +601,8 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
     int64_t nb = (n + 255) / 256;
     h->red_blocks = (int)(nb < RED_BLOCKS_MAX ? nb : RED_BLOCKS_MAX);
     const bool tmap_ok = cfg->variant != LBM_VARIANT_MERGED ||
-                         (h->m3 ? make_tmap(*cfg, 32, h->ops->m3_ty, 1, h->f, &h->tmap) &&
+                         (h->ns ? make_tmap(*cfg, h->ops->ns_box_w, h->ops->ns_ty + 2, Q, h->f, &h->tmapns) :
+                          h->m3 ? make_tmap(*cfg, 32, h->ops->m3_ty, 1, h->f, &h->tmap) &&
                                       (!h->ZC || make_tmap(*cfg, 32, h->ops->m3_ty, 1, h->ZC, &h->tmapz,
                                                            2 * (int64_t)(h->si.nzc - 1)))
                                 : make_tmap(*cfg, h->ti.TX, h->ti.TY, Q, h->f, &h->tmap));
@@ -730,6 +768,12 @@ static int step_units(lbm_handle *h, int64_t n)
                 h->parity = PARITY_NATURAL;
                 h->g3fresh = false;
                 n -= 1; h->t += 1;
+            } else if (n >= 2 && h->ns) {
+                CK(cudaMemsetAsync(h->prog, 0, sizeof(int) * NS_PROG_INTS * (size_t)h->si.ntx * h->si.nty, h->stream));
+                CK(timed(h, LBM_KERNEL_MERGED, [&] {
+                    return o.nsweep(h->hg, h->nxp, h->force, h->f, h->si, h->prog, &h->tmapns, h->status, h->stream);
+                }));
+                n -= 2; h->t += 2;
             } else if (n >= 2 && h->m3) {
                 if (!h->g3fresh) {
                     CK(timed(h, LBM_KERNEL_SNAPSHOT, [&] {

@@ -87,6 +87,15 @@ struct StorageOps {
     // copy of the planes zb-1 and zb of every z-chunk boundary zb into zc
     // ([19][2 (nzc-1)][ny][pitch], stored elements)
     cudaError_t (*zcopy)(const HostGeom &, int64_t pitch, const void *f, void *zc, const ShellInfo &, cudaStream_t);
+    // neighbour-synchronised merged sweep (every face a wall or lid): one
+    // cooperative launch of si.ntx x si.nty CTAs, all resident; prog holds
+    // NS_PROG_INTS * si.ntx * si.nty ints that must be zero at launch; tmap is the
+    // CUtensorMap of f with a box of ns_box_w x (ns_ty + 2) cells and all 19
+    // directions.  nsweep is null where the format has no such sweep (FP64).
+    cudaError_t (*nsweep)(const HostGeom &, int64_t pitch, bool force, void *f, const ShellInfo &, int *prog,
+                          const void *tmap, int *status, cudaStream_t);
+    int (*nsweep_ctas_per_sm)(bool force);
+    int ns_ty, ns_box_w, ns_margin;
     // persistent plane-wavefront sweep (two time steps); sched points to a
     // WaveSchedule (device pointers inside), grid = number of CTAs
     cudaError_t (*wavefront)(const HostGeom &, int64_t pitch, bool force, void *f, const void *sched, int grid,
@@ -110,5 +119,8 @@ const StorageOps &ops_f16s();
 const StorageOps &ops_bf16s();
 
 constexpr int RED_BLOCKS_MAX = 1024;
+// ints per tile of the neighbour-synchronised sweep's progress words (one
+// 128-byte line each)
+constexpr int NS_PROG_INTS = 32;
 
 }  // namespace lbm

@@ -278,3 +278,61 @@ def test_merged_explicit_z_chunks_equal_aa(gpu, monkeypatch, shape, nzc, storage
     load_state(ref, f0)
     ref.step(6)
     assert torch.equal(_raw(lat), _raw(ref))
+
+
+def _walled_config(rng):
+    """A random lattice with walls or lids on every face (the faces the
+    neighbour-synchronised sweep serves), ragged against the 32-wide tiles
+    and the 14-row bands."""
+    import oracle
+    from oracle import BC_LID, BC_WALL, FORCE_NONE, FORCE_UNIFORM
+    nx, ny, nz = (int(v) for v in rng.integers([1, 1, 1], [100, 60, 12]))
+    bc = tuple(BC_LID if rng.random() < 0.3 else BC_WALL for _ in range(6))
+    lid = tuple(float(v) for v in rng.uniform(-0.04, 0.04, 3))
+    fm = FORCE_UNIFORM if rng.random() < 0.5 else FORCE_NONE
+    fu = tuple(float(v) for v in rng.uniform(-2e-5, 2e-5, 3)) if fm == FORCE_UNIFORM else (0.0, 0.0, 0.0)
+    return oracle.Config(nx=nx, ny=ny, nz=nz, tau=float(rng.uniform(0.52, 1.2)), bc=bc, u_lid=lid,
+                         force_mode=fm, force_uniform=fu)
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_neighbour_synchronised_sweep_equals_aa(gpu, monkeypatch, seed):
+    """The neighbour-synchronised merged sweep (forced for every tile count
+    with LBM_MERGED_SWEEP=neighbour) is bit-identical to AA on random walled
+    lattices in the four formats that have it, over mixed step counts."""
+    import torch
+    from paper_2208_05429_gb300.lbm import lbm_required_bytes, make_config
+    rng = np.random.default_rng(7000 + seed)
+    cfg = _walled_config(rng)
+    storage = ["f32", "f32s", "f16s", "bf16s"][seed % 4]
+    f0 = start_state(cfg, seed=seed)
+    monkeypatch.setenv("LBM_MERGED_SWEEP", "neighbour")
+    shape = (cfg.nx, cfg.ny, cfg.nz)
+    ns_bytes = lbm_required_bytes(make_config(shape, cfg.tau, cfg.bc, storage=storage, variant="merged"))
+    lat = make_gpu(cfg, storage, "merged")
+    monkeypatch.setenv("LBM_MERGED_SWEEP", "shadow")
+    shadow_bytes = lbm_required_bytes(make_config(shape, cfg.tau, cfg.bc, storage=storage, variant="merged"))
+    assert ns_bytes < shadow_bytes  # no shell shadow: the other sweep is not the one running
+    monkeypatch.delenv("LBM_MERGED_SWEEP")
+    load_state(lat, f0)
+    for k in (2, 2, 1, 3, 2):
+        lat.step(k)
+    ref = make_gpu(cfg, storage, "aa")
+    load_state(ref, f0)
+    ref.step(10)
+    assert torch.equal(_raw(lat), _raw(ref)), (cfg.nx, cfg.ny, cfg.nz, cfg.bc, storage)
+
+
+def test_neighbour_synchronised_sweep_at_bench_size_equals_aa(gpu):
+    """256^3 cavity, FP32: 152 tiles, one per SM, the sweep MERGED runs by
+    default there; 6 steps equal AA bit for bit."""
+    import torch
+    import oracle
+    cfg = oracle.cavity(256, 0.55)
+    m = make_gpu(cfg, "f32", "merged")
+    m.init_equilibrium()
+    m.step(6)
+    a = make_gpu(cfg, "f32", "aa")
+    a.init_equilibrium()
+    a.step(6)
+    assert torch.equal(_raw(m), _raw(a))
