@@ -193,6 +193,110 @@ __device__ __forceinline__ Mom<R> moments_of(const R (&s)[Q], R Fx, R Fy, R Fz)
 __device__ __forceinline__ float rrcp(float a) { return __frcp_rn(a); }
 __device__ __forceinline__ double rrcp(double a) { return __drcp_rn(a); }
 
+// Packed two-lane FP32 arithmetic (sm_100 and later).  Each lane rounds
+// exactly as the scalar round-to-nearest operation does, so a pair of
+// results is bit-identical to the two scalar ones.
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 p_dup(float a) { return make_float2(a, a); }
+
+// c_i . (A, B, C) on duplicated pairs, in the order cdot() uses.
+template <int I>
+__device__ __forceinline__ float2 cdot_pair(float2 A, float2 B, float2 C)
+{
+    float2 v = make_float2(0.f, 0.f);
+    bool first = true;
+    auto acc = [&](int c, float2 a) {
+        if (c == 0) return;
+        if (first) { v = c > 0 ? a : p_neg(a); first = false; }
+        else v = p_add(v, c > 0 ? a : p_neg(a));
+    };
+    acc(cx(I), A);
+    acc(cy(I), B);
+    acc(cz(I), C);
+    return v;
+}
+
+// The FP32 collision of bgk_collide() on the pairs P_i = {s_i, s_i+9} of
+// opposite directions, two lanes per instruction.
+//  * Moments: D = sum_i P_i gives delta_rho = (s_0 + D.x) + D.y, and
+//    S_a = sum_i c_ia P_i gives j_a = S_a.x - S_a.y (c_i+9 = -c_i).
+//  * Relaxation: per pair the common part sym and the odd part +-anti of
+//    the equilibrium, {a, b} = P + omega ({sym + anti, sym - anti} - P)
+//    (plus the Guo source the same way), with exactly the operations, order
+//    and rounding of the scalar form.
+template <bool FORCE>
+__device__ __forceinline__ void bgk_collide_pairs(float (&s)[Q], float omega, float kf, float Fx, float Fy, float Fz)
+{
+    float2 P[10];
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        P[i] = make_float2(s[i], s[i + 9]);
+    });
+    float2 D = P[1];
+    static_for<8>([&](auto K) { D = p_add(D, P[decltype(K)::value + 2]); });
+    float2 Sx = make_float2(0.f, 0.f), Sy = Sx, Sz = Sx;
+    bool fx = true, fy = true, fz = true;
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        auto acc = [&](float2 &S, bool &first, int c) {
+            if (c == 0) return;
+            if (first) { S = c > 0 ? P[i] : p_neg(P[i]); first = false; }
+            else S = p_add(S, c > 0 ? P[i] : p_neg(P[i]));
+        };
+        acc(Sx, fx, cx(i));
+        acc(Sy, fy, cy(i));
+        acc(Sz, fz, cz(i));
+    });
+    const float drho = radd(radd(s[0], D.x), D.y);
+    float jx = rsub(Sx.x, Sx.y), jy = rsub(Sy.x, Sy.y), jz = rsub(Sz.x, Sz.y);
+    const float rho = radd(1.f, drho);
+    if constexpr (FORCE) {
+        jx = rfma(0.5f, Fx, jx);
+        jy = rfma(0.5f, Fy, jy);
+        jz = rfma(0.5f, Fz, jz);
+    }
+    const float inv = rrcp(rho);
+    const float ux = rmul(jx, inv), uy = rmul(jy, inv), uz = rmul(jz, inv);
+    const float ux2 = rmul(ux, ux), uy2 = rmul(uy, uy), uz2 = rmul(uz, uz);
+    const float m15 = rmul(-1.5f, radd(radd(ux2, uy2), uz2));
+    const float C0 = rfma(rmul(1.f / 3.f, rho), m15, rmul(1.f / 3.f, drho));
+    const float A1 = rmul(1.f / 18.f, rho), A2 = rmul(1.f / 36.f, rho);
+    const float C1 = rfma(A1, m15, rmul(1.f / 18.f, drho)), C2 = rfma(A2, m15, rmul(1.f / 36.f, drho));
+    const float D1 = rmul(4.5f, A1), D2 = rmul(4.5f, A2);
+    const float E1 = rmul(3.f, A1), E2 = rmul(3.f, A2);
+    float uF = 0.f;
+    if constexpr (FORCE) uF = rfma(ux, Fx, rfma(uy, Fy, rmul(uz, Fz)));
+    s[0] = rfma(omega, rsub(C0, s[0]), s[0]);
+    if constexpr (FORCE) s[0] = rfma(kf, -uF, s[0]);
+    const float2 UX = p_dup(ux), UY = p_dup(uy), UZ = p_dup(uz);
+    const float2 OM = p_dup(omega);
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        constexpr bool face = csq(i) == 1;
+        const float2 CU = cdot_pair<i>(UX, UY, UZ);
+        float2 T;
+        if constexpr (face) T = p_dup(cx(i) != 0 ? ux2 : (cy(i) != 0 ? uy2 : uz2));
+        else T = p_mul(CU, CU);
+        const float2 SYM = p_fma(p_dup(face ? D1 : D2), T, p_dup(face ? C1 : C2));
+        const float E = face ? E1 : E2;
+        const float2 ANTI = p_mul(make_float2(E, -E), CU);
+        const float2 V = p_add(SYM, ANTI);
+        float2 R2 = p_fma(OM, p_add(V, p_neg(P[i])), P[i]);
+        if constexpr (FORCE) {
+            constexpr double w = wgt(i);
+            const float cF = cdot<i, float>(Fx, Fy, Fz);
+            const float ssym = rfma(rmul(float(9 * w), CU.x), cF, rmul(float(-3 * w), uF));
+            const float santi = rmul(float(3 * w), cF);
+            R2 = p_fma(p_dup(kf), p_add(p_dup(ssym), make_float2(santi, -santi)), R2);
+        }
+        s[i] = R2.x;
+        s[i + 9] = R2.y;
+    });
+}
+
 // In-place BGK + Guo collision of one cell's shifted populations s_i =
 // f_i - w_i.  omega = 1/tau, kf = 1 - omega/2.
 //
@@ -209,6 +313,10 @@ __device__ __forceinline__ double rrcp(double a) { return __drcp_rn(a); }
 template <class R, bool FORCE>
 __device__ __forceinline__ void bgk_collide(R (&s)[Q], R omega, R kf, R Fx, R Fy, R Fz)
 {
+    if constexpr (std::is_same<R, float>::value) {
+        bgk_collide_pairs<FORCE>(s, omega, kf, Fx, Fy, Fz);
+        return;
+    }
     // moments from pair sums and differences
     R dif[10];
     R drho = s[0];

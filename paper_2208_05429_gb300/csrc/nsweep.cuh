@@ -97,7 +97,7 @@ struct NSCta {
     uint64_t *bar;
     int role, x0, y0, tw, th, lx, ly, x, y, pos, sidx, nx, ny, nz, cxy;
     unsigned wxy, lxy;  // wall links through the x / y faces; those ending on a lid
-    bool active, xybnd;
+    bool active, xybnd, xwall, ywall;
 
     __device__ __forceinline__ NSCta(const Geom<R> &g_, const Dirs<T> &fd_, const Dirs<T> &fo_,
                                      const ShellInfo &si, unsigned char *smem_)
@@ -135,6 +135,8 @@ struct NSCta {
         pos = (ly + 1) * W + (lx + 1);
         sidx = (ly + 1) * L::BW + lx + XM;
         xybnd = x == 0 || x == nx - 1 || y == 0 || y == ny - 1;
+        xwall = active && (x == 0 || x == nx - 1);
+        ywall = active && (y == 0 || y == ny - 1);
         cxy = y * (int)g.nxp + x;
         wxy = lxy = 0u;
         if (active) {
@@ -194,22 +196,45 @@ struct NSCta {
         });
     }
 
+    // Path of a tile warp's odd step, the same for all its lanes (no lane
+    // may diverge from the others): no wall link in the warp, wall links only
+    // through the x faces (one lane at a lattice edge, handled by selecting
+    // addresses), or any other wall (whole warps: a y-edge row or a z-edge
+    // plane).
+    enum { PATH_FREE = 0, PATH_XWALL = 1, PATH_WALL = 2 };
+
     // Odd step of plane k (tile threads): gather from the rings and the
     // registers, collide.  rk = rest of plane k; zpm / zp0 = +z values of
     // planes k-1 / k; zm0 / zm1 = -z values of planes k / k+1.
-    __device__ __forceinline__ void consume(int k, R (&s)[Q], R rk, R zpm, R zp0, R zm0, R zm1) const
+    __device__ __forceinline__ void consume(int k, int path, R (&s)[Q], R rk, R zpm, R zp0, R zm0, R zm1) const
     {
         const bool zlo = k == 0, zhi = k == nz - 1;
         const unsigned wm = wxy | (zlo ? CZM : 0u) | (zhi ? CZP : 0u);
         s[0] = rk;
         s[DIR_ZP] = zlo ? zm0 : zpm;
         s[DIR_ZM] = zhi ? zp0 : zm1;
-        if (!wm) {
+        if (path == PATH_FREE) {
             static_for<Q>([&](auto K) {
                 constexpr int i = decltype(K)::value;
                 constexpr int gg = grp(i);
                 if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P)
                     s[i] = ring_at<gg>(k - cz(i), gidx(i))[pos - cx(i) - cy(i) * W];
+            });
+        } else if (path == PATH_XWALL) {
+            // only directions with c_x != 0 can come back from an x wall;
+            // pick the cell's own outgoing value along c_opp(i) by address
+            static_for<Q>([&](auto K) {
+                constexpr int i = decltype(K)::value;
+                constexpr int gg = grp(i);
+                if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P) {
+                    const R *pn = ring_at<gg>(k - cz(i), gidx(i)) + (pos - cx(i) - cy(i) * W);
+                    if constexpr (cx(i) == 0) {
+                        s[i] = *pn;
+                    } else {
+                        const R *pw = ring_at<grp(opp(i))>(k, gidx(opp(i))) + pos;
+                        s[i] = *((wm >> opp(i)) & 1u ? pw : pn);
+                    }
+                }
             });
         } else {
             // a link from x - c_i that crosses a wall brings back the cell's
@@ -234,13 +259,28 @@ struct NSCta {
     // ZP = true the five with c_z = +1 (targets in plane k+1, or plane k
     // across the top wall), which wait for the neighbours' copies of k+1.
     template <bool ZP>
-    __device__ __forceinline__ void scatter(int k, const R (&s)[Q]) const
+    __device__ __forceinline__ void scatter(int k, int path, const R (&s)[Q]) const
     {
         const int c = cxy + k * (int)g.plane;
-        if (!xybnd && k > 0 && k < nz - 1) {
+        if (path == PATH_FREE) {
             static_for<Q>([&](auto K) {
                 constexpr int i = decltype(K)::value;
                 if constexpr ((cz(i) == 1) == ZP) st_no_l1(&fo.p[i][c], encode<S, i>(s[i]));
+            });
+        } else if (path == PATH_XWALL) {
+            // an x-wall link stores into the cell's own slot opp(i) (same
+            // weight, so the same encoding), with the lid term on a lid face
+            static_for<Q>([&](auto K) {
+                constexpr int i = decltype(K)::value;
+                if constexpr ((cz(i) == 1) == ZP) {
+                    if constexpr (cx(i) == 0) {
+                        st_no_l1(&fo.p[i][c], encode<S, i>(s[i]));
+                    } else {
+                        const bool w = (wxy >> i) & 1u;
+                        const R v = (lxy >> i) & 1u ? radd(s[i], g.L[opp(i)]) : s[i];
+                        st_no_l1(w ? &fd.p[opp(i)][c] : &fo.p[i][c], encode<S, i>(v));
+                    }
+                }
             });
         } else {
             const Faces fc = faces_of(g, x, y, k);
@@ -334,9 +374,13 @@ __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
     // sync warp: publish our copies as they land (at least planes 0 ..
     // must_pub) and wait until every neighbour has loaded plane `need`
     // (need < 0: no condition).  The progress words are read and written
-    // relaxed; the data a word vouches for is in shared memory before it is
-    // written (its mbarrier phase completed), and one fence after the
-    // neighbours' words were seen orders the CTA's later pushes after them.
+    // relaxed, without fences: a word is written only after the copy it
+    // vouches for has completed (its mbarrier phase, data in shared memory),
+    // and the CTA's pushes that depend on a neighbour's word are issued only
+    // after the load that saw it has returned (the push barrier follows the
+    // poll), so no push can reach a location before the copy that reads it.
+    // (A fence here would wait for the CTA's whole store stream to drain,
+    // several microseconds per interval.)
     auto sync_interval = [&](int need, int must_pub) {
         bool mine = nb < 0 || need < 0;
         bool done = false;
@@ -353,7 +397,6 @@ __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
             __nanosleep(64);
         }
         if (!done && lane == 0) abort_flag[ph & 1] = 1;
-        __threadfence();
     };
     // the tile warps and the sync warp meet here once per interval, before
     // the pushes into plane k+1
@@ -361,6 +404,9 @@ __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
         asm volatile("bar.sync 1, %0;" ::"r"(32 * (TY + 1)) : "memory");
     };
 
+    // which of the warp's cells have wall links through x or y faces (tile
+    // warps; every lane votes)
+    const bool warp_x = __any_sync(0xffffffffu, c.xwall), warp_y = __any_sync(0xffffffffu, c.ywall);
     // rest of planes k, k+1; +z of planes k-1, k, k+1; -z of planes k, k+1
     R rk = R(0), rk1 = R(0), zpm = R(0), zp0 = R(0), zp1 = R(0), zm0 = R(0), zm1 = R(0);
     // prologue: even steps of planes 0 and 1; the copy of plane 2 goes into
@@ -396,6 +442,7 @@ __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
         R s[Q];
         R rn = R(0), zpn = R(0), zmn = R(0);
         const bool odd_first = (threadIdx.x & 32) == 0;
+        const int path = (k == 0 || k == nz - 1 || warp_y) ? C::PATH_WALL : (warp_x ? C::PATH_XWALL : C::PATH_FREE);
         if (c.role == C::SYNC) {
             if (lane == 0 && k + 3 < nz) issue(k + 3);
             sync_interval(k + 1 < nz ? k + 1 : nz - 1, k + 2 < nz ? k + 2 : nz - 1);
@@ -403,20 +450,20 @@ __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
         } else {
             const bool tile_cell = c.role == C::TILE && cell;
             if (tile_cell && odd_first) {
-                c.consume(k, s, rk, zpm, zp0, zm0, zm1);
-                c.template scatter<false>(k, s);
+                c.consume(k, path, s, rk, zpm, zp0, zm0, zm1);
+                c.template scatter<false>(k, path, s);
             }
             if (k + 2 < nz && cell) {
                 if (wait_stage(k + 2)) c.produce(k + 2, rn, zpn, zmn);
                 else abort_flag[ph & 1] = 1;
             }
             if (tile_cell && !odd_first) {
-                c.consume(k, s, rk, zpm, zp0, zm0, zm1);
-                c.template scatter<false>(k, s);
+                c.consume(k, path, s, rk, zpm, zp0, zm0, zm1);
+                c.template scatter<false>(k, path, s);
             }
             if (c.role == C::TILE) {
                 push_barrier();
-                if (tile_cell && !abort_flag[ph & 1]) c.template scatter<true>(k, s);
+                if (tile_cell && !abort_flag[ph & 1]) c.template scatter<true>(k, path, s);
             }
         }
         rk = rk1; rk1 = rn;
