@@ -197,11 +197,51 @@ struct NSCta {
     }
 
     // Path of a tile warp's odd step, the same for all its lanes (no lane
-    // may diverge from the others): no wall link in the warp, wall links only
-    // through the x faces (one lane at a lattice edge, handled by selecting
-    // addresses), or any other wall (whole warps: a y-edge row or a z-edge
-    // plane).
-    enum { PATH_FREE = 0, PATH_XWALL = 1, PATH_WALL = 2 };
+    // may diverge from the others): no wall link in the warp; wall links
+    // through x or y faces only (a lane at an x edge, a y-edge row), handled
+    // by selecting addresses; or a z-edge plane (general path).  One select
+    // path serves every x/y case: separate variants per face made the kernel
+    // larger and every tile slower.
+    enum { PATH_FREE = 0, PATH_XYWALL = 3, PATH_WALL = 4 };
+    // directions whose links can cross the faces of select set SEL (bit 0:
+    // x faces, bit 1: y faces)
+    template <int SEL, int I>
+    __host__ __device__ static constexpr bool selected() { return ((SEL & 1) && cx(I) != 0) || ((SEL & 2) && cy(I) != 0); }
+
+    template <int SEL>
+    __device__ __forceinline__ void gather_sel(int k, unsigned wm, R (&s)[Q]) const
+    {
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            constexpr int gg = grp(i);
+            if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P) {
+                const R *pn = ring_at<gg>(k - cz(i), gidx(i)) + (pos - cx(i) - cy(i) * W);
+                if constexpr (selected<SEL, i>()) {
+                    const R *pw = ring_at<grp(opp(i))>(k, gidx(opp(i))) + pos;
+                    s[i] = *((wm >> opp(i)) & 1u ? pw : pn);
+                } else {
+                    s[i] = *pn;
+                }
+            }
+        });
+    }
+
+    template <int SEL, bool ZP>
+    __device__ __forceinline__ void push_sel(int c, const R (&s)[Q]) const
+    {
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            if constexpr ((cz(i) == 1) == ZP) {
+                if constexpr (selected<SEL, i>()) {
+                    const bool w = (wxy >> i) & 1u;
+                    const R v = (lxy >> i) & 1u ? radd(s[i], g.L[opp(i)]) : s[i];
+                    st_no_l1(w ? &fd.p[opp(i)][c] : &fo.p[i][c], encode<S, i>(v));
+                } else {
+                    st_no_l1(&fo.p[i][c], encode<S, i>(s[i]));
+                }
+            }
+        });
+    }
 
     // Odd step of plane k (tile threads): gather from the rings and the
     // registers, collide.  rk = rest of plane k; zpm / zp0 = +z values of
@@ -220,22 +260,10 @@ struct NSCta {
                 if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P)
                     s[i] = ring_at<gg>(k - cz(i), gidx(i))[pos - cx(i) - cy(i) * W];
             });
-        } else if (path == PATH_XWALL) {
-            // only directions with c_x != 0 can come back from an x wall;
-            // pick the cell's own outgoing value along c_opp(i) by address
-            static_for<Q>([&](auto K) {
-                constexpr int i = decltype(K)::value;
-                constexpr int gg = grp(i);
-                if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P) {
-                    const R *pn = ring_at<gg>(k - cz(i), gidx(i)) + (pos - cx(i) - cy(i) * W);
-                    if constexpr (cx(i) == 0) {
-                        s[i] = *pn;
-                    } else {
-                        const R *pw = ring_at<grp(opp(i))>(k, gidx(opp(i))) + pos;
-                        s[i] = *((wm >> opp(i)) & 1u ? pw : pn);
-                    }
-                }
-            });
+        } else if (path == PATH_XYWALL) {
+            // a link from x - c_i that crosses a wall brings back the cell's
+            // own outgoing value along c_opp(i): picked by address
+            gather_sel<3>(k, wm, s);
         } else {
             // a link from x - c_i that crosses a wall brings back the cell's
             // own outgoing value along c_opp(i) (lid term already added)
@@ -267,21 +295,11 @@ struct NSCta {
                 constexpr int i = decltype(K)::value;
                 if constexpr ((cz(i) == 1) == ZP) st_no_l1(&fo.p[i][c], encode<S, i>(s[i]));
             });
-        } else if (path == PATH_XWALL) {
-            // an x-wall link stores into the cell's own slot opp(i) (same
-            // weight, so the same encoding), with the lid term on a lid face
-            static_for<Q>([&](auto K) {
-                constexpr int i = decltype(K)::value;
-                if constexpr ((cz(i) == 1) == ZP) {
-                    if constexpr (cx(i) == 0) {
-                        st_no_l1(&fo.p[i][c], encode<S, i>(s[i]));
-                    } else {
-                        const bool w = (wxy >> i) & 1u;
-                        const R v = (lxy >> i) & 1u ? radd(s[i], g.L[opp(i)]) : s[i];
-                        st_no_l1(w ? &fd.p[opp(i)][c] : &fo.p[i][c], encode<S, i>(v));
-                    }
-                }
-            });
+        } else if (path == PATH_XYWALL) {
+            // a wall link through an x or y face stores into the cell's own
+            // slot opp(i) (same weight, so the same encoding), with the lid
+            // term on a lid face
+            push_sel<3, ZP>(c, s);
         } else {
             const Faces fc = faces_of(g, x, y, k);
             static_for<Q>([&](auto K) {
@@ -442,7 +460,7 @@ __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
         R s[Q];
         R rn = R(0), zpn = R(0), zmn = R(0);
         const bool odd_first = (threadIdx.x & 32) == 0;
-        const int path = (k == 0 || k == nz - 1 || warp_y) ? C::PATH_WALL : (warp_x ? C::PATH_XWALL : C::PATH_FREE);
+        const int path = (k == 0 || k == nz - 1) ? C::PATH_WALL : (warp_x || warp_y ? C::PATH_XYWALL : C::PATH_FREE);
         if (c.role == C::SYNC) {
             if (lane == 0 && k + 3 < nz) issue(k + 3);
             sync_interval(k + 1 < nz ? k + 1 : nz - 1, k + 2 < nz ? k + 2 : nz - 1);
