@@ -160,6 +160,43 @@ struct NSCta {
         else if constexpr (GG == GRP_0) return ring0 + (slot(plane, L::RS0) * ND0 + gi) * NPOS;
         else return ringp + (slot(plane, L::RSP) * NDP + gi) * NPOS;
     }
+    // Ring bases at this thread's position for the planes one interval
+    // touches, computed once per interval (the slot arithmetic stays out of
+    // the unrolled direction loops, whose accesses become base + constant).
+    struct Bases {
+        R *m0, *m1;  // c_z = -1 group: planes k, k+1
+        R *z0;       // c_z = 0 group: plane k
+        R *pm, *p0;  // c_z = +1 group: planes k-1, k
+    };
+    __device__ __forceinline__ Bases bases(int k) const
+    {
+        const int s3 = k % L::RSM;
+        Bases b;
+        b.m0 = ringm + s3 * (NDM * NPOS) + pos;
+        b.m1 = ringm + (s3 + 1 == L::RSM ? 0 : s3 + 1) * (NDM * NPOS) + pos;
+        b.z0 = ring0 + (k % L::RS0) * (ND0 * NPOS) + pos;
+        b.pm = ringp + ((k + L::RSP - 1) % L::RSP) * (NDP * NPOS) + pos;
+        b.p0 = ringp + (k % L::RSP) * (NDP * NPOS) + pos;
+        return b;
+    }
+    // value gathered for direction I from x - c_I (plane k - c_z), and the
+    // cell's own outgoing value along c_opp(I) (plane k)
+    template <int I>
+    __device__ __forceinline__ static const R *from_neighbour(const Bases &b)
+    {
+        constexpr int gg = grp(I), off = gidx(I) * NPOS - cx(I) - cy(I) * W;
+        if constexpr (gg == GRP_M) return b.m1 + off;
+        else if constexpr (gg == GRP_0) return b.z0 + off;
+        else return b.pm + off;
+    }
+    template <int I>
+    __device__ __forceinline__ static const R *own_outgoing(const Bases &b)
+    {
+        constexpr int j = opp(I), gg = grp(j), off = gidx(j) * NPOS;
+        if constexpr (gg == GRP_M) return b.m0 + off;
+        else if constexpr (gg == GRP_0) return b.z0 + off;
+        else return b.p0 + off;
+    }
     __device__ __forceinline__ T *stage(int p) const { return reinterpret_cast<T *>(smem + (p & 1) * SM::stage_bytes); }
 
     // Even step of plane p (tile and halo threads): collide the staged
@@ -185,11 +222,16 @@ struct NSCta {
                 if (lm & (1u << i)) s[i] = radd(s[i], g.L[opp(i)]);
             });
         }
+        R *const wm_ = ringm + (p % L::RSM) * (NDM * NPOS) + pos;
+        R *const w0_ = ring0 + (p % L::RS0) * (ND0 * NPOS) + pos;
+        R *const wp_ = ringp + (p % L::RSP) * (NDP * NPOS) + pos;
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;
             constexpr int gg = grp(i);
             const R v = roundtrip<S, i>(s[i]);
-            if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P) ring_at<gg>(p, gidx(i))[pos] = v;
+            if constexpr (gg == GRP_M) wm_[gidx(i) * NPOS] = v;
+            else if constexpr (gg == GRP_0) w0_[gidx(i) * NPOS] = v;
+            else if constexpr (gg == GRP_P) wp_[gidx(i) * NPOS] = v;
             else if constexpr (i == 0) rest = v;
             else if constexpr (i == DIR_ZP) zp = v;
             else zm = v;
@@ -209,19 +251,16 @@ struct NSCta {
     __host__ __device__ static constexpr bool selected() { return ((SEL & 1) && cx(I) != 0) || ((SEL & 2) && cy(I) != 0); }
 
     template <int SEL>
-    __device__ __forceinline__ void gather_sel(int k, unsigned wm, R (&s)[Q]) const
+    __device__ __forceinline__ void gather_sel(const Bases &b, unsigned wm, R (&s)[Q]) const
     {
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;
             constexpr int gg = grp(i);
             if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P) {
-                const R *pn = ring_at<gg>(k - cz(i), gidx(i)) + (pos - cx(i) - cy(i) * W);
-                if constexpr (selected<SEL, i>()) {
-                    const R *pw = ring_at<grp(opp(i))>(k, gidx(opp(i))) + pos;
-                    s[i] = *((wm >> opp(i)) & 1u ? pw : pn);
-                } else {
-                    s[i] = *pn;
-                }
+                if constexpr (selected<SEL, i>())
+                    s[i] = *((wm >> opp(i)) & 1u ? own_outgoing<i>(b) : from_neighbour<i>(b));
+                else
+                    s[i] = *from_neighbour<i>(b);
             }
         });
     }
@@ -253,17 +292,17 @@ struct NSCta {
         s[0] = rk;
         s[DIR_ZP] = zlo ? zm0 : zpm;
         s[DIR_ZM] = zhi ? zp0 : zm1;
+        const Bases b = bases(k);
         if (path == PATH_FREE) {
             static_for<Q>([&](auto K) {
                 constexpr int i = decltype(K)::value;
                 constexpr int gg = grp(i);
-                if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P)
-                    s[i] = ring_at<gg>(k - cz(i), gidx(i))[pos - cx(i) - cy(i) * W];
+                if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P) s[i] = *from_neighbour<i>(b);
             });
         } else if (path == PATH_XYWALL) {
             // a link from x - c_i that crosses a wall brings back the cell's
             // own outgoing value along c_opp(i): picked by address
-            gather_sel<3>(k, wm, s);
+            gather_sel<3>(b, wm, s);
         } else {
             // a link from x - c_i that crosses a wall brings back the cell's
             // own outgoing value along c_opp(i) (lid term already added)
@@ -271,8 +310,8 @@ struct NSCta {
                 constexpr int i = decltype(K)::value;
                 constexpr int gg = grp(i);
                 if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P) {
-                    if (wm & (1u << opp(i))) s[i] = ring_at<grp(opp(i))>(k, gidx(opp(i)))[pos];
-                    else s[i] = ring_at<gg>(k - cz(i), gidx(i))[pos - cx(i) - cy(i) * W];
+                    if (wm & (1u << opp(i))) s[i] = *own_outgoing<i>(b);
+                    else s[i] = *from_neighbour<i>(b);
                 }
             });
         }
@@ -416,17 +455,14 @@ __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
         }
         if (!done && lane == 0) abort_flag[ph & 1] = 1;
     };
-    // the tile warps and the sync warp meet here once per interval, before
-    // the pushes into plane k+1
-    auto push_barrier = [&]() {
-        asm volatile("bar.sync 1, %0;" ::"r"(32 * (TY + 1)) : "memory");
-    };
-
     // which of the warp's cells have wall links through x or y faces (tile
     // warps; every lane votes)
     const bool warp_x = __any_sync(0xffffffffu, c.xwall), warp_y = __any_sync(0xffffffffu, c.ywall);
     // rest of planes k, k+1; +z of planes k-1, k, k+1; -z of planes k, k+1
     R rk = R(0), rk1 = R(0), zpm = R(0), zp0 = R(0), zp1 = R(0), zm0 = R(0), zm1 = R(0);
+    // the odd step's pushes into the next plane, held until the next interval
+    R held[Q];
+    int held_k = -1, held_path = C::PATH_WALL;
     // prologue: even steps of planes 0 and 1; the copy of plane 2 goes into
     // the slot plane 0 leaves; every neighbour must have loaded plane 0
     // before the first pushes
@@ -453,9 +489,11 @@ __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
     // order: even and odd tile warps take them in opposite orders, so that
     // their pushes and collisions interleave); the copy of plane k+3 goes
     // into the slot plane k+1 left in the previous interval.  The pushes
-    // into planes k-1 and k need the neighbours' copies of plane k (waited
-    // for in the previous interval); those into plane k+1 wait at the push
-    // barrier for the sync warp's check of plane k+1.
+    // into planes k-1 and k need the neighbours' copies of plane k; the
+    // pushes of the odd step of plane k into plane k+1 are held in registers
+    // and issued at the start of interval k+1, after the sync warp has seen
+    // the neighbours' copies of plane k+1 (it polls during interval k, before
+    // the barrier that ends it).
     for (int k = 0; k < nz; ++k) {
         R s[Q];
         R rn = R(0), zpn = R(0), zmn = R(0);
@@ -464,9 +502,9 @@ __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
         if (c.role == C::SYNC) {
             if (lane == 0 && k + 3 < nz) issue(k + 3);
             sync_interval(k + 1 < nz ? k + 1 : nz - 1, k + 2 < nz ? k + 2 : nz - 1);
-            push_barrier();
         } else {
             const bool tile_cell = c.role == C::TILE && cell;
+            if (tile_cell && held_k >= 0) c.template scatter<true>(held_k, held_path, held);
             if (tile_cell && odd_first) {
                 c.consume(k, path, s, rk, zpm, zp0, zm0, zm1);
                 c.template scatter<false>(k, path, s);
@@ -479,10 +517,12 @@ __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
                 c.consume(k, path, s, rk, zpm, zp0, zm0, zm1);
                 c.template scatter<false>(k, path, s);
             }
-            if (c.role == C::TILE) {
-                push_barrier();
-                if (tile_cell && !abort_flag[ph & 1]) c.template scatter<true>(k, path, s);
-            }
+            static_for<Q>([&](auto K) {
+                constexpr int i = decltype(K)::value;
+                if constexpr (cz(i) == 1) held[i] = s[i];
+            });
+            held_k = k;
+            held_path = path;
         }
         rk = rk1; rk1 = rn;
         zpm = zp0; zp0 = zp1; zp1 = zpn;
@@ -490,6 +530,9 @@ __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
         cta_barrier();
         if (abort_flag[ph++ & 1]) goto bail;
     }
+    // the last plane's held pushes (the sync warp saw plane nz-1 loaded by
+    // every neighbour before the last barrier)
+    if (c.role == C::TILE && cell && held_k >= 0) c.template scatter<true>(held_k, held_path, held);
     return;
 
 bail:
