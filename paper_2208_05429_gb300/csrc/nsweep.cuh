@@ -244,7 +244,7 @@ struct NSCta {
     // by selecting addresses; or a z-edge plane (general path).  One select
     // path serves every x/y case: separate variants per face made the kernel
     // larger and every tile slower.
-    enum { PATH_FREE = 0, PATH_XYWALL = 3, PATH_WALL = 4 };
+    enum { PATH_FREE = 0, PATH_XYWALL = 3, PATH_XYLID = 5, PATH_WALL = 4 };
     // directions whose links can cross the faces of select set SEL (bit 0:
     // x faces, bit 1: y faces)
     template <int SEL, int I>
@@ -265,7 +265,9 @@ struct NSCta {
         });
     }
 
-    template <int SEL, bool ZP>
+    // LID: some lane of the warp has a wall link ending on a lid through an
+    // x or y face (else the lid term is left out altogether)
+    template <int SEL, bool ZP, bool LID>
     __device__ __forceinline__ void push_sel(int c, const R (&s)[Q]) const
     {
         static_for<Q>([&](auto K) {
@@ -273,7 +275,8 @@ struct NSCta {
             if constexpr ((cz(i) == 1) == ZP) {
                 if constexpr (selected<SEL, i>()) {
                     const bool w = (wxy >> i) & 1u;
-                    const R v = (lxy >> i) & 1u ? radd(s[i], g.L[opp(i)]) : s[i];
+                    R v = s[i];
+                    if constexpr (LID) v = (lxy >> i) & 1u ? radd(s[i], g.L[opp(i)]) : s[i];
                     st_no_l1(w ? &fd.p[opp(i)][c] : &fo.p[i][c], encode<S, i>(v));
                 } else {
                     st_no_l1(&fo.p[i][c], encode<S, i>(s[i]));
@@ -299,7 +302,7 @@ struct NSCta {
                 constexpr int gg = grp(i);
                 if constexpr (gg == GRP_M || gg == GRP_0 || gg == GRP_P) s[i] = *from_neighbour<i>(b);
             });
-        } else if (path == PATH_XYWALL) {
+        } else if (path == PATH_XYWALL || path == PATH_XYLID) {
             // a link from x - c_i that crosses a wall brings back the cell's
             // own outgoing value along c_opp(i): picked by address
             gather_sel<3>(b, wm, s);
@@ -338,7 +341,9 @@ struct NSCta {
             // a wall link through an x or y face stores into the cell's own
             // slot opp(i) (same weight, so the same encoding), with the lid
             // term on a lid face
-            push_sel<3, ZP>(c, s);
+            push_sel<3, ZP, false>(c, s);
+        } else if (path == PATH_XYLID) {
+            push_sel<3, ZP, true>(c, s);
         } else {
             const Faces fc = faces_of(g, x, y, k);
             static_for<Q>([&](auto K) {
@@ -458,6 +463,8 @@ __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
     // which of the warp's cells have wall links through x or y faces (tile
     // warps; every lane votes)
     const bool warp_x = __any_sync(0xffffffffu, c.xwall), warp_y = __any_sync(0xffffffffu, c.ywall);
+    const bool warp_lid = __any_sync(0xffffffffu, c.lxy != 0u);
+    const int xy_path = warp_lid ? C::PATH_XYLID : C::PATH_XYWALL;
     // rest of planes k, k+1; +z of planes k-1, k, k+1; -z of planes k, k+1
     R rk = R(0), rk1 = R(0), zpm = R(0), zp0 = R(0), zp1 = R(0), zm0 = R(0), zm1 = R(0);
     // the odd step's pushes into the next plane, held until the next interval
@@ -498,7 +505,7 @@ __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
         R s[Q];
         R rn = R(0), zpn = R(0), zmn = R(0);
         const bool odd_first = (threadIdx.x & 32) == 0;
-        const int path = (k == 0 || k == nz - 1) ? C::PATH_WALL : (warp_x || warp_y ? C::PATH_XYWALL : C::PATH_FREE);
+        const int path = (k == 0 || k == nz - 1) ? C::PATH_WALL : (warp_x || warp_y ? xy_path : C::PATH_FREE);
         if (c.role == C::SYNC) {
             if (lane == 0 && k + 3 < nz) issue(k + 3);
             sync_interval(k + 1 < nz ? k + 1 : nz - 1, k + 2 < nz ? k + 2 : nz - 1);
