@@ -4,9 +4,10 @@
 Workload (the benchmark configuration): lid-driven cavity 256^3, D3Q19 BGK,
 tau = 0.55, lid u = (0.05, 0, 0) on the z+ face, half-way bounce-back on the
 other five faces, fluid at rest at t = 0; FP32 storage and arithmetic; the
-single-copy AA schedule by default (--variant selects the two-step merged
-sweep, the plane wavefront or two lattices; the other schedules and storage
-formats are reported under "variants").  One benchmark step = two lattice
+two-step merged sweep by default (on this lattice the neighbour-synchronised
+kernel; --variant selects the single-copy AA pair, the plane wavefront or two
+lattices; the other schedules and storage formats are reported under
+"variants", the shadow-shell merged sweep as merged_shadow).  One benchmark step = two lattice
 time steps over all 16.8 M cells (one merged sweep, or an AA even/odd pair).
 MLUPS counts every cell as a fluid node (million lattice-node updates per
 second).
@@ -70,7 +71,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--size", type=int, default=256)
     p.add_argument("--storage", default="f32", choices=sorted(ELEM))
-    p.add_argument("--variant", default="aa", choices=["merged", "wavefront", "aa", "two_lattice"])
+    p.add_argument("--variant", default="merged", choices=["merged", "wavefront", "aa", "two_lattice"])
     p.add_argument("--tile-y", type=int, default=0)
     p.add_argument("--no-extras", action="store_true", help="skip the per-variant, adjoint and CPU legs")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle baseline")
@@ -218,10 +219,22 @@ def alg_bytes_per_launch(kernel: str, storage: str, cells: int) -> float:
     return 2.0 * Q * ELEM[storage] * cells
 
 
-def time_variant(n, storage, variant, steps, warmup, dist_on=False, tile_y=0):
-    """(elapsed ms over `steps` calls of step(2), per-kernel records, lattice)."""
+def time_variant(n, storage, variant, steps, warmup, dist_on=False, tile_y=0, sweep_env=None):
+    """(elapsed ms over `steps` calls of step(2), per-kernel records, lattice).
+    sweep_env: value of LBM_MERGED_SWEEP while the lattice is created (None:
+    the library's own choice)."""
     import torch
-    lat = make_cavity(n, storage, variant, tile_y)
+    old = os.environ.get("LBM_MERGED_SWEEP")
+    if sweep_env is not None:
+        os.environ["LBM_MERGED_SWEEP"] = sweep_env
+    try:
+        lat = make_cavity(n, storage, variant, tile_y)
+    finally:
+        if sweep_env is not None:
+            if old is None:
+                del os.environ["LBM_MERGED_SWEEP"]
+            else:
+                os.environ["LBM_MERGED_SWEEP"] = old
     lat.init_equilibrium()
     for _ in range(warmup):
         lat.step(2)
@@ -597,19 +610,21 @@ def main():
         except Exception as e:  # keep the main line if a secondary leg fails
             line["e2e"] = {"error": repr(e)}
         variants = {}
-        for st, var in (("f32", "merged"), ("f32", "wavefront"), ("f32", "aa"), ("f32", "two_lattice"),
-                        ("f16s", "wavefront"), ("bf16s", "wavefront"), ("f16s", "merged"), ("f16s", "aa"),
-                        ("f64", "wavefront")):
-            if (st, var) == (args.storage, args.variant):
+        for st, var, env in (("f32", "merged", None), ("f32", "aa", None), ("f32", "two_lattice", None),
+                             ("f32", "wavefront", None), ("f32", "merged", "shadow"), ("f32s", "merged", None),
+                             ("f16s", "merged", None), ("f16s", "aa", None), ("bf16s", "merged", None),
+                             ("bf16s", "aa", None), ("f64", "wavefront", None)):
+            if (st, var, env) == (args.storage, args.variant, None):
                 continue
             k = min(args.steps, 300)
-            vms, vprof, vl = time_variant(n, st, var, k, 5)
+            vms, vprof, vl = time_variant(n, st, var, k, 5, sweep_env=env)
             del vl
             dk = {"merged": "merged", "wavefront": "wavefront", "aa": "aa_odd"}.get(var, "two_lattice")
             r = roofline_of(vprof, dk, st, cells, peak, peak_kind)
-            variants[f"{var}_{st}"] = {"MLUPS": round(cells * 2 * k / (vms * 1e3), 1),
-                                       "kernel_frac_of_peak": r["frac"] if r else None,
-                                       "kernel": dk}
+            name = f"{var}_{env}_{st}" if env else f"{var}_{st}"
+            variants[name] = {"MLUPS": round(cells * 2 * k / (vms * 1e3), 1),
+                              "kernel_frac_of_peak": r["frac"] if r else None,
+                              "kernel": dk}
         line["variants"] = variants
         try:
             line["adjoint"] = adjoint_leg()
