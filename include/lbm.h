@@ -75,20 +75,31 @@ enum { LBM_STORAGE_F64 = 0, LBM_STORAGE_F32 = 1, LBM_STORAGE_F32S = 2,
  *                and scatters (the "swap_stream" half of Sec. 3)
  *   MERGED       single copy of the lattice, two time steps per sweep
  *                (Sec. 4): one CTA per 32 x 14 column tile (32 x 4 in F64)
- *                marches z (periodic z included; with fewer tiles than SMs,
- *                one CTA per tile and z chunk of at least 4 planes; the
- *                environment variable LBM_MERGED_ZCHUNKS sets the chunk
- *                count at handle creation), its
- *                even-step warps collide plane k+2 into shared-memory rings
- *                while its odd-step warps collide plane k and scatter.  The
- *                cells on the tile boundaries (read by up to four tiles) are
- *                also kept in a double-buffered shadow: a sweep reads them
- *                from the current copy and writes the next one, so tiles
- *                never read what a neighbour has already overwritten (the
- *                role of the intersection layers, Stage I of Alg. 3).  With
- *                an explicit tile_y (or a periodic z with nz = 1) the older
- *                form runs instead: a pre-pass snapshots the tile shells
- *                every sweep.
+ *                marches z; each interval it does the odd step of plane k and
+ *                the even step of plane k+2, handing post-collision values
+ *                between the two through shared-memory rings.  Two kernels
+ *                make the tiles safe where they meet (the role of the
+ *                intersection layers of Alg. 3):
+ *                - neighbour-synchronised sweep (every face a wall or lid,
+ *                  4- and 2-byte storage, at least half as many tiles as
+ *                  SMs, all tiles resident at once): one cooperative launch;
+ *                  a tile pushes into a plane only after its eight neighbour
+ *                  tiles have copied that plane, which they announce in
+ *                  per-tile progress words in global memory (bounded waits,
+ *                  status bit 8);
+ *                - shadow-shell sweep (otherwise): the tile-boundary cells
+ *                  also live in a double-buffered shadow that the sweep
+ *                  reads from the current copy and writes to the next, so
+ *                  tiles need no synchronisation (with fewer tiles than
+ *                  SMs, z is split into chunks of at least 4 planes; the
+ *                  environment variable LBM_MERGED_ZCHUNKS sets the chunk
+ *                  count at handle creation).
+ *                LBM_MERGED_SWEEP=shadow at handle creation selects the
+ *                shadow-shell sweep, =neighbour the neighbour-synchronised
+ *                one for any tile count it can hold resident.  With an
+ *                explicit tile_y (or a periodic z with nz = 1) an older form
+ *                runs instead: a pre-pass snapshots the tile shells every
+ *                sweep.
  *   WAVEFRONT    single copy, two time steps per DRAM round trip through the
  *                L2 cache (the cache reuse of Sec. 4.1 and 5.2): one
  *                persistent kernel runs the even step of plane p+L+1 and the
@@ -135,12 +146,14 @@ void lbm_config_default(lbm_config *cfg);
 int lbm_validate(const lbm_config *cfg);
 
 /* Device bytes a handle of this configuration uses (populations, second
- * lattice for TWO_LATTICE, tile-shell snapshot for MERGED, work schedule
- * for WAVEFRONT, reduction scratch), each region aligned to 256 bytes.
+ * lattice for TWO_LATTICE, tile-shell shadow or progress words for MERGED,
+ * work schedule for WAVEFRONT, reduction scratch), each region aligned to
+ * 256 bytes.
  * *bytes is a host output.  For MERGED the figure depends on the current
- * device (its SM count sets the z chunks) and on LBM_MERGED_ZCHUNKS, both
- * read at each call: query with the device and environment the handle will
- * be created with. */
+ * device (its SM count and the resident CTAs choose the sweep and the z
+ * chunks) and on LBM_MERGED_SWEEP and LBM_MERGED_ZCHUNKS, all read at each
+ * call: query with the device and environment the handle will be created
+ * with. */
 int lbm_required_bytes(const lbm_config *cfg, size_t *bytes);
 
 /* Create a handle that allocates its own device memory (stream-ordered,
@@ -212,9 +225,10 @@ int lbm_init_populations(lbm_handle *h, const void *f_in, int32_t dtype);
  * Deterministic (fixed summation tree).  Synchronises the stream.
  * LBM_ENONFINITE if any cell has a non-finite density or velocity; out is
  * still written.  LBM_ETIMEOUT if, since the previous call, a MERGED sweep
- * gave up waiting for one of its asynchronous plane copies or a WAVEFRONT
- * sweep for one of its work items (every wait in the kernels is bounded);
- * the lattice is then invalid and the flag is cleared. */
+ * gave up waiting for one of its asynchronous plane copies or for a
+ * neighbouring tile's progress word, or a WAVEFRONT sweep for one of its
+ * work items (every wait in the kernels is bounded); the lattice is then
+ * invalid and the flag is cleared. */
 int lbm_reduce(lbm_handle *h, double *out);
 
 /* The sums of lbm_reduce() for a population field the caller holds, computed
