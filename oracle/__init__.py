@@ -34,6 +34,7 @@ import numpy as np
 Q = 19
 BC_PERIODIC, BC_WALL, BC_LID = 0, 1, 2
 FORCE_NONE, FORCE_UNIFORM, FORCE_FIELD = 0, 1, 2
+COLL_BGK, COLL_TRT = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
@@ -67,6 +68,8 @@ class _Cfg(ctypes.Structure):
         ("force_mode", ctypes.c_int32),
         ("force_uniform", ctypes.c_double * 3),
         ("force_field", ctypes.POINTER(ctypes.c_double)),
+        ("collision", ctypes.c_int32),
+        ("trt_lambda", ctypes.c_double),
     ]
 
 
@@ -84,6 +87,7 @@ def _load():
                 "orc_lattice": [_I32, _D, _I32],
                 "orc_equilibrium": [ctypes.c_double, _D, _D],
                 "orc_collide_cell": [ctypes.c_double, _D, _D, _D],
+                "orc_collide_cell_trt": [ctypes.c_double, ctypes.c_double, _D, _D, _D],
                 "orc_init_equilibrium": [P, _D, _D, _D],
                 "orc_step": [P, _D, _D],
                 "orc_run": [P, _D, ctypes.c_int64, _D],
@@ -128,6 +132,8 @@ class Config:
     force_mode: int = FORCE_NONE
     force_uniform: Sequence[float] = (0.0, 0.0, 0.0)
     force_field: Optional[np.ndarray] = field(default=None, repr=False)
+    collision: int = 0            # COLL_BGK or COLL_TRT
+    trt_lambda: float = 3.0 / 16.0
 
     @property
     def shape(self):
@@ -148,6 +154,8 @@ class Config:
             c.force_uniform[a] = float(self.force_uniform[a])
         c.rho_wall = float(self.rho_wall)
         c.force_mode = int(self.force_mode)
+        c.collision = int(self.collision)
+        c.trt_lambda = float(self.trt_lambda)
         if self.force_mode == FORCE_FIELD:
             ff = np.ascontiguousarray(self.force_field, dtype=np.float64).reshape(3, *self.shape)
             self._ff_keep = ff  # keep the buffer alive for the call
@@ -178,6 +186,15 @@ def equilibrium(rho: float, u) -> np.ndarray:
     uu = np.ascontiguousarray(u, dtype=np.float64)
     out = np.zeros(Q, np.float64)
     lib.orc_equilibrium(float(rho), _ptr(uu), _ptr(out))
+    return out
+
+
+def collide_cell_trt(tau: float, lam: float, f, F=(0.0, 0.0, 0.0)) -> np.ndarray:
+    lib = _load()
+    ff = np.ascontiguousarray(f, dtype=np.float64)
+    FF = np.ascontiguousarray(F, dtype=np.float64)
+    out = np.zeros(Q, np.float64)
+    lib.orc_collide_cell_trt(float(tau), float(lam), _ptr(ff), _ptr(FF), _ptr(out))
     return out
 
 

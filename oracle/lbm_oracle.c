@@ -26,6 +26,14 @@
  *                feq_i = w_i rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u)
  *                S_i   = w_i (3 (c_i - u) + 9 (c_i.u) c_i) . F
  *                f*_i  = f_i - omega (f_i - feq_i) + (1 - omega/2) S_i
+ *              or, as one of the "collision models" the paper's solver
+ *              builds on (Sec. 1), the two-relaxation-time (TRT) form: with
+ *              the symmetric and antisymmetric parts a^+-_i = (a_i +- a_opp(i))/2
+ *              of f, feq and S, the rates omega+ = 1/tau and omega- given by
+ *              the "magic" product Lambda = (1/omega+ - 1/2)(1/omega- - 1/2),
+ *                f*_i  = f_i - omega+ (f+_i - feq+_i) - omega- (f-_i - feq-_i)
+ *                        + (1 - omega+/2) S+_i + (1 - omega-/2) S-_i
+ *              (omega- = omega+ gives back BGK).
  *   streaming  f_i(x + c_i, t+1) = f*_i(x); periodic axes wrap; a link that
  *              leaves the box across a non-periodic face is a wall link
  *              (half-way bounce-back):
@@ -55,6 +63,7 @@
 
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_LID = 2 };
 enum { FORCE_NONE = 0, FORCE_UNIFORM = 1, FORCE_FIELD = 2 };
+enum { COLL_BGK = 0, COLL_TRT = 1 };
 
 /* The D3Q19 velocity set in the half-neighbour order described above. */
 static const int C[Q][3] = {
@@ -84,6 +93,8 @@ typedef struct {
     int32_t force_mode;
     double force_uniform[3];
     const double *force_field; /* [3][N] canonical, used when FORCE_FIELD */
+    int32_t collision;         /* COLL_BGK or COLL_TRT */
+    double trt_lambda;         /* Lambda of the TRT form */
 } orc_cfg;
 
 static int64_t ncells(const orc_cfg *g) { return g->nx * g->ny * g->nz; }
@@ -184,6 +195,44 @@ void orc_collide_cell(double tau, const double *f, const double *F, double *fsta
     }
 }
 
+/* TRT collision of one cell: the BGK ingredients above, relaxed by parts. */
+void orc_collide_cell_trt(double tau, double lambda, const double *f, const double *F, double *fstar)
+{
+    double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < Q; ++i) {
+        rho += f[i];
+        for (int a = 0; a < 3; ++a) m[a] += f[i] * C[i][a];
+    }
+    double u[3];
+    for (int a = 0; a < 3; ++a) u[a] = (m[a] + 0.5 * F[a]) / rho;
+    const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+    const double omega_p = 1.0 / tau;
+    const double omega_m = 1.0 / (0.5 + lambda / (tau - 0.5));
+    double feq[Q], S[Q];
+    for (int i = 0; i < Q; ++i) {
+        const double cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
+        const double cF = C[i][0] * F[0] + C[i][1] * F[1] + C[i][2] * F[2];
+        feq[i] = W[i] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+        S[i] = W[i] * (3.0 * (cF - uF) + 9.0 * cu * cF);
+    }
+    for (int i = 0; i < Q; ++i) {
+        const int o = OPP(i);
+        const double fp = 0.5 * (f[i] + f[o]), fm = 0.5 * (f[i] - f[o]);
+        const double ep = 0.5 * (feq[i] + feq[o]), em = 0.5 * (feq[i] - feq[o]);
+        const double sp = 0.5 * (S[i] + S[o]), sm = 0.5 * (S[i] - S[o]);
+        fstar[i] = f[i] - omega_p * (fp - ep) - omega_m * (fm - em) + (1.0 - 0.5 * omega_p) * sp +
+                   (1.0 - 0.5 * omega_m) * sm;
+    }
+}
+
+/* The collision the configuration selects. */
+static void collide_cfg(const orc_cfg *g, const double *f, const double *F, double *fstar)
+{
+    if (g->collision == COLL_TRT) orc_collide_cell_trt(g->tau, g->trt_lambda, f, F, fstar);
+    else orc_collide_cell(g->tau, f, F, fstar);
+}
+
 /* ------------------------------------------------------------------ */
 /* field operations                                                    */
 /* ------------------------------------------------------------------ */
@@ -215,7 +264,7 @@ void orc_step(const orc_cfg *g, const double *f_in, double *f_out)
                 double f[Q], fs[Q], F[3];
                 for (int i = 0; i < Q; ++i) f[i] = f_in[i * n + cell];
                 cell_force(g, cell, F);
-                orc_collide_cell(g->tau, f, F, fs);
+                collide_cfg(g, f, F, fs);
                 for (int i = 0; i < Q; ++i) {
                     int64_t t;
                     int lid;
@@ -244,13 +293,13 @@ void orc_step_cells(const orc_cfg *g, const double *f_in, const int64_t *xyz, in
             if (link_target(g, x, y, z, OPP(i), &src, &lid)) {
                 for (int j = 0; j < Q; ++j) f[j] = f_in[j * n + src];
                 cell_force(g, src, F);
-                orc_collide_cell(g->tau, f, F, fs);
+                collide_cfg(g, f, F, fs);
                 out[k * Q + i] = fs[i];
             } else {
                 const int64_t self = cell_index(g, x, y, z);
                 for (int j = 0; j < Q; ++j) f[j] = f_in[j * n + self];
                 cell_force(g, self, F);
-                orc_collide_cell(g->tau, f, F, fs);
+                collide_cfg(g, f, F, fs);
                 out[k * Q + i] = fs[OPP(i)] - wall_term(g, OPP(i), lid);
             }
         }
