@@ -207,10 +207,10 @@ def sync_all(dist_on):
 
 # ------------------------------------------------------------------ GPU legs
 
-def make_cavity(n, storage, variant, tile_y=0):
+def make_cavity(n, storage, variant, tile_y=0, collision="bgk"):
     from paper_2208_05429_gb300.lbm import CAVITY_BC, Lattice
     return Lattice((n, n, n), TAU, bc=CAVITY_BC, u_lid=U_LID, storage=storage, variant=variant,
-                   tile=(32 if tile_y else 0, tile_y))
+                   tile=(32 if tile_y else 0, tile_y), collision=collision)
 
 
 def alg_bytes_per_launch(kernel: str, storage: str, cells: int) -> float:
@@ -219,7 +219,7 @@ def alg_bytes_per_launch(kernel: str, storage: str, cells: int) -> float:
     return 2.0 * Q * ELEM[storage] * cells
 
 
-def time_variant(n, storage, variant, steps, warmup, dist_on=False, tile_y=0, sweep_env=None):
+def time_variant(n, storage, variant, steps, warmup, dist_on=False, tile_y=0, sweep_env=None, collision="bgk"):
     """(elapsed ms over `steps` calls of step(2), per-kernel records, lattice).
     sweep_env: value of LBM_MERGED_SWEEP while the lattice is created (None:
     the library's own choice)."""
@@ -228,7 +228,7 @@ def time_variant(n, storage, variant, steps, warmup, dist_on=False, tile_y=0, sw
     if sweep_env is not None:
         os.environ["LBM_MERGED_SWEEP"] = sweep_env
     try:
-        lat = make_cavity(n, storage, variant, tile_y)
+        lat = make_cavity(n, storage, variant, tile_y, collision)
     finally:
         if sweep_env is not None:
             if old is None:
@@ -613,11 +613,14 @@ def main():
         for st, var, env in (("f32", "merged", None), ("f32", "aa", None), ("f32", "two_lattice", None),
                              ("f32", "wavefront", None), ("f32", "merged", "shadow"), ("f32s", "merged", None),
                              ("f16s", "merged", None), ("f16s", "aa", None), ("bf16s", "merged", None),
-                             ("bf16s", "aa", None), ("f64", "wavefront", None)):
+                             ("bf16s", "aa", None), ("f64", "wavefront", None), ("f32", "aa", "trt"),
+                             ("f16s", "aa", "trt")):
             if (st, var, env) == (args.storage, args.variant, None):
                 continue
             k = min(args.steps, 300)
-            vms, vprof, vl = time_variant(n, st, var, k, 5, sweep_env=env)
+            coll = "trt" if env == "trt" else "bgk"
+            vms, vprof, vl = time_variant(n, st, var, k, 5, sweep_env=None if env == "trt" else env,
+                                          collision=coll)
             del vl
             dk = {"merged": "merged", "wavefront": "wavefront", "aa": "aa_odd"}.get(var, "two_lattice")
             r = roofline_of(vprof, dk, st, cells, peak, peak_kind)

@@ -117,6 +117,15 @@ enum { LBM_VARIANT_TWO_LATTICE = 0, LBM_VARIANT_AA = 1, LBM_VARIANT_MERGED = 2, 
  * FP32 field [3][z][y][x] set with lbm_set_force(). */
 enum { LBM_FORCE_NONE = 0, LBM_FORCE_UNIFORM = 1, LBM_FORCE_FIELD = 2 };
 
+/* Collision operator.  BGK: one relaxation rate 1/tau.  TRT: the parts of
+ * the populations that are symmetric / antisymmetric under c -> -c relax
+ * with 1/tau and with omega-, where (tau - 1/2)(1/omega- - 1/2) = trt_lambda
+ * (the paper's solver builds on "collision models" without naming one,
+ * Sec. 1; the schedules of Sec. 3-4 are independent of the model).  TRT runs
+ * on the AA and TWO_LATTICE schedules; with the others, and for the
+ * adjoint, lbm_validate / the adjoint calls return LBM_EUNSUPPORTED. */
+enum { LBM_COLLISION_BGK = 0, LBM_COLLISION_TRT = 1 };
+
 /* Element type of caller-provided field buffers. */
 enum { LBM_DTYPE_F32 = 0, LBM_DTYPE_F64 = 1 };
 
@@ -132,9 +141,12 @@ typedef struct lbm_config {
     double force_uniform[3];  /* the force of LBM_FORCE_UNIFORM                */
     int32_t tile_x, tile_y;   /* MERGED: 0 = shadow-shell sweep (32 x 14 tiles),
                                  else the snapshot sweep with 32 x tile_y tiles */
+    int32_t collision;        /* LBM_COLLISION_* (default BGK)                  */
+    double trt_lambda;        /* TRT magic product, > 0 (default 3/16)          */
 } lbm_config;
 
-/* Fill cfg with a 32^3 fully periodic FP32 AA lattice, tau = 0.6. */
+/* Fill cfg with a 32^3 fully periodic FP32 AA lattice, tau = 0.6, BGK
+ * (trt_lambda = 3/16 for a later switch to TRT). */
 void lbm_config_default(lbm_config *cfg);
 
 /* Check a configuration without allocating.  LBM_EINVAL on: a dimension < 1,
@@ -142,7 +154,10 @@ void lbm_config_default(lbm_config *cfg);
  * one periodic and one non-periodic face, |u_lid| >= 0.3, rho_wall <= 0,
  * unknown storage/variant/force mode, a tile_x other than 0 or 32, or a
  * tile_y other than 0, 4, 8, 16 or too large for the shared memory of the
- * merged kernel in this storage format (F64 allows 4 only). */
+ * merged kernel in this storage format (F64 allows 4 only), an unknown
+ * collision or a trt_lambda that is not positive and finite.
+ * LBM_EUNSUPPORTED for the TRT collision with a schedule other than AA and
+ * TWO_LATTICE. */
 int lbm_validate(const lbm_config *cfg);
 
 /* Device bytes a handle of this configuration uses (populations, second

@@ -382,6 +382,70 @@ __device__ __forceinline__ void bgk_collide(R (&s)[Q], R omega, R kf, R Fx, R Fy
     });
 }
 
+// Two-relaxation-time (TRT) collision of one cell's shifted populations
+// s_i = f_i - w_i: for each pair of opposite directions the symmetric parts
+// of s, of the equilibrium and of the Guo source relax with omega+ = 1/tau
+// (kf = 1 - omega+/2), the antisymmetric parts with omega- (kfm = 1 -
+// omega-/2), where (1/omega+ - 1/2)(1/omega- - 1/2) = Lambda.  In the
+// notation of bgk_collide, per pair i, i+9:
+//   n+ = (s_i + s_i+9)/2 - sym,  n- = (s_i - s_i+9)/2 - anti,
+//   s_i   <- s_i   - omega+ n+ - omega- n- + kf ssym + kfm santi,
+//   s_i+9 <- s_i+9 - omega+ n+ + omega- n- + kf ssym - kfm santi.
+template <class R, bool FORCE>
+__device__ __forceinline__ void trt_collide(R (&s)[Q], R omega, R kf, R om, R kfm, R Fx, R Fy, R Fz)
+{
+    R dif[10];
+    R drho = s[0];
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        drho = radd(drho, radd(s[i], s[i + 9]));
+        dif[i] = rsub(s[i], s[i + 9]);
+    });
+    R jx = R(0), jy = R(0), jz = R(0);
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        if constexpr (cx(i) != 0) jx = cx(i) > 0 ? radd(jx, dif[i]) : rsub(jx, dif[i]);
+        if constexpr (cy(i) != 0) jy = cy(i) > 0 ? radd(jy, dif[i]) : rsub(jy, dif[i]);
+        if constexpr (cz(i) != 0) jz = cz(i) > 0 ? radd(jz, dif[i]) : rsub(jz, dif[i]);
+    });
+    const R rho = radd(R(1), drho);
+    if constexpr (FORCE) {
+        jx = rfma(R(0.5), Fx, jx);
+        jy = rfma(R(0.5), Fy, jy);
+        jz = rfma(R(0.5), Fz, jz);
+    }
+    const R inv = rrcp(rho);
+    const R ux = rmul(jx, inv), uy = rmul(jy, inv), uz = rmul(jz, inv);
+    const R m15 = rmul(R(-1.5), radd(radd(rmul(ux, ux), rmul(uy, uy)), rmul(uz, uz)));
+    R uF = R(0);
+    if constexpr (FORCE) uF = rfma(ux, Fx, rfma(uy, Fy, rmul(uz, Fz)));
+    // rest: symmetric only, seq_0 = w_0 (rho (-1.5 u.u) + drho), w_0 S_0 = -u.F
+    const R C0 = rfma(rmul(R(1.0 / 3.0), rho), m15, rmul(R(1.0 / 3.0), drho));
+    s[0] = rsub(s[0], rmul(omega, rsub(s[0], C0)));
+    if constexpr (FORCE) s[0] = rfma(kf, -uF, s[0]);
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        constexpr double w = wgt(i);
+        const R cu = cdot<i, R>(ux, uy, uz);
+        const R A = rmul(R(w), rho);
+        const R sym = rfma(rmul(R(4.5), A), rmul(cu, cu), rfma(A, m15, rmul(R(w), drho)));
+        const R anti = rmul(rmul(R(3), A), cu);
+        const R np_ = rsub(rmul(R(0.5), radd(s[i], s[i + 9])), sym);
+        const R nm = rsub(rmul(R(0.5), rsub(s[i], s[i + 9])), anti);
+        R a = rsub(rsub(s[i], rmul(omega, np_)), rmul(om, nm));
+        R b = radd(rsub(s[i + 9], rmul(omega, np_)), rmul(om, nm));
+        if constexpr (FORCE) {
+            const R cF = cdot<i, R>(Fx, Fy, Fz);
+            const R ssym = rfma(rmul(R(9 * w), cu), cF, rmul(R(-3 * w), uF));
+            const R santi = rmul(R(3 * w), cF);
+            a = rfma(kfm, santi, rfma(kf, ssym, a));
+            b = rfma(kfm, -santi, rfma(kf, ssym, b));
+        }
+        s[i] = a;
+        s[i + 9] = b;
+    });
+}
+
 // ---------------------------------------------------------------------------
 // Geometry and boundary description passed by value to every kernel.
 // ---------------------------------------------------------------------------
@@ -394,6 +458,8 @@ struct Geom {
     int64_t plane;       // nxp * ny
     int64_t slot;        // plane * nz: elements per direction
     R omega, kf;         // 1/tau, 1 - omega/2
+    int trt;             // TRT collision (AA and two-lattice kernels)
+    R om, kfm;           // TRT: omega-, 1 - omega-/2
     R L[Q];              // 6 w_k rho_w (c_k . u_lid): added to incoming slot k of a lid link
     R Fu[3];             // uniform force
     const float *Ff;     // per-cell force field [3][N] canonical, or nullptr
@@ -533,6 +599,15 @@ __device__ __forceinline__ void force_at(const Geom<R> &g, int64_t c, int64_t n,
     } else {
         Fx = Fy = Fz = R(0);
     }
+}
+
+// The collision a kernel of the AA or two-lattice schedule applies: BGK, or
+// TRT (a separate kernel instantiation; the other schedules are BGK only).
+template <class R, bool FORCE, bool TRT>
+__device__ __forceinline__ void collide_sel(const Geom<R> &g, R (&s)[Q], R Fx, R Fy, R Fz)
+{
+    if constexpr (TRT) trt_collide<R, FORCE>(s, g.omega, g.kf, g.om, g.kfm, Fx, Fy, Fz);
+    else bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
 }
 
 }  // namespace lbm

@@ -108,6 +108,9 @@ inline Geom<R> make_geom(const HostGeom &h, int64_t pitch)
     g.slot = g.plane * h.nz;
     g.omega = R(h.omega);
     g.kf = R(h.kf);
+    g.trt = h.trt;
+    g.om = R(h.omega_m);
+    g.kfm = R(h.kf_m);
     for (int i = 0; i < Q; ++i) g.L[i] = R(h.L[i]);
     for (int a = 0; a < 3; ++a) g.Fu[a] = R(h.Fu[a]);
     g.Ff = h.Ff;
@@ -307,7 +310,7 @@ __global__ void k_init_eq(Geom<typename S::R> g, typename S::T *__restrict__ f, 
 // K1: two-lattice fused collide-and-push (natural -> natural)
 // ---------------------------------------------------------------------------
 // dout.p[i] = dst.p[i] + noff[i]: the push address of an interior cell.
-template <class S, bool FORCE>
+template <class S, bool FORCE, bool TRT = false>
 __global__ void __launch_bounds__(128) k_two_lattice(Geom<typename S::R> g, Dirs<const typename S::T> src,
                                                      Dirs<typename S::T> dst, Dirs<typename S::T> dout)
 {
@@ -319,7 +322,7 @@ __global__ void __launch_bounds__(128) k_two_lattice(Geom<typename S::R> g, Dirs
     load_natural_d<S>(src, c, s);
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
-    bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
+    collide_sel<R, FORCE, TRT>(g, s, Fx, Fy, Fz);
     if (interior(g, x, y, z)) {
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;
@@ -350,7 +353,7 @@ __device__ __forceinline__ void even_outputs(const Geom<typename S::R> &g, int x
     });
 }
 
-template <class S, bool FORCE>
+template <class S, bool FORCE, bool TRT>
 __device__ __forceinline__ void aa_even_cell(const Geom<typename S::R> &g, const Dirs<typename S::T> &f, int x, int y,
                                              int z, int c)
 {
@@ -362,7 +365,7 @@ __device__ __forceinline__ void aa_even_cell(const Geom<typename S::R> &g, const
     });
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
-    bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
+    collide_sel<R, FORCE, TRT>(g, s, Fx, Fy, Fz);
     even_outputs<S>(g, x, y, z, s);
     static_for<Q>([&](auto K) {
         constexpr int i = decltype(K)::value;
@@ -370,12 +373,12 @@ __device__ __forceinline__ void aa_even_cell(const Geom<typename S::R> &g, const
     });
 }
 
-template <class S, bool FORCE>
+template <class S, bool FORCE, bool TRT = false>
 __global__ void __launch_bounds__(128) k_aa_even(Geom<typename S::R> g, Dirs<typename S::T> f, int z0)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z + z0;
     if (x >= g.nx) return;
-    aa_even_cell<S, FORCE>(g, f, x, y, z, cell32(g, x, y, z));
+    aa_even_cell<S, FORCE, TRT>(g, f, x, y, z, cell32(g, x, y, z));
 }
 
 // The even step for 2-byte storage, two neighbouring cells (x, x+1), x even,
@@ -408,7 +411,7 @@ struct Pair2 {
     }
 };
 
-template <class S, bool FORCE>
+template <class S, bool FORCE, bool TRT = false>
 __global__ void __launch_bounds__(128) k_aa_even_pair(Geom<typename S::R> g, Dirs<typename S::T> f, int z0)
 {
     static_assert(sizeof(typename S::T) == 2 && S::shifted, "2-byte shifted storage");
@@ -417,7 +420,7 @@ __global__ void __launch_bounds__(128) k_aa_even_pair(Geom<typename S::R> g, Dir
     if (x >= g.nx) return;
     const int c = cell32(g, x, y, z);
     if (x + 1 >= g.nx) {  // odd nx: the last cell alone
-        aa_even_cell<S, FORCE>(g, f, x, y, z, c);
+        aa_even_cell<S, FORCE, TRT>(g, f, x, y, z, c);
         return;
     }
     R a[Q], b[Q];
@@ -427,9 +430,9 @@ __global__ void __launch_bounds__(128) k_aa_even_pair(Geom<typename S::R> g, Dir
     });
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
-    bgk_collide<R, FORCE>(a, g.omega, g.kf, Fx, Fy, Fz);
+    collide_sel<R, FORCE, TRT>(g, a, Fx, Fy, Fz);
     force_at<R, FORCE>(g, canon(g, x + 1, y, z), ncanon(g), Fx, Fy, Fz);
-    bgk_collide<R, FORCE>(b, g.omega, g.kf, Fx, Fy, Fz);
+    collide_sel<R, FORCE, TRT>(g, b, Fx, Fy, Fz);
     even_outputs<S>(g, x, y, z, a);
     even_outputs<S>(g, x + 1, y, z, b);
     static_for<Q>([&](auto K) {
@@ -445,7 +448,7 @@ __global__ void __launch_bounds__(128) k_aa_even_pair(Geom<typename S::R> g, Dir
 // locations in this sweep, so the update is race-free in place.  Planes
 // z0 .. z0 + gridDim.z - 1.
 // ---------------------------------------------------------------------------
-template <class S, bool FORCE>
+template <class S, bool FORCE, bool TRT = false>
 __global__ void __launch_bounds__(128) k_aa_odd(Geom<typename S::R> g, Dirs<typename S::T> f, Dirs<typename S::T> fin,
                                                 Dirs<typename S::T> fout, int z0)
 {
@@ -468,7 +471,7 @@ __global__ void __launch_bounds__(128) k_aa_odd(Geom<typename S::R> g, Dirs<type
     }
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
-    bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
+    collide_sel<R, FORCE, TRT>(g, s, Fx, Fy, Fz);
     if (in) {
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;

@@ -36,8 +36,13 @@ struct Launch {
         const Dirs<T> b = make_dirs((T *)dst, slot_of(h, pitch));
         Dirs<T> bo;  // push addresses of an interior cell, one index away
         for (int i = 0; i < Q; ++i) bo.p[i] = b.p[i] + g.noff[i];
-        if (force) k_two_lattice<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo);
-        else k_two_lattice<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo);
+        if (h.trt) {
+            if (force) k_two_lattice<S, true, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo);
+            else k_two_lattice<S, false, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo);
+        } else {
+            if (force) k_two_lattice<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo);
+            else k_two_lattice<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo);
+        }
         return cudaGetLastError();
     }
     // planes [z0, z1) only
@@ -48,12 +53,22 @@ struct Launch {
         const Dirs<T> d = make_dirs((T *)f, slot_of(h, pitch));
         if constexpr (sizeof(T) == 2) {  // two cells per thread (packed 4-byte accesses)
             const dim3 grid((h.nx + 2 * CELL_BLOCK - 1) / (2 * CELL_BLOCK), h.ny, z1 - z0);
-            if (force) k_aa_even_pair<S, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
-            else k_aa_even_pair<S, false><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+            if (h.trt) {
+                if (force) k_aa_even_pair<S, true, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+                else k_aa_even_pair<S, false, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+            } else {
+                if (force) k_aa_even_pair<S, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+                else k_aa_even_pair<S, false><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+            }
         } else {
             const dim3 grid((h.nx + CELL_BLOCK - 1) / CELL_BLOCK, h.ny, z1 - z0);
-            if (force) k_aa_even<S, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
-            else k_aa_even<S, false><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+            if (h.trt) {
+                if (force) k_aa_even<S, true, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+                else k_aa_even<S, false, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+            } else {
+                if (force) k_aa_even<S, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+                else k_aa_even<S, false><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+            }
         }
         return cudaGetLastError();
     }
@@ -68,8 +83,13 @@ struct Launch {
             dout.p[i] = d.p[i] + g.noff[i];
         }
         const dim3 grid((h.nx + CELL_BLOCK - 1) / CELL_BLOCK, h.ny, z1 - z0);
-        if (force) k_aa_odd<S, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, din, dout, z0);
-        else k_aa_odd<S, false><<<grid, CELL_BLOCK, 0, st>>>(g, d, din, dout, z0);
+        if (h.trt) {
+            if (force) k_aa_odd<S, true, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, din, dout, z0);
+            else k_aa_odd<S, false, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, din, dout, z0);
+        } else {
+            if (force) k_aa_odd<S, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, din, dout, z0);
+            else k_aa_odd<S, false><<<grid, CELL_BLOCK, 0, st>>>(g, d, din, dout, z0);
+        }
         return cudaGetLastError();
     }
     static cudaError_t aa_even(const HostGeom &h, int64_t pitch, bool force, void *f, cudaStream_t st)

@@ -333,6 +333,9 @@ HostGeom host_geom(const lbm_config &c)
     for (int k = 0; k < 6; ++k) h.lid[k] = c.face_bc[k] == LBM_BC_LID;
     h.omega = 1.0 / c.tau;
     h.kf = 1.0 - 0.5 * h.omega;
+    h.trt = c.collision == LBM_COLLISION_TRT;
+    h.omega_m = h.trt ? 1.0 / (0.5 + c.trt_lambda / (c.tau - 0.5)) : h.omega;
+    h.kf_m = 1.0 - 0.5 * h.omega_m;
     for (int k = 0; k < Q; ++k) {
         const double cu = cx(k) * c.u_lid[0] + cy(k) * c.u_lid[1] + cz(k) * c.u_lid[2];
         h.L[k] = 6.0 * wgt(k) * c.rho_wall * cu;
@@ -452,6 +455,8 @@ void lbm_config_default(lbm_config *cfg)
     cfg->storage = LBM_STORAGE_F32;
     cfg->variant = LBM_VARIANT_AA;
     cfg->force_mode = LBM_FORCE_NONE;
+    cfg->collision = LBM_COLLISION_BGK;
+    cfg->trt_lambda = 3.0 / 16.0;
 }
 
 int lbm_validate(const lbm_config *c)
@@ -477,6 +482,11 @@ int lbm_validate(const lbm_config *c)
     if (c->tile_x != 0 && c->tile_x != 32) return LBM_EINVAL;
     if (c->tile_y != 0 && c->tile_y != 4 && c->tile_y != 8 && c->tile_y != 16) return LBM_EINVAL;
     if (c->tile_y != 0 && ops_for(c->storage)->merged_smem(c->tile_y) == 0) return LBM_EINVAL;
+    if (c->collision != LBM_COLLISION_BGK && c->collision != LBM_COLLISION_TRT) return LBM_EINVAL;
+    if (!(c->trt_lambda > 0.0) || !isfinite(c->trt_lambda)) return LBM_EINVAL;
+    if (c->collision == LBM_COLLISION_TRT && c->variant != LBM_VARIANT_AA &&
+        c->variant != LBM_VARIANT_TWO_LATTICE)
+        return LBM_EUNSUPPORTED;
     return LBM_OK;
 }
 
@@ -1027,6 +1037,7 @@ int lbm_profile_read(lbm_handle *h, int32_t kernel, int64_t *launches, double *t
 int lbm_adjoint_step(lbm_handle *h, const void *f_t, const void *lambda_in, void *lambda_out, int32_t dtype,
                      double *dLdF)
 {
+    if (h && h->cfg.collision != LBM_COLLISION_BGK) return LBM_EUNSUPPORTED;
     if (!h || !f_t || !lambda_in || !lambda_out || lambda_in == lambda_out || check_dtype(dtype)) return LBM_EINVAL;
     if (!h->force_set) return LBM_ESTATE;
     DeviceGuard g(h->device);
@@ -1037,6 +1048,7 @@ int lbm_adjoint_step(lbm_handle *h, const void *f_t, const void *lambda_in, void
 
 int lbm_adjoint_seed(lbm_handle *h, const void *dLdrho, const void *dLdu, void *lambda, int32_t dtype, double *dLdF)
 {
+    if (h && h->cfg.collision != LBM_COLLISION_BGK) return LBM_EUNSUPPORTED;
     if (!h || !dLdu || !lambda || check_dtype(dtype)) return LBM_EINVAL;
     if (!h->force_set) return LBM_ESTATE;
     DeviceGuard g(h->device);
@@ -1077,6 +1089,7 @@ int lbm_adjoint_workspace_bytes(const lbm_handle *h, int64_t T, int64_t K, size_
 
 int lbm_adjoint_forward(lbm_handle *h, int64_t T, int64_t K, void *work, size_t work_bytes)
 {
+    if (h && h->cfg.collision != LBM_COLLISION_BGK) return LBM_EUNSUPPORTED;
     if (!h || !work || T < 1 || K < 1 || ((uintptr_t)work % ALIGN) != 0) return LBM_EINVAL;
     if (!h->force_set) return LBM_ESTATE;
     const AdjLayout A = adj_layout(h, T, K);

@@ -15,6 +15,8 @@ struct HostGeom {
     int per[3];
     int lid[6];
     double omega, kf;
+    int trt;             // TRT collision
+    double omega_m, kf_m;
     double L[19];
     double Fu[3];
     const float *Ff;

@@ -63,7 +63,8 @@ def make_gpu(cfg: "oracle.Config", storage: str, variant: str, tile=(0, 0), devi
     else:
         force = None
     return Lattice((cfg.nx, cfg.ny, cfg.nz), cfg.tau, bc=tuple(int(b) for b in cfg.bc), u_lid=tuple(cfg.u_lid),
-                   rho_wall=cfg.rho_wall, storage=storage, variant=variant, force=force, tile=tile, device=device)
+                   rho_wall=cfg.rho_wall, storage=storage, variant=variant, force=force, tile=tile, device=device,
+                   collision="trt" if cfg.collision == oracle.COLL_TRT else "bgk", trt_lambda=cfg.trt_lambda)
 
 
 def oracle_force_as_f32(cfg: "oracle.Config") -> "oracle.Config":

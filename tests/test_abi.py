@@ -45,6 +45,7 @@ def test_default_config_valid(cuda_lib):
 @pytest.mark.parametrize("field,value", [
     ("nx", 0), ("ny", -3), ("nz", 70000), ("tau", 0.5), ("tau", float("nan")), ("rho_wall", 0.0),
     ("storage", 9), ("variant", 4), ("force_mode", 5), ("tile_x", 16), ("tile_y", 5),
+    ("collision", 2), ("trt_lambda", 0.0), ("trt_lambda", float("inf")),
 ])
 def test_invalid_configs_rejected(cuda_lib, field, value):
     cfg = lbm.lbm_config_default()
@@ -78,6 +79,14 @@ def test_required_bytes_scale(cuda_lib):
     assert pop // 2 <= lbm.lbm_required_bytes(h16) < pop
 
 
+def test_trt_only_on_aa_and_two_lattice(cuda_lib):
+    for variant, want in (("aa", lbm.LBM_OK), ("two_lattice", lbm.LBM_OK), ("merged", lbm.LBM_EUNSUPPORTED),
+                          ("wavefront", lbm.LBM_EUNSUPPORTED)):
+        cfg = lbm.make_config((16, 16, 16), 0.7, lbm.CAVITY_BC, storage="f32", variant=variant, collision="trt")
+        assert lbm.lbm_validate(cfg) == want, variant
+    assert lbm.lbm_config_default().collision == lbm.LBM_COLLISION_BGK
+
+
 def test_strerror(cuda_lib):
     assert lbm.lbm_strerror(0) == "success"
     assert "non-finite" in lbm.lbm_strerror(lbm.LBM_ENONFINITE)
@@ -87,10 +96,11 @@ def test_strerror(cuda_lib):
 def test_config_struct_layout_matches_header(cuda_lib):
     """The ctypes mirror of lbm_config has the C layout (checked through a
     round trip: lbm_config_default writes every field)."""
-    assert ctypes.sizeof(lbm.lbm_config) == 136
+    assert ctypes.sizeof(lbm.lbm_config) == 152
     cfg = lbm.lbm_config_default()
     assert cfg.tau == 0.6 and cfg.rho_wall == 1.0 and list(cfg.face_bc) == [0] * 6
     assert cfg.storage == lbm.LBM_STORAGE_F32 and cfg.variant == lbm.LBM_VARIANT_AA
+    assert cfg.collision == lbm.LBM_COLLISION_BGK and cfg.trt_lambda == 3.0 / 16.0
 
 
 def test_create_without_gpu_fails_cleanly(cuda_lib):
