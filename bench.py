@@ -5,8 +5,8 @@ Workload (the benchmark configuration): lid-driven cavity 256^3, D3Q19 BGK,
 tau = 0.55, lid u = (0.05, 0, 0) on the z+ face, half-way bounce-back on the
 other five faces, fluid at rest at t = 0; FP32 storage and arithmetic; the
 two-step merged sweep by default (on this lattice the neighbour-synchronised
-kernel; --variant selects the single-copy AA pair, the plane wavefront or two
-lattices; the other schedules and storage formats are reported under
+kernel; --variant selects the single-copy AA pair or two lattices; the
+other schedules and storage formats are reported under
 "variants", the shadow-shell merged sweep as merged_shadow).  One benchmark step = two lattice
 time steps over all 16.8 M cells (one merged sweep, or an AA even/odd pair).
 MLUPS counts every cell as a fluid node (million lattice-node updates per
@@ -71,8 +71,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--size", type=int, default=256)
     p.add_argument("--storage", default="f32", choices=sorted(ELEM))
-    p.add_argument("--variant", default="merged", choices=["merged", "wavefront", "aa", "two_lattice"])
-    p.add_argument("--tile-y", type=int, default=0)
+    p.add_argument("--variant", default="merged", choices=["merged", "aa", "two_lattice"])
     p.add_argument("--no-extras", action="store_true", help="skip the per-variant, adjoint and CPU legs")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle baseline")
     p.add_argument("--sweep", action="store_true", help="cavity size sweep (prints its own JSON line)")
@@ -207,10 +206,10 @@ def sync_all(dist_on):
 
 # ------------------------------------------------------------------ GPU legs
 
-def make_cavity(n, storage, variant, tile_y=0, collision="bgk"):
+def make_cavity(n, storage, variant, collision="bgk"):
     from paper_2208_05429_gb300.lbm import CAVITY_BC, Lattice
     return Lattice((n, n, n), TAU, bc=CAVITY_BC, u_lid=U_LID, storage=storage, variant=variant,
-                   tile=(32 if tile_y else 0, tile_y), collision=collision)
+                   collision=collision)
 
 
 def alg_bytes_per_launch(kernel: str, storage: str, cells: int) -> float:
@@ -219,7 +218,7 @@ def alg_bytes_per_launch(kernel: str, storage: str, cells: int) -> float:
     return 2.0 * Q * ELEM[storage] * cells
 
 
-def time_variant(n, storage, variant, steps, warmup, dist_on=False, tile_y=0, sweep_env=None, collision="bgk"):
+def time_variant(n, storage, variant, steps, warmup, dist_on=False, sweep_env=None, collision="bgk"):
     """(elapsed ms over `steps` calls of step(2), per-kernel records, lattice).
     sweep_env: value of LBM_MERGED_SWEEP while the lattice is created (None:
     the library's own choice)."""
@@ -228,7 +227,7 @@ def time_variant(n, storage, variant, steps, warmup, dist_on=False, tile_y=0, sw
     if sweep_env is not None:
         os.environ["LBM_MERGED_SWEEP"] = sweep_env
     try:
-        lat = make_cavity(n, storage, variant, tile_y, collision)
+        lat = make_cavity(n, storage, variant, collision)
     finally:
         if sweep_env is not None:
             if old is None:
@@ -573,7 +572,7 @@ def main():
 
     sampler = ClockSampler(local)
     sampler.start()
-    ms, prof, lat = time_variant(n, args.storage, args.variant, args.steps, args.warmup, dist_on, args.tile_y)
+    ms, prof, lat = time_variant(n, args.storage, args.variant, args.steps, args.warmup, dist_on)
     clocks = sampler.stop()
     ms = slowest_rank_ms(ms, dist_on, "cuda")
     # mass check of the timed state: a broken kernel shows up here
@@ -582,7 +581,7 @@ def main():
     del lat
 
     value = whole_job_mlups(world, cells, args.steps, ms)
-    dominant = {"merged": "merged", "wavefront": "wavefront", "aa": "aa_odd"}.get(args.variant, "two_lattice")
+    dominant = {"merged": "merged", "aa": "aa_odd"}.get(args.variant, "two_lattice")
     roof = roofline_of(prof, dominant, args.storage, cells, peak, peak_kind)
     launches = sum(v[0] for v in prof.values())
     if "snapshot" in prof and roof is not None:
@@ -611,9 +610,9 @@ def main():
             line["e2e"] = {"error": repr(e)}
         variants = {}
         for st, var, env in (("f32", "merged", None), ("f32", "aa", None), ("f32", "two_lattice", None),
-                             ("f32", "wavefront", None), ("f32", "merged", "shadow"), ("f32s", "merged", None),
+                             ("f32", "merged", "shadow"), ("f32s", "merged", None),
                              ("f16s", "merged", None), ("f16s", "aa", None), ("bf16s", "merged", None),
-                             ("bf16s", "aa", None), ("f64", "wavefront", None), ("f32", "aa", "trt"),
+                             ("bf16s", "aa", None), ("f64", "aa", None), ("f32", "aa", "trt"),
                              ("f16s", "aa", "trt")):
             if (st, var, env) == (args.storage, args.variant, None):
                 continue
@@ -622,7 +621,7 @@ def main():
             vms, vprof, vl = time_variant(n, st, var, k, 5, sweep_env=None if env == "trt" else env,
                                           collision=coll)
             del vl
-            dk = {"merged": "merged", "wavefront": "wavefront", "aa": "aa_odd"}.get(var, "two_lattice")
+            dk = {"merged": "merged", "aa": "aa_odd"}.get(var, "two_lattice")
             r = roofline_of(vprof, dk, st, cells, peak, peak_kind)
             name = f"{var}_{env}_{st}" if env else f"{var}_{st}"
             variants[name] = {"MLUPS": round(cells * 2 * k / (vms * 1e3), 1),

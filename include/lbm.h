@@ -96,22 +96,10 @@ enum { LBM_STORAGE_F64 = 0, LBM_STORAGE_F32 = 1, LBM_STORAGE_F32S = 2,
  *                  count at handle creation).
  *                LBM_MERGED_SWEEP=shadow at handle creation selects the
  *                shadow-shell sweep, =neighbour the neighbour-synchronised
- *                one for any tile count it can hold resident.  With an
- *                explicit tile_y (or a periodic z with nz = 1) an older form
- *                runs instead: a pre-pass snapshots the tile shells every
- *                sweep.
- *   WAVEFRONT    single copy, two time steps per DRAM round trip through the
- *                L2 cache (the cache reuse of Sec. 4.1 and 5.2): one
- *                persistent kernel runs the even step of plane p+L+1 and the
- *                odd step of plane p as ordered work items; the few planes in
- *                flight stay in L2 between their two steps.  The lead L
- *                (default 3 planes, 5 with F16S and BF16S storage) can be
- *                set at handle creation with the
- *                environment variable LBM_WAVEFRONT_AHEAD (1..64), the
- *                cells per work item (default 2048, whole rows) with
- *                LBM_WAVEFRONT_ITEM_CELLS and the resident CTAs per SM
- *                (default: as many as fit) with LBM_WAVEFRONT_CTAS_PER_SM. */
-enum { LBM_VARIANT_TWO_LATTICE = 0, LBM_VARIANT_AA = 1, LBM_VARIANT_MERGED = 2, LBM_VARIANT_WAVEFRONT = 3 };
+ *                one for any tile count it can hold resident.  Where
+ *                neither sweep can run (a periodic z with nz = 1, or a
+ *                shadow beyond 2^31 elements) MERGED runs the AA pair. */
+enum { LBM_VARIANT_TWO_LATTICE = 0, LBM_VARIANT_AA = 1, LBM_VARIANT_MERGED = 2 };
 
 /* Body force (Guo forcing): none, one vector for every cell, or a per-cell
  * FP32 field [3][z][y][x] set with lbm_set_force(). */
@@ -139,8 +127,6 @@ typedef struct lbm_config {
     int32_t variant;          /* LBM_VARIANT_*                                 */
     int32_t force_mode;       /* LBM_FORCE_*                                   */
     double force_uniform[3];  /* the force of LBM_FORCE_UNIFORM                */
-    int32_t tile_x, tile_y;   /* MERGED: 0 = shadow-shell sweep (32 x 14 tiles),
-                                 else the snapshot sweep with 32 x tile_y tiles */
     int32_t collision;        /* LBM_COLLISION_* (default BGK)                  */
     double trt_lambda;        /* TRT magic product, > 0 (default 3/16)          */
 } lbm_config;
@@ -152,17 +138,15 @@ void lbm_config_default(lbm_config *cfg);
 /* Check a configuration without allocating.  LBM_EINVAL on: a dimension < 1,
  * cell count beyond 2^31, tau <= 0.5, a face type out of range, an axis with
  * one periodic and one non-periodic face, |u_lid| >= 0.3, rho_wall <= 0,
- * unknown storage/variant/force mode, a tile_x other than 0 or 32, or a
- * tile_y other than 0, 4, 8, 16 or too large for the shared memory of the
- * merged kernel in this storage format (F64 allows 4 only), an unknown
- * collision or a trt_lambda that is not positive and finite.
+ * unknown storage/variant/force mode or collision, or a trt_lambda that is
+ * not positive and finite.
  * LBM_EUNSUPPORTED for the TRT collision with a schedule other than AA and
  * TWO_LATTICE. */
 int lbm_validate(const lbm_config *cfg);
 
 /* Device bytes a handle of this configuration uses (populations, second
  * lattice for TWO_LATTICE, tile-shell shadow or progress words for MERGED,
- * work schedule for WAVEFRONT, reduction scratch), each region aligned to
+ * reduction scratch), each region aligned to
  * 256 bytes.
  * *bytes is a host output.  For MERGED the figure depends on the current
  * device (its SM count and the resident CTAs choose the sweep and the z
@@ -209,7 +193,7 @@ int lbm_init_equilibrium(lbm_handle *h, const void *rho, const void *u, int32_t 
 int lbm_set_force(lbm_handle *h, const float *F);
 
 /* Advance n >= 0 time steps (one step = collide then stream, Sec. 3).  With
- * MERGED and WAVEFRONT, pairs of steps run as one two-step sweep (Sec. 4) and
+ * MERGED, pairs of steps run as one two-step sweep (Sec. 4) and
  * an odd remainder as one AA step.  Asynchronous on the handle's stream.
  * Calls with n >= 32 (outside profiling) capture the launches of 32 steps
  * once into a CUDA graph and replay it, on an internal stream ordered after
@@ -241,8 +225,8 @@ int lbm_init_populations(lbm_handle *h, const void *f_in, int32_t dtype);
  * LBM_ENONFINITE if any cell has a non-finite density or velocity; out is
  * still written.  LBM_ETIMEOUT if, since the previous call, a MERGED sweep
  * gave up waiting for one of its asynchronous plane copies or for a
- * neighbouring tile's progress word, or a WAVEFRONT sweep for one of its
- * work items (every wait in the kernels is bounded); the lattice is then
+ * neighbouring tile's progress word (every wait in the kernels is
+ * bounded); the lattice is then
  * invalid and the flag is cleared. */
 int lbm_reduce(lbm_handle *h, double *out);
 
@@ -257,7 +241,7 @@ int lbm_reduce(lbm_handle *h, double *out);
  *   cfg    lattice sizes and body force (force_mode, force_uniform); the
  *          whole config must pass lbm_validate(), so lattices beyond
  *          2^31 - 1 cells are rejected with LBM_EINVAL; storage, variant
- *          and tiles are ignored
+ *          and collision are ignored
  *   f      device, canonical natural-parity populations f[19][z][y][x] of
  *          element type `dtype` (LBM_DTYPE_F32 or _F64), directions as
  *          lbm_lattice() -- what lbm_populations() writes
@@ -284,7 +268,10 @@ int lbm_reduce_populations(const lbm_config *cfg, const void *f, int32_t dtype, 
 /* ---------------- per-kernel timing ----------------
  * Kernel classes launched by lbm_step(). */
 enum { LBM_KERNEL_TWO_LATTICE = 0, LBM_KERNEL_AA_EVEN = 1, LBM_KERNEL_AA_ODD = 2,
-       LBM_KERNEL_SNAPSHOT = 3, LBM_KERNEL_MERGED = 4, LBM_KERNEL_WAVEFRONT = 5, LBM_KERNEL_COUNT = 6 };
+       LBM_KERNEL_SNAPSHOT = 3, LBM_KERNEL_MERGED = 4, LBM_KERNEL_COUNT = 5 };
+/* LBM_KERNEL_SNAPSHOT: the shadow-shell sweep's copies made before a sweep
+ * (the tile shells after a single step, the planes at z-chunk boundaries);
+ * LBM_KERNEL_MERGED: either two-step sweep. */
 
 /* enable = 1: from now on every kernel lbm_step() launches is bracketed by
  * two CUDA events recorded on the handle's stream (earlier records are
@@ -297,13 +284,18 @@ int lbm_profile(lbm_handle *h, int32_t enable);
  * outputs.  Synchronises on the recorded events. */
 int lbm_profile_read(lbm_handle *h, int32_t kernel, int64_t *launches, double *total_ms);
 
-/* Self-test of the failure detection of a WAVEFRONT handle: runs one sweep
- * in which only the odd-step items are scheduled, so that every bounded
- * inter-CTA wait runs out (about a second) and gives up without touching
- * the lattice; the state and the step count stay unchanged.  Returns
- * LBM_ETIMEOUT when the give-up was recorded in the status word (which is
- * cleared again), LBM_OK if nothing was recorded, LBM_ESTATE for another
- * schedule.  Synchronises the stream. */
+/* Self-test of the failure detection of a MERGED handle that runs the
+ * neighbour-synchronised sweep: runs one sweep in which the tile in the
+ * middle of the grid never announces its progress, so that its neighbours'
+ * bounded waits for it run out (a second or two), they give up, and so does
+ * every tile that waits for them.  No kernel faults, traps or spins without
+ * a limit.  The populations are left undefined (partly stepped): re-create
+ * the state with lbm_init_equilibrium() or lbm_init_populations() before
+ * stepping again; the step count is unchanged.  Returns LBM_ETIMEOUT when
+ * the give-up was recorded in the status word (which is cleared again),
+ * LBM_OK if nothing was recorded, LBM_ESTATE for a handle without that
+ * sweep, at odd parity (after an odd number of steps) or with a force
+ * field not yet set.  Synchronises the stream. */
 int lbm_selftest_wait_timeout(lbm_handle *h);
 
 /* ---------------- adjoint (reverse-mode) ----------------

@@ -667,7 +667,8 @@ static __global__ void __launch_bounds__(RED_THREADS) k_reduce_final(const doubl
 }
 
 // ---------------------------------------------------------------------------
-// K4: two steps per sweep.  See merged.cuh.
+// K4: two steps per sweep: nsweep.cuh (neighbour-synchronised) and
+// merged3.cuh (shadow-shell).
 // ---------------------------------------------------------------------------
 
 // ---------------------------------------------------------------------------

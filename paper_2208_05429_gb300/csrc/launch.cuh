@@ -3,10 +3,8 @@
 #pragma once
 
 #include "kernels.cuh"
-#include "merged.cuh"
 #include "merged3.cuh"
 #include "nsweep.cuh"
-#include "wavefront.cuh"
 
 #include <string.h>
 
@@ -150,71 +148,6 @@ struct Launch {
         k_reduce_final<<<1, RED_THREADS, 0, st>>>(partial, nblocks, out);
         return cudaGetLastError();
     }
-    static cudaError_t snapshot(const HostGeom &h, int64_t pitch, bool force, const void *f, void *G,
-                                const TileInfo &ti, cudaStream_t st)
-    {
-        const int64_t cz_ = ti.zshell ? 2LL * h.ny * h.nx : 0;
-        const int64_t cy_ = ti.yshell ? (int64_t)h.nz * 2 * ti.nty * h.nx : 0;
-        const int64_t cx_ = ti.xshell ? (int64_t)h.nz * 2 * ti.ntx * h.ny : 0;
-        const int64_t tot = cz_ + cy_ + cx_;
-        if (tot == 0) return cudaSuccess;
-        const unsigned blocks = (unsigned)((tot + 255) / 256);
-        const Geom<R> g = make_geom<R>(h, pitch);
-        if (force) k_snapshot<S, true><<<blocks, 256, 0, st>>>(g, (const T *)f, (R *)G, ti, cz_, cy_, cx_);
-        else k_snapshot<S, false><<<blocks, 256, 0, st>>>(g, (const T *)f, (R *)G, ti, cz_, cy_, cx_);
-        return cudaGetLastError();
-    }
-
-    template <int TY>
-    static constexpr size_t smem_of() { return MergedSmem<32, TY, T, R>::bytes; }
-    static size_t merged_smem(int ty)
-    {
-        constexpr size_t LIMIT = 232448;  // opt-in shared memory per block
-        size_t b = 0;
-        if (ty == 4) b = smem_of<4>();
-        else if (ty == 8) b = smem_of<8>();
-        else if (ty == 16) b = smem_of<16>();
-        return b <= LIMIT ? b : 0;
-    }
-
-    template <int TX, int TY>
-    static cudaError_t merged_t(const HostGeom &h, int64_t pitch, bool force, void *f, const void *G,
-                                const TileInfo &ti, const void *tmap, int *status, cudaStream_t st)
-    {
-        const size_t smem = MergedSmem<TX, TY, T, R>::bytes;
-        const dim3 grid(ti.ntx, ti.nty), block(TX, TY);
-        const Geom<R> g = make_geom<R>(h, pitch);
-        const Dirs<T> fd = make_dirs((T *)f, slot_of(h, pitch));
-        CUtensorMap map;
-        memcpy(&map, tmap, sizeof(map));
-        static bool attr_set[2] = {false, false};  // once per process: not inside a stream capture
-        if (!attr_set[force]) {
-            const cudaError_t e = cudaFuncSetAttribute(force ? k_merged<S, true, TX, TY> : k_merged<S, false, TX, TY>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            attr_set[force] = true;
-        }
-        if (force) k_merged<S, true, TX, TY><<<grid, block, smem, st>>>(map, g, fd, (const R *)G, ti, status);
-        else k_merged<S, false, TX, TY><<<grid, block, smem, st>>>(map, g, fd, (const R *)G, ti, status);
-        return cudaGetLastError();
-    }
-    static cudaError_t merged(const HostGeom &h, int64_t pitch, bool force, void *f, const void *G,
-                              const TileInfo &ti, const void *tmap, int *status, cudaStream_t st)
-    {
-        if (ti.TX != 32 || merged_smem(ti.TY) == 0) return cudaErrorInvalidValue;
-        switch (ti.TY) {
-        case 4: return merged_t<32, 4>(h, pitch, force, f, G, ti, tmap, status, st);
-        case 8:
-            if constexpr (MergedSmem<32, 8, T, R>::bytes <= 232448)
-                return merged_t<32, 8>(h, pitch, force, f, G, ti, tmap, status, st);
-            else return cudaErrorInvalidValue;
-        case 16:
-            if constexpr (MergedSmem<32, 16, T, R>::bytes <= 232448)
-                return merged_t<32, 16>(h, pitch, force, f, G, ti, tmap, status, st);
-            else return cudaErrorInvalidValue;
-        default: return cudaErrorInvalidValue;
-        }
-    }
     // band height of the shadow-shell sweep: 32 x 14 tiles (one per SM on a
     // 256^2 plane) for 4-byte and 2-byte storage, 32 x 4 for FP64 (shared
     // memory)
@@ -346,30 +279,6 @@ struct Launch {
             return n;
         }
     }
-    static cudaError_t wavefront(const HostGeom &h, int64_t pitch, bool force, void *f, const void *sched, int grid,
-                                 cudaStream_t st)
-    {
-        const Geom<R> g = make_geom<R>(h, pitch);
-        const Dirs<T> d = make_dirs((T *)f, slot_of(h, pitch));
-        WaveSchedule ws;
-        memcpy(&ws, sched, sizeof(ws));
-        Dirs<T> din, dout;  // odd-step gather and push addresses of an interior cell
-        for (int i = 0; i < Q; ++i) {
-            din.p[i] = d.p[opp(i)] - g.noff[i];
-            dout.p[i] = d.p[i] + g.noff[i];
-        }
-        if (force) k_wavefront<S, true><<<grid, WF_THREADS, 0, st>>>(g, d, din, dout, ws);
-        else k_wavefront<S, false><<<grid, WF_THREADS, 0, st>>>(g, d, din, dout, ws);
-        return cudaGetLastError();
-    }
-    static int wavefront_blocks_per_sm(bool force)
-    {
-        int n = 0;
-        const cudaError_t e = force
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_wavefront<S, true>, WF_THREADS, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_wavefront<S, false>, WF_THREADS, 0);
-        return e == cudaSuccess ? n : 0;
-    }
     static cudaError_t adjoint(const HostGeom &h, int64_t pitch, bool force, const void *f, const void *lam_in,
                                void *lam_out, double *gF, cudaStream_t st)
     {
@@ -412,15 +321,11 @@ StorageOps make_ops()
     StorageOps o;
     o.elem_size = sizeof(typename S::T);
     o.real_size = sizeof(typename S::R);
-    o.max_tile_y = L::merged_smem(16) ? 16 : (L::merged_smem(8) ? 8 : 4);
-    o.merged_smem = &L::merged_smem;
-    o.wavefront = &L::wavefront;
     o.nsweep = L::HAS_NS ? &L::nsweep : nullptr;
     o.nsweep_ctas_per_sm = &L::nsweep_ctas_per_sm;
     o.ns_ty = L::NS_TY;
     o.ns_box_w = 32 + 2 * (16 / (int)sizeof(typename S::T));
     o.ns_margin = 16 / (int)sizeof(typename S::T);
-    o.wavefront_blocks_per_sm = &L::wavefront_blocks_per_sm;
     o.init_eq = &L::init_eq;
     o.two_lattice = &L::two_lattice;
     o.aa_even = &L::aa_even;
@@ -432,8 +337,6 @@ StorageOps make_ops()
     o.import_pop = &L::import_pop;
     o.raw_natural = &L::raw_natural;
     o.reduce = &L::reduce;
-    o.snapshot = &L::snapshot;
-    o.merged = &L::merged;
     o.m3_ty = L::M3_TY;
     o.m3_nsp = M3<L::M3_TY>::NSP;
     o.m3_zsave = M3<L::M3_TY>::ZSAVE;

@@ -13,7 +13,6 @@
 #include "d3q19.cuh"
 #include "lbm.h"
 #include "ops.h"
-#include "wavefront.cuh"
 
 using namespace lbm;
 
@@ -30,8 +29,6 @@ struct lbm_handle {
     size_t bytes;
     void *f;       // populations
     void *f2;      // second lattice (TWO_LATTICE)
-    void *G;       // shell snapshot (MERGED with explicit tile or periodic z)
-    TileInfo ti;
     bool m3;           // MERGED runs the shadow-shell sweep
     ShellInfo si;
     void *G3[2];       // shadow of the tile shells: current / next
@@ -60,9 +57,7 @@ struct lbm_handle {
     bool ns;           // MERGED runs the neighbour-synchronised sweep
     int *prog;         // its progress words, one per tile
     CUtensorMap tmapns;  // its copy box: tile + halo, all 19 directions
-    int *status;       // device status word: bits 2 / 4 = a bounded wait gave up
-    int *wf_words;     // WAVEFRONT schedule (device): entries, ticket, done flags
-    int wf_nentries, wf_rb, wf_nrb, wf_grid, wf_ahead;
+    int *status;       // device status word: a bit per sweep whose bounded wait gave up
     double *partial;
     double *red_out;
     int *flag;
@@ -129,35 +124,12 @@ size_t elem_size_of(int storage)
 }
 size_t real_size_of(int storage) { return storage == LBM_STORAGE_F64 ? 8 : 4; }
 
-int default_tile_y(const lbm_config &c) { return ops_for(c.storage)->max_tile_y; }
-
-TileInfo tile_info(const lbm_config &c)
-{
-    TileInfo ti;
-    memset(&ti, 0, sizeof(ti));
-    ti.TX = c.tile_x > 0 ? c.tile_x : 32;
-    ti.TY = c.tile_y > 0 ? c.tile_y : default_tile_y(c);
-    ti.ntx = (int)((c.nx + ti.TX - 1) / ti.TX);
-    ti.nty = (int)((c.ny + ti.TY - 1) / ti.TY);
-    ti.xshell = ti.ntx > 1;
-    ti.yshell = ti.nty > 1;
-    ti.zshell = c.face_bc[4] == LBM_BC_PERIODIC;
-    ti.gy_slot = ti.yshell ? (int64_t)c.nz * 2 * ti.nty * c.nx : 0;
-    ti.gx_slot = ti.xshell ? (int64_t)c.nz * 2 * ti.ntx * c.ny : 0;
-    ti.gz_slot = ti.zshell ? 2LL * c.ny * c.nx : 0;
-    ti.gy_off = 0;
-    ti.gx_off = (int64_t)Q * ti.gy_slot;
-    ti.gz_off = (int64_t)Q * (ti.gy_slot + ti.gx_slot);
-    return ti;
-}
-
-// The shadow-shell sweep serves MERGED with automatic tiles (and at least
-// two planes when z is periodic); an explicit tile height selects the
-// snapshot sweep (merged.cuh).
+// The shadow-shell sweep serves MERGED where the neighbour-synchronised
+// one cannot run (and z has at least two planes when it is periodic); where
+// neither can, MERGED runs the AA pair.
 int sm_count();
 
-// The neighbour-synchronised sweep serves MERGED with automatic tiles when
-// every face is a wall or lid, the format has the sweep, all tiles can be
+// The neighbour-synchronised sweep serves MERGED when every face is a wall or lid, the format has the sweep, all tiles can be
 // resident at once and they are at least half as many as the SMs (fewer
 // tiles leave SMs idle; the shadow-shell sweep splits z for them).  The
 // environment variable LBM_MERGED_SWEEP=shadow selects the shadow-shell
@@ -165,7 +137,7 @@ int sm_count();
 // (any tile count up to the resident limit).
 bool uses_ns(const lbm_config &c, const ShellInfo &si)
 {
-    if (c.variant != LBM_VARIANT_MERGED || c.tile_y != 0) return false;
+    if (c.variant != LBM_VARIANT_MERGED) return false;
     bool any_count = false;
     if (const char *e = getenv("LBM_MERGED_SWEEP")) {
         if (strcmp(e, "shadow") == 0) return false;
@@ -183,7 +155,7 @@ bool uses_ns(const lbm_config &c, const ShellInfo &si)
 // si: the tiles of c (shell_info), computed once per query or creation.
 bool uses_m3(const lbm_config &c, const ShellInfo &si)
 {
-    if (c.variant != LBM_VARIANT_MERGED || c.tile_y != 0) return false;
+    if (c.variant != LBM_VARIANT_MERGED) return false;
     if (uses_ns(c, si)) return false;
     if (c.face_bc[4] == LBM_BC_PERIODIC && c.nz < 2) return false;
     // the sweep indexes one shadow copy with 32-bit offsets
@@ -218,6 +190,7 @@ ShellInfo shell_info(const lbm_config &c)
     // than its own (the march prologue and the even steps of the planes
     // next to it); kept at 1 unless that saves 5% or more
     si.nzc = 1;
+    si.mute = -1;
     if (c.face_bc[4] != LBM_BC_PERIODIC) {
         const int64_t tiles = (int64_t)si.ntx * si.nty, sms = sm_count();
         auto cost = [&](int64_t n) {
@@ -248,54 +221,9 @@ int64_t zcopy_elems(const lbm_config &c, const ShellInfo &si)
     return si.nzc > 1 ? (int64_t)Q * 2 * (si.nzc - 1) * c.ny * pitch_of(c) : 0;
 }
 
-int64_t ghost_elems(const lbm_config &c, const ShellInfo &si)
-{
-    if (c.variant != LBM_VARIANT_MERGED || uses_m3(c, si)) return 0;
-    const TileInfo ti = tile_info(c);
-    return (int64_t)Q * (ti.gy_slot + ti.gx_slot + ti.gz_slot);
-}
-
 struct Layout {
-    size_t f, f2, G, G3, Z3, ZC, prog, wf, partial, red_out, flag, status, total;
+    size_t f, f2, G3, Z3, ZC, prog, partial, red_out, flag, status, total;
 };
-
-// WAVEFRONT schedule words: entries (2 nz + 4), ticket, done[nz * ny] (at
-// most ny row blocks per plane).
-// Planes by which even steps lead odd steps: 3, or 5 for the 2-byte storage
-// formats (best of 2, 3 and 5 on the 256^3 cavity).
-inline int wf_ahead_default(int storage)
-{
-    return storage == LBM_STORAGE_F16S || storage == LBM_STORAGE_BF16S ? 5 : 3;
-}
-
-int64_t wf_ints(const lbm_config &c)
-{
-    return c.variant == LBM_VARIANT_WAVEFRONT ? 2 * c.nz + 4 + 1 + c.nz * c.ny : 0;
-}
-
-// Order of the even (2p) and odd (2p+1) steps of the planes for a lookahead
-// of `ahead` planes.
-int wf_entries(const lbm_config &c, int ahead, int *out)
-{
-    const int nz = (int)c.nz;
-    int n = 0;
-    bool *issued = new (std::nothrow) bool[nz]();
-    if (!issued) return -1;
-    auto even = [&](int p) {
-        if (p >= 0 && p < nz && !issued[p]) {
-            issued[p] = true;
-            out[n++] = 2 * p;
-        }
-    };
-    if (c.face_bc[4] == LBM_BC_PERIODIC) even(nz - 1);
-    for (int p = 0; p <= ahead; ++p) even(p);
-    for (int q = 0; q < nz; ++q) {
-        even(q + ahead + 1);
-        out[n++] = 2 * q + 1;
-    }
-    delete[] issued;
-    return n;
-}
 
 Layout layout_of(const lbm_config &c, const ShellInfo &si)
 {
@@ -305,7 +233,6 @@ Layout layout_of(const lbm_config &c, const ShellInfo &si)
     size_t off = 0;
     L.f = off; off += pop;
     L.f2 = off; if (c.variant == LBM_VARIANT_TWO_LATTICE) off += pop;
-    L.G = off; off += align_up((size_t)ghost_elems(c, si) * real_size_of(c.storage));
     L.G3 = off;
     if (uses_m3(c, si)) off += 2 * align_up((size_t)(si.gplane * c.nz) * es);
     L.Z3 = off;
@@ -315,7 +242,6 @@ Layout layout_of(const lbm_config &c, const ShellInfo &si)
     L.ZC = off; off += align_up((size_t)zcopy_elems(c, si) * es);
     L.prog = off;
     if (uses_ns(c, si)) off += align_up(sizeof(int) * NS_PROG_INTS * (size_t)si.ntx * si.nty);
-    L.wf = off; off += align_up((size_t)wf_ints(c) * sizeof(int));
     L.partial = off; off += align_up(sizeof(double) * 5 * RED_BLOCKS_MAX);
     L.red_out = off; off += align_up(sizeof(double) * 5);
     L.flag = off; off += align_up(sizeof(int));
@@ -474,14 +400,11 @@ int lbm_validate(const lbm_config *c)
     if (!(ul < 0.3)) return LBM_EINVAL;
     if (!(c->rho_wall > 0.0) || !isfinite(c->rho_wall)) return LBM_EINVAL;
     if (c->storage < LBM_STORAGE_F64 || c->storage > LBM_STORAGE_BF16S) return LBM_EINVAL;
-    if (c->variant < LBM_VARIANT_TWO_LATTICE || c->variant > LBM_VARIANT_WAVEFRONT) return LBM_EINVAL;
+    if (c->variant < LBM_VARIANT_TWO_LATTICE || c->variant > LBM_VARIANT_MERGED) return LBM_EINVAL;
     if ((double)((c->nx + 15) / 16 * 16) * (double)c->ny * (double)c->nz > 2147483647.0) return LBM_EINVAL;
     if (c->force_mode < LBM_FORCE_NONE || c->force_mode > LBM_FORCE_FIELD) return LBM_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (!isfinite(c->force_uniform[a])) return LBM_EINVAL;
-    if (c->tile_x != 0 && c->tile_x != 32) return LBM_EINVAL;
-    if (c->tile_y != 0 && c->tile_y != 4 && c->tile_y != 8 && c->tile_y != 16) return LBM_EINVAL;
-    if (c->tile_y != 0 && ops_for(c->storage)->merged_smem(c->tile_y) == 0) return LBM_EINVAL;
     if (c->collision != LBM_COLLISION_BGK && c->collision != LBM_COLLISION_TRT) return LBM_EINVAL;
     if (!(c->trt_lambda > 0.0) || !isfinite(c->trt_lambda)) return LBM_EINVAL;
     if (c->collision == LBM_COLLISION_TRT && c->variant != LBM_VARIANT_AA &&
@@ -496,44 +419,6 @@ int lbm_required_bytes(const lbm_config *cfg, size_t *bytes)
     if (v != LBM_OK) return v;
     if (!bytes) return LBM_EINVAL;
     *bytes = layout_of(*cfg, shell_info(*cfg)).total;
-    return LBM_OK;
-}
-
-// Schedule of the WAVEFRONT sweep: entry order for the lookahead, row blocks
-// of about 4096 cells, one CTA per resident slot on the device.
-static int wf_setup(lbm_handle *h, int ahead)
-{
-    const lbm_config &c = h->cfg;
-    int *ent = new (std::nothrow) int[2 * c.nz + 4];
-    if (!ent) return LBM_ENOMEM;
-    const int n = wf_entries(c, ahead, ent);
-    if (n < 0) { delete[] ent; return LBM_ENOMEM; }
-    const cudaError_t e = cudaMemcpyAsync(h->wf_words, ent, sizeof(int) * n, cudaMemcpyHostToDevice, h->stream);
-    const cudaError_t e2 = cudaStreamSynchronize(h->stream);
-    delete[] ent;
-    if (e != cudaSuccess || e2 != cudaSuccess) return LBM_ECUDA;
-    h->wf_nentries = n;
-    h->wf_ahead = ahead;
-    int64_t item_cells = 2048;  // tunable through LBM_WAVEFRONT_ITEM_CELLS
-    if (const char *env = getenv("LBM_WAVEFRONT_ITEM_CELLS")) {
-        const long v = atol(env);
-        if (v >= 32 && v <= (1L << 22)) item_cells = v;
-    }
-    const int64_t want = item_cells / c.nx;
-    h->wf_rb = (int)(want < 1 ? 1 : (want > c.ny ? c.ny : want));
-    h->wf_nrb = (int)((c.ny + h->wf_rb - 1) / h->wf_rb);
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) return LBM_ECUDA;
-    int per = h->ops->wavefront_blocks_per_sm(h->force);
-    if (per <= 0) return LBM_ECUDA;
-    // CTAs per SM (resident items bound the planes in flight), tunable
-    // through LBM_WAVEFRONT_CTAS_PER_SM
-    if (const char *env = getenv("LBM_WAVEFRONT_CTAS_PER_SM")) {
-        const int v = atoi(env);
-        if (v >= 1 && v < per) per = v;
-    }
-    const int64_t items = (int64_t)n * h->wf_nrb;
-    h->wf_grid = (int)(items < (int64_t)sms * per ? items : (int64_t)sms * per);
     return LBM_OK;
 }
 
@@ -558,7 +443,6 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
     h->nxp = pitch_of(*cfg);
     h->force = cfg->force_mode != LBM_FORCE_NONE;
     h->force_set = cfg->force_mode != LBM_FORCE_FIELD;
-    h->ti = tile_info(*cfg);
     h->ev_pool = new (std::nothrow) std::vector<cudaEvent_t>();
     h->rec_kind = new (std::nothrow) std::vector<int>();
     if (!h->ev_pool || !h->rec_kind) {
@@ -585,7 +469,6 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
     char *b = (char *)buf;
     h->f = b + L.f;
     h->f2 = cfg->variant == LBM_VARIANT_TWO_LATTICE ? b + L.f2 : nullptr;
-    h->G = cfg->variant == LBM_VARIANT_MERGED ? b + L.G : nullptr;
     h->m3 = uses_m3(*cfg, si);
     h->ns = uses_ns(*cfg, si);
     if (h->ns) {
@@ -606,7 +489,6 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
     h->red_out = (double *)(b + L.red_out);
     h->flag = (int *)(b + L.flag);
     h->status = (int *)(b + L.status);
-    h->wf_words = cfg->variant == LBM_VARIANT_WAVEFRONT ? (int *)(b + L.wf) : nullptr;
     const int64_t n = cfg->nx * cfg->ny * cfg->nz;
     int64_t nb = (n + 255) / 256;
     h->red_blocks = (int)(nb < RED_BLOCKS_MAX ? nb : RED_BLOCKS_MAX);
@@ -615,7 +497,7 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
                           h->m3 ? make_tmap(*cfg, 32, h->ops->m3_ty, 1, h->f, &h->tmap) &&
                                       (!h->ZC || make_tmap(*cfg, 32, h->ops->m3_ty, 1, h->ZC, &h->tmapz,
                                                            2 * (int64_t)(h->si.nzc - 1)))
-                                : make_tmap(*cfg, h->ti.TX, h->ti.TY, Q, h->f, &h->tmap));
+                                : true);
     if (!tmap_ok ||
         cudaMemsetAsync(buf, 0, L.total, h->stream) != cudaSuccess) {
         if (own) cudaFreeAsync(buf, h->stream);
@@ -623,22 +505,6 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
         delete h->rec_kind;
         delete h;
         return LBM_ECUDA;
-    }
-    if (cfg->variant == LBM_VARIANT_WAVEFRONT) {
-        // lookahead (planes) of the even steps, tunable through LBM_WAVEFRONT_AHEAD
-        int ahead = wf_ahead_default(cfg->storage);
-        if (const char *env = getenv("LBM_WAVEFRONT_AHEAD")) {
-            const int v = atoi(env);
-            if (v >= 1 && v <= 64) ahead = v;
-        }
-        const int rc = wf_setup(h, ahead);
-        if (rc != LBM_OK) {
-            if (own) cudaFreeAsync(buf, h->stream);
-            delete h->ev_pool;
-            delete h->rec_kind;
-            delete h;
-            return rc;
-        }
     }
     *out = h;
     return LBM_OK;
@@ -745,33 +611,6 @@ static int step_units(lbm_handle *h, int64_t n)
             }
             n -= 1; h->t += 1;
             break;
-        case LBM_VARIANT_WAVEFRONT:
-            if (h->parity == PARITY_A) {
-                CK(timed(h, LBM_KERNEL_AA_ODD, [&] { return o.aa_odd(h->hg, h->nxp, h->force, h->f, h->stream); }));
-                h->parity = PARITY_NATURAL;
-                h->g3fresh = false;
-                n -= 1; h->t += 1;
-            } else if (n >= 2) {
-                WaveSchedule ws;
-                ws.entries = h->wf_words;
-                ws.nentries = h->wf_nentries;
-                ws.rb = h->wf_rb;
-                ws.nrb = h->wf_nrb;
-                ws.ticket = h->wf_words + 2 * h->cfg.nz + 4;
-                ws.done = ws.ticket + 1;
-                ws.status = h->status;
-                CK(cudaMemsetAsync(ws.ticket, 0, sizeof(int) * (1 + h->cfg.nz * h->wf_nrb), h->stream));
-                CK(timed(h, LBM_KERNEL_WAVEFRONT, [&] {
-                    return o.wavefront(h->hg, h->nxp, h->force, h->f, &ws, h->wf_grid, h->stream);
-                }));
-                n -= 2; h->t += 2;
-            } else {
-                CK(timed(h, LBM_KERNEL_AA_EVEN, [&] { return o.aa_even(h->hg, h->nxp, h->force, h->f, h->stream); }));
-                h->parity = PARITY_A;
-                h->g3fresh = false;
-                n -= 1; h->t += 1;
-            }
-            break;
         default:  // MERGED
             if (h->parity == PARITY_A) {
                 CK(timed(h, LBM_KERNEL_AA_ODD, [&] { return o.aa_odd(h->hg, h->nxp, h->force, h->f, h->stream); }));
@@ -800,12 +639,6 @@ static int step_units(lbm_handle *h, int64_t n)
                                      h->Z3, &h->tmap, &h->tmapz, h->status, h->stream);
                 }));
                 h->g3cur ^= 1;
-                n -= 2; h->t += 2;
-            } else if (n >= 2) {
-                CK(timed(h, LBM_KERNEL_SNAPSHOT, [&] { return o.snapshot(h->hg, h->nxp, h->force, h->f, h->G, h->ti, h->stream); }));
-                CK(timed(h, LBM_KERNEL_MERGED, [&] {
-                    return o.merged(h->hg, h->nxp, h->force, h->f, h->G, h->ti, &h->tmap, h->status, h->stream);
-                }));
                 n -= 2; h->t += 2;
             } else {
                 CK(timed(h, LBM_KERNEL_AA_EVEN, [&] { return o.aa_even(h->hg, h->nxp, h->force, h->f, h->stream); }));
@@ -972,35 +805,23 @@ int lbm_reduce(lbm_handle *h, double *out)
 int lbm_selftest_wait_timeout(lbm_handle *h)
 {
     if (!h) return LBM_EINVAL;
-    if (h->cfg.variant != LBM_VARIANT_WAVEFRONT) return LBM_ESTATE;
-    if (!h->force_set) return LBM_ESTATE;
+    if (!h->ns || h->parity != PARITY_NATURAL || !h->force_set) return LBM_ESTATE;
     DeviceGuard g(h->device);
     if (!g.ok) return LBM_ECUDA;
-    // a schedule of odd-step entries only: their completion flags never come
-    const int nz = (int)h->cfg.nz;
-    std::vector<int> odd((size_t)nz);
-    for (int p = 0; p < nz; ++p) odd[(size_t)p] = 2 * p + 1;
-    int *ent = nullptr;
-    CK(cudaMallocAsync((void **)&ent, sizeof(int) * (size_t)nz, h->stream));
-    WaveSchedule ws;
-    ws.entries = ent;
-    ws.nentries = nz;
-    ws.rb = h->wf_rb;
-    ws.nrb = h->wf_nrb;
-    ws.ticket = h->wf_words + 2 * h->cfg.nz + 4;
-    ws.done = ws.ticket + 1;
-    ws.status = h->status;
+    // one sweep in which the tile at the middle of the grid never publishes
+    // its progress: its neighbours' waits for it run out, they give up, and
+    // so does every tile waiting for them
+    ShellInfo si = h->si;
+    si.mute = (si.nty / 2) * si.ntx + si.ntx / 2;
     int st = 0;
-    const bool ok = cudaMemcpyAsync(ent, odd.data(), sizeof(int) * (size_t)nz, cudaMemcpyHostToDevice, h->stream) ==
-                        cudaSuccess &&
-                    cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) == cudaSuccess &&
-                    cudaMemsetAsync(ws.ticket, 0, sizeof(int) * (1 + h->cfg.nz * h->wf_nrb), h->stream) ==
-                        cudaSuccess &&
-                    h->ops->wavefront(h->hg, h->nxp, h->force, h->f, &ws, h->wf_grid, h->stream) == cudaSuccess &&
-                    cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream) == cudaSuccess &&
-                    cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) == cudaSuccess;
-    cudaFreeAsync(ent, h->stream);
+    const bool ok =
+        cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) == cudaSuccess &&
+        cudaMemsetAsync(h->prog, 0, sizeof(int) * NS_PROG_INTS * (size_t)si.ntx * si.nty, h->stream) == cudaSuccess &&
+        h->ops->nsweep(h->hg, h->nxp, h->force, h->f, si, h->prog, &h->tmapns, h->status, h->stream) == cudaSuccess &&
+        cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream) == cudaSuccess &&
+        cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) == cudaSuccess;
     if (!ok || cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
+    h->adj_ready = false;
     return st ? LBM_ETIMEOUT : LBM_OK;
 }
 

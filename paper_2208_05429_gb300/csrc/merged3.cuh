@@ -38,7 +38,7 @@
 // sizeof(T) x (1 + NS / (32 TY)) bytes per cell.
 #pragma once
 
-#include "merged.cuh"
+#include "tma.cuh"
 
 namespace lbm {
 

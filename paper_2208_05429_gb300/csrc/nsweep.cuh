@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
             if (lane == 0) {
                 const int before = pub;
                 while (pub < issued && landed(pub)) ++pub;
-                if (pub != before) ns_store_relaxed(prog + NS_PROG_INTS * tile, pub);
+                if (pub != before && tile != si.mute) ns_store_relaxed(prog + NS_PROG_INTS * tile, pub);
             }
             const int pw = __shfl_sync(0xffffffffu, pub, 0);
             if (!mine) mine = ns_load_relaxed(prog + NS_PROG_INTS * nb) >= need + 1;

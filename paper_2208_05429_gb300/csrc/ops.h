@@ -22,15 +22,6 @@ struct HostGeom {
     const float *Ff;
 };
 
-// Tile geometry of the merged sweep and the layout of its shell snapshot.
-struct TileInfo {
-    int TX, TY;
-    int ntx, nty;
-    int xshell, yshell, zshell;
-    int64_t gx_off, gy_off, gz_off;
-    int64_t gx_slot, gy_slot, gz_slot;
-};
-
 // Tiles of the shadow-shell merged sweep: 32 cells wide along x, bands of
 // near-equal height along y; its shadow G[z][tile][q][nsp] (tile = by * ntx
 // + bx) holds the stored populations of every tile-boundary cell.
@@ -39,6 +30,9 @@ struct ShellInfo {
     int hb, rem;       // band heights: hb + 1 for the first rem bands, else hb
     int64_t gplane;    // elements of one z-plane of G
     int nzc;           // z chunks marched by separate CTAs (1 with periodic z)
+    int mute;          // neighbour-synchronised sweep: a tile that never
+                       // publishes its progress (-1: none; the self-test of
+                       // the bounded waits sets it)
 };
 
 enum { PARITY_NATURAL = 0, PARITY_A = 1 };
@@ -48,7 +42,6 @@ enum { PARITY_NATURAL = 0, PARITY_A = 1 };
 struct StorageOps {
     size_t elem_size;  // bytes of a stored population
     size_t real_size;  // bytes of the compute type
-    int max_tile_y;    // largest merged tile height the shared memory allows
     cudaError_t (*init_eq)(const HostGeom &, int64_t pitch, void *f, const void *rho, const void *u, int dtype,
                            cudaStream_t);
     cudaError_t (*two_lattice)(const HostGeom &, int64_t pitch, bool force, const void *src, void *dst,
@@ -67,19 +60,14 @@ struct StorageOps {
     // partial: 5 * nblocks doubles; out: 5 doubles (device)
     cudaError_t (*reduce)(const HostGeom &, int64_t pitch, bool force, int parity, const void *f, double *partial,
                           int nblocks, int *flag, double *out, cudaStream_t);
-    // G holds compute-type values; tmap is the CUtensorMap of f (64 bytes,
-    // host memory); status receives bit 2 when a bounded wait gave up
-    cudaError_t (*snapshot)(const HostGeom &, int64_t pitch, bool force, const void *f, void *G, const TileInfo &,
-                            cudaStream_t);
-    cudaError_t (*merged)(const HostGeom &, int64_t pitch, bool force, void *f, const void *G, const TileInfo &,
-                          const void *tmap, int *status, cudaStream_t);
-    size_t (*merged_smem)(int tile_y);  // dynamic shared memory of the merged kernel (0 = not built)
     // shadow-shell merged sweep: band height limit and shell slots per tile
     // of this storage's instantiation; G* arrays hold stored elements
     int m3_ty, m3_nsp;
     int m3_zsave;  // compute-type elements per tile saved across a periodic-z march
     cudaError_t (*shell_gather)(const HostGeom &, int64_t pitch, const void *f, void *G, const ShellInfo &,
                                 cudaStream_t);
+    // Tensor maps (tmap, tmapz) are CUtensorMaps in host memory (64 bytes);
+    // status receives a bit when a bounded wait of a sweep gave up.
     // tmap: CUtensorMap of f with a box of one direction of a 32 x m3_ty tile;
     // tmapz: the same over the chunk-boundary copy (nzc > 1, else unused);
     // zsave: m3_zsave elements per tile with periodic z (else unused)
@@ -98,11 +86,6 @@ struct StorageOps {
                           const void *tmap, int *status, cudaStream_t);
     int (*nsweep_ctas_per_sm)(bool force);
     int ns_ty, ns_box_w, ns_margin;
-    // persistent plane-wavefront sweep (two time steps); sched points to a
-    // WaveSchedule (device pointers inside), grid = number of CTAs
-    cudaError_t (*wavefront)(const HostGeom &, int64_t pitch, bool force, void *f, const void *sched, int grid,
-                             cudaStream_t);
-    int (*wavefront_blocks_per_sm)(bool force);
     // lam_* are arrays of the compute type with the given pitch
     cudaError_t (*adjoint)(const HostGeom &, int64_t pitch, bool force, const void *f, const void *lam_in,
                            void *lam_out, double *gF, cudaStream_t);

@@ -24,20 +24,19 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ESTATE, LBM_ENONFINITE, LBM_ETIME
     0, -1, -2, -3, -4, -5, -6, -7
 LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_LID = 0, 1, 2
 LBM_STORAGE_F64, LBM_STORAGE_F32, LBM_STORAGE_F32S, LBM_STORAGE_F16S, LBM_STORAGE_BF16S = 0, 1, 2, 3, 4
-LBM_VARIANT_TWO_LATTICE, LBM_VARIANT_AA, LBM_VARIANT_MERGED, LBM_VARIANT_WAVEFRONT = 0, 1, 2, 3
+LBM_VARIANT_TWO_LATTICE, LBM_VARIANT_AA, LBM_VARIANT_MERGED = 0, 1, 2
 LBM_FORCE_NONE, LBM_FORCE_UNIFORM, LBM_FORCE_FIELD = 0, 1, 2
 LBM_DTYPE_F32, LBM_DTYPE_F64 = 0, 1
 LBM_COLLISION_BGK, LBM_COLLISION_TRT = 0, 1
 COLLISION = {"bgk": LBM_COLLISION_BGK, "trt": LBM_COLLISION_TRT}
-LBM_KERNEL_TWO_LATTICE, LBM_KERNEL_AA_EVEN, LBM_KERNEL_AA_ODD, LBM_KERNEL_SNAPSHOT, LBM_KERNEL_MERGED, \
-    LBM_KERNEL_WAVEFRONT = 0, 1, 2, 3, 4, 5
+LBM_KERNEL_TWO_LATTICE, LBM_KERNEL_AA_EVEN, LBM_KERNEL_AA_ODD, LBM_KERNEL_SNAPSHOT, LBM_KERNEL_MERGED = \
+    0, 1, 2, 3, 4
 KERNELS = {"two_lattice": LBM_KERNEL_TWO_LATTICE, "aa_even": LBM_KERNEL_AA_EVEN, "aa_odd": LBM_KERNEL_AA_ODD,
-           "snapshot": LBM_KERNEL_SNAPSHOT, "merged": LBM_KERNEL_MERGED, "wavefront": LBM_KERNEL_WAVEFRONT}
+           "snapshot": LBM_KERNEL_SNAPSHOT, "merged": LBM_KERNEL_MERGED}
 
 STORAGE = {"f64": LBM_STORAGE_F64, "f32": LBM_STORAGE_F32, "f32s": LBM_STORAGE_F32S,
            "f16s": LBM_STORAGE_F16S, "bf16s": LBM_STORAGE_BF16S}
-VARIANT = {"two_lattice": LBM_VARIANT_TWO_LATTICE, "aa": LBM_VARIANT_AA, "merged": LBM_VARIANT_MERGED,
-           "wavefront": LBM_VARIANT_WAVEFRONT}
+VARIANT = {"two_lattice": LBM_VARIANT_TWO_LATTICE, "aa": LBM_VARIANT_AA, "merged": LBM_VARIANT_MERGED}
 BC = {"periodic": LBM_BC_PERIODIC, "wall": LBM_BC_WALL, "lid": LBM_BC_LID}
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -62,7 +61,6 @@ class lbm_config(ctypes.Structure):
         ("variant", ctypes.c_int32),
         ("force_mode", ctypes.c_int32),
         ("force_uniform", ctypes.c_double * 3),
-        ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
         ("collision", ctypes.c_int32),
         ("trt_lambda", ctypes.c_double),
     ]
@@ -293,7 +291,7 @@ def lbm_adjoint_backward(h, dLdrho, dLdu, dtype_code: int, dLdf0, dLdF, work, nb
 
 def make_config(shape: Sequence[int], tau: float, bc: Sequence[Union[str, int]] = ("periodic",) * 6,
                 u_lid=(0.0, 0.0, 0.0), rho_wall: float = 1.0, storage: str = "f32", variant: str = "aa",
-                force_mode: int = LBM_FORCE_NONE, force_uniform=(0.0, 0.0, 0.0), tile=(0, 0),
+                force_mode: int = LBM_FORCE_NONE, force_uniform=(0.0, 0.0, 0.0),
                 collision: Union[str, int] = "bgk", trt_lambda: float = 3.0 / 16.0) -> lbm_config:
     """Build an lbm_config; shape is (nx, ny, nz), bc lists x-, x+, y-, y+, z-, z+."""
     c = lbm_config()
@@ -309,7 +307,6 @@ def make_config(shape: Sequence[int], tau: float, bc: Sequence[Union[str, int]] 
     c.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     c.variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
     c.force_mode = int(force_mode)
-    c.tile_x, c.tile_y = int(tile[0]), int(tile[1])
     c.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
     c.trt_lambda = float(trt_lambda)
     return c
@@ -326,7 +323,7 @@ class Lattice:
     """
 
     def __init__(self, shape, tau: float, bc=("periodic",) * 6, u_lid=(0.0, 0.0, 0.0), rho_wall: float = 1.0,
-                 storage: str = "f32", variant: str = "aa", force=None, tile=(0, 0), device=None, stream=None,
+                 storage: str = "f32", variant: str = "aa", force=None, device=None, stream=None,
                  collision: str = "bgk", trt_lambda: float = 3.0 / 16.0):
         import torch
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -336,7 +333,7 @@ class Lattice:
             fm, fu = LBM_FORCE_FIELD, (0.0, 0.0, 0.0)
         else:
             fm, fu = LBM_FORCE_UNIFORM, tuple(float(v) for v in force)
-        self.cfg = make_config(shape, tau, bc, u_lid, rho_wall, storage, variant, fm, fu, tile, collision, trt_lambda)
+        self.cfg = make_config(shape, tau, bc, u_lid, rho_wall, storage, variant, fm, fu, collision, trt_lambda)
         self.shape = tuple(int(v) for v in shape)  # (nx, ny, nz)
         self.nbytes = lbm_required_bytes(self.cfg)
         with torch.cuda.device(self.device):
@@ -429,8 +426,10 @@ class Lattice:
         return out
 
     def selftest_wait_timeout(self) -> int:
-        """WAVEFRONT only: make every bounded inter-CTA wait of one sweep run
-        out and return the recorded status (LBM_ETIMEOUT expected)."""
+        """MERGED with the neighbour-synchronised sweep only: run one sweep in
+        which one tile never announces its progress, so that the bounded
+        waits for it run out; return the recorded status (LBM_ETIMEOUT
+        expected).  The populations are undefined afterwards."""
         return lbm_selftest_wait_timeout(self.h)
 
     # adjoint --------------------------------------------------------------

@@ -54,7 +54,7 @@ def to_oracle_order(f_gpu: np.ndarray) -> np.ndarray:
     return f_gpu[p]
 
 
-def make_gpu(cfg: "oracle.Config", storage: str, variant: str, tile=(0, 0), device="cuda:0") -> Lattice:
+def make_gpu(cfg: "oracle.Config", storage: str, variant: str, device="cuda:0") -> Lattice:
     import torch
     if cfg.force_mode == FORCE_FIELD:
         force = torch.tensor(np.asarray(cfg.force_field, dtype=np.float32), device=device)
@@ -63,7 +63,7 @@ def make_gpu(cfg: "oracle.Config", storage: str, variant: str, tile=(0, 0), devi
     else:
         force = None
     return Lattice((cfg.nx, cfg.ny, cfg.nz), cfg.tau, bc=tuple(int(b) for b in cfg.bc), u_lid=tuple(cfg.u_lid),
-                   rho_wall=cfg.rho_wall, storage=storage, variant=variant, force=force, tile=tile, device=device,
+                   rho_wall=cfg.rho_wall, storage=storage, variant=variant, force=force, device=device,
                    collision="trt" if cfg.collision == oracle.COLL_TRT else "bgk", trt_lambda=cfg.trt_lambda)
 
 

@@ -17,14 +17,7 @@ from helpers import relmax
 pytestmark = pytest.mark.gpu
 
 CASES = cases()
-VARIANTS = ["two_lattice", "aa", "merged", "merged_snapshot", "wavefront"]
-
-
-def _variant(v):
-    """(variant, tile): "merged" takes the automatic tiles (the shadow-shell
-    sweep where z is not periodic), "merged_snapshot" an explicit 32 x 4 tile
-    (the snapshot sweep)."""
-    return ("merged", (32, 4)) if v == "merged_snapshot" else (v, (0, 0))
+VARIANTS = ["two_lattice", "aa", "merged"]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -33,8 +26,7 @@ def test_cavity_32_fp64_100_steps(gpu, variant):
     cfg = oracle.cavity(32, 0.6)
     ref = oracle.run(cfg, oracle.init_equilibrium(cfg), 100)
     rho_r, u_r = oracle.moments(cfg, ref)
-    v, tile = _variant(variant)
-    lat = make_gpu(cfg, "f64", v, tile=tile)
+    lat = make_gpu(cfg, "f64", variant)
     lat.init_equilibrium()
     lat.step(100)
     assert relmax(gpu_state(lat), ref) <= 1e-12
@@ -49,10 +41,7 @@ def test_cavity_32_fp32_100_steps(gpu, storage, variant):
     cfg = oracle.cavity(32, 0.6)
     ref = oracle.run(cfg, oracle.init_equilibrium(cfg), 100)
     _, u_r = oracle.moments(cfg, ref)
-    v, tile = _variant(variant)
-    if storage != "f64" and v == "merged" and tile != (0, 0):
-        tile = (32, 16)
-    lat = make_gpu(cfg, storage, v, tile=tile)
+    lat = make_gpu(cfg, storage, variant)
     lat.init_equilibrium()
     lat.step(100)
     _, u = gpu_moments(lat)
@@ -66,8 +55,7 @@ def test_fp64_cases(gpu, name, variant, nsteps):
     cfg = oracle_force_as_f32(CASES[name])
     f0 = start_state(cfg, seed=nsteps)
     ref = oracle.run(cfg, f0, nsteps)
-    v, tile = _variant(variant)
-    lat = make_gpu(cfg, "f64", v, tile=tile)
+    lat = make_gpu(cfg, "f64", variant)
     load_state(lat, f0)
     lat.step(nsteps)
     assert lat.time == nsteps
@@ -131,14 +119,23 @@ def _bench_lattice(variant, storage="f32"):
     return cfg, lat
 
 
-@pytest.mark.parametrize("variant", ["merged", "wavefront"])
-def test_full_lattice_two_step_sweep_at_bench_size(gpu, variant):
+# the two-step sweeps of MERGED: the neighbour-synchronised one (the default
+# on the walled 256^3 cavity) and the shadow-shell one (selected at creation)
+SWEEPS = {"neighbour": "neighbour", "shadow": "shadow"}
+
+
+@pytest.mark.parametrize("sweep", sorted(SWEEPS))
+def test_full_lattice_two_step_sweep_at_bench_size(gpu, monkeypatch, sweep):
     """256^3 cavity (the benchmark workload, FP32, default launch shapes):
-    after 20 steps, one more two-step sweep -- k_merged3 (one CTA per 32 x 14
-    tile, all 256 planes, shadow refreshed by the previous sweep) or
-    k_wavefront -- is compared on every population of the lattice with the
-    FP64 oracle stepping the GPU's own state twice."""
-    cfg, lat = _bench_lattice(variant)
+    after 20 steps, one more two-step sweep -- k_nsweep (the benchmark
+    kernel: 152 CTAs of 32 x 14 tiles, all resident, all 256 planes) or
+    k_merged3 (the same tiles, shadow refreshed by the previous sweep) -- is
+    compared on every population of the lattice with the FP64 oracle
+    stepping the GPU's own state twice."""
+    monkeypatch.setenv("LBM_MERGED_SWEEP", SWEEPS[sweep])
+    cfg, lat = _bench_lattice("merged")
+    monkeypatch.delenv("LBM_MERGED_SWEEP")
+    variant = f"merged/{sweep}"
     f20 = gpu_state(lat)                       # oracle order, float64
     lat.step(2)
     exp = oracle.run(cfg, f20, 2)
@@ -197,12 +194,14 @@ def test_velocity_error_fp32_vs_fp64_bench_case(gpu):
         assert errs[t][("f32s", "merged")] <= bound
 
 
-@pytest.mark.parametrize("variant", ["merged", "wavefront"])
-def test_mass_conservation_bench_size(gpu, variant):
+@pytest.mark.parametrize("sweep", sorted(SWEEPS))
+def test_mass_conservation_bench_size(gpu, monkeypatch, sweep):
     """Exact mass conservation of the cavity holds at 256^3 (FP64 sums of an
     FP32 lattice: drift only from storage rounding)."""
     cfg = oracle.cavity(256, 0.55)
-    lat = make_gpu(cfg, "f32s", variant)
+    monkeypatch.setenv("LBM_MERGED_SWEEP", SWEEPS[sweep])
+    lat = make_gpu(cfg, "f32s", "merged")
+    monkeypatch.delenv("LBM_MERGED_SWEEP")
     lat.init_equilibrium()
     m0 = lat.reduce()[0]
     lat.step(100)

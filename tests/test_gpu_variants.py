@@ -1,8 +1,9 @@
 """The schedules agree bit for bit (the paper verifies its two-step solvers
 against the single-step ones, Sec. 5.1; here the check is exact):
-TWO_LATTICE == AA == WAVEFRONT == MERGED for every storage format, the
-shadow-shell MERGED sweep (automatic tiles) and the snapshot sweep (explicit
-tiles), odd and even step counts and mixed step(n) sequences."""
+TWO_LATTICE == AA == MERGED for every storage format, both two-step sweeps
+of MERGED (neighbour-synchronised and shadow-shell, chosen with
+LBM_MERGED_SWEEP when the handle is created), odd and even step counts and
+mixed step(n) sequences."""
 import numpy as np
 import pytest
 
@@ -22,23 +23,27 @@ def _raw(lat):
 @pytest.mark.parametrize("storage", STORAGES)
 @pytest.mark.parametrize("name", sorted(CASES))
 @pytest.mark.parametrize("nsteps", [5, 6])
-def test_schedules_bitwise_equal(gpu, storage, name, nsteps):
+def test_schedules_bitwise_equal(gpu, monkeypatch, storage, name, nsteps):
+    """(Where a lattice has a periodic face, or the storage is FP64, the
+    neighbour-synchronised sweep cannot run and the handle takes the
+    shadow-shell one.)"""
     import torch
     cfg = oracle_force_as_f32(CASES[name])
     f0 = start_state(cfg, seed=3)
     ref = None
-    tiles = [(32, 4)] + ([] if storage == "f64" else [(32, 8), (32, 16)])
-    runs = [("two_lattice", (0, 0)), ("aa", (0, 0)), ("wavefront", (0, 0)), ("merged", (0, 0))] + \
-        [("merged", t) for t in tiles]
-    for variant, tile in runs:
-        lat = make_gpu(cfg, storage, variant, tile=tile)
+    runs = [("two_lattice", None), ("aa", None), ("merged", None), ("merged", "neighbour"), ("merged", "shadow")]
+    for variant, sweep in runs:
+        if sweep:
+            monkeypatch.setenv("LBM_MERGED_SWEEP", sweep)
+        lat = make_gpu(cfg, storage, variant)
+        monkeypatch.delenv("LBM_MERGED_SWEEP", raising=False)
         load_state(lat, f0)
         lat.step(nsteps)
         got = _raw(lat)
         if ref is None:
             ref = got
         else:
-            assert torch.equal(got, ref), (variant, tile)
+            assert torch.equal(got, ref), (variant, sweep)
         rho, u = lat.moments(torch.float64)
         assert torch.isfinite(u).all()
 
@@ -53,7 +58,7 @@ def test_mixed_step_sequences(gpu, storage):
     a = make_gpu(cfg, storage, "aa")
     load_state(a, f0)
     a.step(9)
-    m = make_gpu(cfg, storage, "merged", tile=(32, 8))
+    m = make_gpu(cfg, storage, "merged")
     load_state(m, f0)
     for k in (1, 2, 3, 1, 2):
         m.step(k)
@@ -61,21 +66,17 @@ def test_mixed_step_sequences(gpu, storage):
     load_state(t, f0)
     for _ in range(9):
         t.step(1)
-    w = make_gpu(cfg, storage, "wavefront")
-    load_state(w, f0)
-    for k in (2, 1, 4, 2):
-        w.step(k)
     # shadow-shell sweep: consecutive sweeps reuse the shadow, a single step
     # in between invalidates it
     s3 = make_gpu(cfg, storage, "merged")
     load_state(s3, f0)
     for k in (2, 2, 1, 3, 1):
         s3.step(k)
-    assert m.time == a.time == t.time == w.time == s3.time == 9
-    ra, rm, rt, rw, r3 = _raw(a), _raw(m), _raw(t), _raw(w), _raw(s3)
-    assert torch.equal(ra, rm) and torch.equal(ra, rt) and torch.equal(ra, rw) and torch.equal(ra, r3)
+    assert m.time == a.time == t.time == s3.time == 9
+    ra, rm, rt, r3 = _raw(a), _raw(m), _raw(t), _raw(s3)
+    assert torch.equal(ra, rm) and torch.equal(ra, rt) and torch.equal(ra, r3)
     # moments agree at both parities (a is at the odd parity after 9 steps)
-    for lat in (a, m, t, w, s3):
+    for lat in (a, m, t, s3):
         rho, u = lat.moments(torch.float64)
         r0, u0 = a.moments(torch.float64)
         assert torch.equal(rho, r0) and torch.equal(u, u0)
@@ -114,7 +115,7 @@ def test_equilibrium_init_matches_oracle(gpu):
     assert relmax(gpu_state(lat), ref) <= 1e-15
 
 
-@pytest.mark.parametrize("variant", ["aa", "two_lattice", "merged", "wavefront"])
+@pytest.mark.parametrize("variant", ["aa", "two_lattice", "merged"])
 @pytest.mark.parametrize("storage", ["f32", "f64"])
 def test_graph_replay_matches_direct_launches(gpu, variant, storage):
     """step(n) with n >= 32 replays a captured CUDA graph of 32 time steps;
@@ -160,28 +161,38 @@ def test_graph_rebuilt_after_force_field_change(gpu):
     assert torch.equal(_raw(a), _raw(b))
 
 
-def test_bounded_wait_gives_up_and_reports(gpu):
-    """Failure detection of the inter-CTA waits: a sweep whose odd-step items
-    wait for even-step items that are never scheduled gives up (bounded
-    waits), reports LBM_ETIMEOUT and leaves the state untouched; the handle
-    keeps working afterwards."""
+def test_bounded_wait_gives_up_and_reports(gpu, monkeypatch):
+    """Failure detection of the inter-CTA waits of the neighbour-synchronised
+    sweep: in a sweep where one tile never announces its progress, the
+    tiles waiting for it give up after their bounded polls, so do the tiles
+    waiting for those, and the sweep reports LBM_ETIMEOUT (no fault, no
+    unbounded spin).  The handle keeps working afterwards: a new state steps
+    exactly like AA.  Other handles and the odd parity are refused."""
     import torch
-    from paper_2208_05429_gb300.lbm import LBM_ETIMEOUT, LBM_ESTATE
+    from paper_2208_05429_gb300.lbm import LBM_ESTATE, LBM_ETIMEOUT
     cfg = oracle_force_as_f32(CASES["cavity16"])
     f0 = start_state(cfg, seed=21)
-    w = make_gpu(cfg, "f32", "wavefront")
+    monkeypatch.setenv("LBM_MERGED_SWEEP", "neighbour")
+    w = make_gpu(cfg, "f32", "merged")
+    monkeypatch.delenv("LBM_MERGED_SWEEP")
     load_state(w, f0)
     w.step(2)
-    before = _raw(w)
     assert w.selftest_wait_timeout() == LBM_ETIMEOUT
-    assert torch.equal(_raw(w), before) and w.time == 2
-    w.step(2)
+    assert w.time == 2
+    load_state(w, f0)
+    w.step(4)
     a = make_gpu(cfg, "f32", "aa")
     load_state(a, f0)
     a.step(4)
     assert torch.equal(_raw(w), _raw(a))
     assert np.all(np.isfinite(w.reduce()))
-    assert make_gpu(cfg, "f32", "aa").selftest_wait_timeout() == LBM_ESTATE
+    w.step(1)
+    assert w.selftest_wait_timeout() == LBM_ESTATE   # odd parity
+    assert a.selftest_wait_timeout() == LBM_ESTATE   # not a MERGED handle
+    monkeypatch.setenv("LBM_MERGED_SWEEP", "shadow")
+    s = make_gpu(cfg, "f32", "merged")
+    monkeypatch.delenv("LBM_MERGED_SWEEP")
+    assert s.selftest_wait_timeout() == LBM_ESTATE   # the shadow-shell sweep
 
 
 def _random_config(rng):
@@ -204,7 +215,7 @@ def _random_config(rng):
 
 
 @pytest.mark.parametrize("seed", range(12))
-def test_random_shapes_merged_and_wavefront_equal_aa(gpu, seed):
+def test_random_shapes_merged_equal_aa(gpu, monkeypatch, seed):
     import torch
     rng = np.random.default_rng(1000 + seed)
     cfg = _random_config(rng)
@@ -215,11 +226,13 @@ def test_random_shapes_merged_and_wavefront_equal_aa(gpu, seed):
     load_state(ref, f0)
     ref.step(nsteps)
     want = _raw(ref)
-    for variant in ("merged", "wavefront"):
-        lat = make_gpu(cfg, storage, variant)
+    for sweep in ("shadow", "neighbour"):
+        monkeypatch.setenv("LBM_MERGED_SWEEP", sweep)
+        lat = make_gpu(cfg, storage, "merged")
+        monkeypatch.delenv("LBM_MERGED_SWEEP")
         load_state(lat, f0)
         lat.step(nsteps)
-        assert torch.equal(_raw(lat), want), (variant, cfg.nx, cfg.ny, cfg.nz, cfg.bc, storage, nsteps)
+        assert torch.equal(_raw(lat), want), (sweep, cfg.nx, cfg.ny, cfg.nz, cfg.bc, storage, nsteps)
 
 
 def _zchunk_config(shape):
