@@ -15,7 +15,9 @@ second).
 Three further modes print their own JSON line instead of the benchmark line:
 ``--sweep`` (cavity cubes 64^3 .. 768^3, FP32 and FP16-shifted storage, AA
 and merged, plus the host oracle at 32^3, 64^3 and 128^3 on all host
-threads and on one),
+threads and on one, and the paper's own CPU algorithms -- Alg. 1, Alg. 2
+with and without prisms and its stride search, Alg. 3 on all host threads
+-- at 64^3, 128^3 and 256^3),
 ``--precision-study`` (periodic Taylor-Green box 512^3, U0 = 0.04, tau =
 0.52: FP32 / FP16 / BF16 storage against an FP64 run of the same case,
 kinetic energy every 100 steps and max-norm velocity error) and
@@ -26,6 +28,11 @@ Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs an
 independent replica on its own GPU (the update shards only through a halo
 exchange that this single-GPU build does not implement): value = the cells
 all ranks updated / the slowest rank's time.
+
+Besides the oracle's "cpu_baseline", the line carries "cpu_paper": the
+paper's parallel two-step memory-aware LBM (Alg. 3, FP64, OpenMP on the host
+cores, cpu_memaware) on the benchmark cavity itself, with its prism stride
+chosen by the paper's stride search.
 
 ``--impl reference`` times the FP64 CPU oracle (the plain two-lattice
 definition of the step, OpenMP on the host cores) on a bounded sample of the
@@ -386,6 +393,49 @@ def oracle_mlups(n, budget_s, pairs=None, nthreads=None):
     return n ** 3 * done / el / 1e6, done, el
 
 
+def paper_cpu_mlups(n, alg, tile, nthreads, sweeps=1, cells=None):
+    """Time the paper's own CPU algorithm `alg` (cpu_memaware: "fuse" Alg. 1,
+    "two_step" Alg. 2, "omp" Alg. 3) on the n^3 cavity: `sweeps` two-step
+    sweeps (two Alg. 1 steps for "fuse") from the rest state."""
+    import numpy as np
+    import cpu_memaware as cm
+    cfg = cm.Config(n, n, n, TAU, u_lid=U_LID)
+    if cells is None:
+        _, w = cm.lattice()
+        cells = np.ascontiguousarray(np.broadcast_to(w, (n, n, n, 19)).astype(np.float64))
+    t0 = time.perf_counter()
+    cm.run_cells(alg, cfg, cells, 2 * sweeps, tile, nthreads)
+    el = time.perf_counter() - t0
+    return n ** 3 * 2 * sweeps / el / 1e6, el, cells
+
+
+def paper_cpu_leg(n, budget_s):
+    """The paper's Alg. 3 (OpenMP two-step prism, FP64) on the host cores with
+    its stride search (Sec. 5.2: strides 8 .. 448, plus no prisms), one sweep
+    per stride after a warm-up sweep, then the best stride for about
+    budget_s."""
+    import cpu_memaware as cm
+    cm.build()
+    nt = omp_threads()
+    rate, el, cells = paper_cpu_mlups(n, "omp", 0, nt)  # warm-up (pages, threads)
+    search = {}
+    for tile in [t for t in (8, 16, 32, 64, 128, 256, 448) if t <= n] + [0]:
+        rate, el, cells = paper_cpu_mlups(n, "omp", tile, nt, cells=cells)
+        search[str(tile) if tile else "none"] = round(rate, 2)
+    best = max(search, key=search.get)
+    tile = 0 if best == "none" else int(best)
+    sweeps = max(1, int(budget_s / max(el, 1e-3)))
+    rate, el, cells = paper_cpu_mlups(n, "omp", tile, nt, sweeps=sweeps, cells=cells)
+    _, w = cm.lattice()
+    mass = float(cells.sum())
+    del cells
+    return {"value": round(rate, 3), "unit": UNIT, "cores": nt,
+            "kind": "the paper's Alg. 3 (parallel two-step memory-aware LBM, OpenMP, FP64)",
+            "prism_stride": best, "stride_search_MLUPS": search,
+            "sample": f"{2 * sweeps} time steps of the {n}^3 cavity itself ({el:.1f} s)",
+            "mass_conserved": abs(mass - n ** 3) / n ** 3 < 1e-10}
+
+
 def omp_threads():
     v = os.environ.get("OMP_NUM_THREADS")
     return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
@@ -476,8 +526,24 @@ def sweep(args):
             rate, done, el = oracle_mlups(n, 5.0, nthreads=nt)
             cpu.append({"n": n, "MLUPS": round(rate, 2), "time_steps": done, "seconds": round(el, 2),
                         "threads": nt, "nproc": os.cpu_count()})
+    # the paper's four sequential solvers (Sec. 5.2: fuse, fuse prism -- not
+    # built, Palabos's own --, 2-step, 2-step prism with its stride search)
+    # and its parallel one (Alg. 3, all threads), FP64
+    import cpu_memaware as cm
+    cm.build()
+    paper = []
+    for n in (64, 128, 256):
+        seq = {"fuse": round(paper_cpu_mlups(n, "fuse", 0, 1)[0], 2),
+               "two_step": round(paper_cpu_mlups(n, "two_step", 0, 1)[0], 2)}
+        tiles = [t for t in (8, 16, 32, 64, 128, 256) if t <= n]
+        if n <= 128:
+            seq["two_step_prism"] = {str(t): round(paper_cpu_mlups(n, "two_step", t, 1)[0], 2) for t in tiles}
+        par = {str(t): round(paper_cpu_mlups(n, "omp", t, omp_threads())[0], 2) for t in tiles + [0]}
+        paper.append({"n": n, "sequential_MLUPS": seq, "omp_MLUPS_by_stride": par, "threads": omp_threads()})
+        print(json.dumps(paper[-1]), file=sys.stderr, flush=True)
     print(json.dumps({"mode": "sweep", "workload": "lid-driven cavity n^3, tau 0.55, lid (0.05,0,0)",
-                      "peak_GBs": peak, "peak_source": peak_kind, "gpu": rows, "cpu_oracle": cpu}), flush=True)
+                      "peak_GBs": peak, "peak_source": peak_kind, "gpu": rows, "cpu_oracle": cpu,
+                      "cpu_paper_algorithms": paper}), flush=True)
     return 0
 
 
@@ -640,6 +706,10 @@ def main():
                 "value": round(rate, 3), "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
                 "sample": f"{done} time steps of the {n}^3 cavity itself, FP64 two-lattice oracle "
                           f"({el:.1f} s, OpenMP)"}
+            try:
+                line["cpu_paper"] = paper_cpu_leg(n, 3.0)
+            except Exception as e:
+                line["cpu_paper"] = {"error": repr(e)[:200]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist_on:
