@@ -321,8 +321,10 @@ int lbm_adjoint_seed(lbm_handle *h, const void *dLdrho, const void *dLdu, void *
                      int32_t dtype, double *dLdF);
 
 /* Workspace bytes for lbm_adjoint_forward/backward with T steps and a
- * checkpoint every K steps: ceil(T/K)+1 checkpoints, K recompute states and
- * two adjoint buffers.  Host output. */
+ * checkpoint every K steps: ceil(T/K)+1 checkpoints, two segment buffers
+ * (one segment is recomputed while the adjoint runs through the other), each
+ * two states and the moments rho, u of K states (all of f^t the adjoint step
+ * reads), and two adjoint buffers.  Host output. */
 int lbm_adjoint_workspace_bytes(const lbm_handle *h, int64_t T, int64_t K, size_t *bytes);
 
 /* Run T >= 1 steps forward from the current state (which becomes f^0),
@@ -336,7 +338,11 @@ int lbm_adjoint_forward(lbm_handle *h, int64_t T, int64_t K, void *work, size_t 
  * f^T (device, `dtype`, dLdrho may be NULL), recomputes each K-step segment
  * from its checkpoint and applies lbm_adjoint_step backwards.  Writes
  * dLdf0 = dL/df^0 (device canonical populations, `dtype`, may be NULL) and
- * accumulates dLdF += dL/dF (device FP64 [3][z][y][x], may be NULL). */
+ * accumulates dLdF += dL/dF (device FP64 [3][z][y][x], may be NULL).
+ * Asynchronous on the handle's stream: the segment recomputes run on an
+ * internal stream of the handle, ordered after the work already on the
+ * handle's stream and before the adjoint steps that read them (events), so
+ * that the recompute of one segment overlaps the adjoint of the next. */
 int lbm_adjoint_backward(lbm_handle *h, const void *dLdrho, const void *dLdu, int32_t dtype,
                          void *dLdf0, double *dLdF, void *work, size_t work_bytes);
 

@@ -306,13 +306,28 @@ __global__ void k_init_eq(Geom<typename S::R> g, typename S::T *__restrict__ f, 
     });
 }
 
+// The moments (rho, u) of a cell that the adjoint step reads, as
+// moments_of computes them: mom[a * slot + c], a = 0 .. 3 (rho, ux, uy, uz),
+// compute type.
+template <class R>
+__device__ __forceinline__ void store_mom(R *__restrict__ mom, int64_t slot, int c, const Mom<R> &m)
+{
+    mom[c] = m.rho;
+    mom[slot + c] = m.ux;
+    mom[2 * slot + c] = m.uy;
+    mom[3 * slot + c] = m.uz;
+}
+
 // ---------------------------------------------------------------------------
 // K1: two-lattice fused collide-and-push (natural -> natural)
 // ---------------------------------------------------------------------------
 // dout.p[i] = dst.p[i] + noff[i]: the push address of an interior cell.
-template <class S, bool FORCE, bool TRT = false>
+// MOM: also store the moments of the input state in mom (the recompute of
+// the adjoint's checkpoint segments).
+template <class S, bool FORCE, bool TRT = false, bool MOM = false>
 __global__ void __launch_bounds__(128) k_two_lattice(Geom<typename S::R> g, Dirs<const typename S::T> src,
-                                                     Dirs<typename S::T> dst, Dirs<typename S::T> dout)
+                                                     Dirs<typename S::T> dst, Dirs<typename S::T> dout,
+                                                     typename S::R *__restrict__ mom)
 {
     using R = typename S::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
@@ -322,6 +337,7 @@ __global__ void __launch_bounds__(128) k_two_lattice(Geom<typename S::R> g, Dirs
     load_natural_d<S>(src, c, s);
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
+    if constexpr (MOM) store_mom<R>(mom, g.slot, c, moments_of<R, FORCE>(s, Fx, Fy, Fz));
     collide_sel<R, FORCE, TRT>(g, s, Fx, Fy, Fz);
     if (interior(g, x, y, z)) {
         static_for<Q>([&](auto K) {
@@ -678,10 +694,12 @@ static __global__ void __launch_bounds__(RED_THREADS) k_reduce_final(const doubl
 // f and lam share the geometry g (pitch g.nxp); gF and the force are canonical.
 // fd.p[i] = f + i slot; lin.p[i] = lam_in + i slot + noff[i], the gather
 // address of an interior cell; lout.p[j] = lam_out + j slot.
-template <class S, bool FORCE>
+// MOMIN: the moments of f^t come from mom (store_mom layout) instead of
+// being computed from f^t (fd unused).
+template <class S, bool FORCE, bool MOMIN = false>
 __global__ void __launch_bounds__(128) k_adjoint(Geom<typename S::R> g, Dirs<const typename S::T> fd,
                                                  Dirs<const typename S::R> lin, Dirs<typename S::R> lout,
-                                                 double *__restrict__ gF)
+                                                 double *__restrict__ gF, const typename S::R *__restrict__ mom)
 {
     using R = typename S::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
@@ -689,14 +707,22 @@ __global__ void __launch_bounds__(128) k_adjoint(Geom<typename S::R> g, Dirs<con
     const int64_t n = ncanon(g), cc = canon(g, x, y, z);
     const int c = cell32(g, x, y, z);
     const uint64_t pf = l2_policy_first(), pl = l2_policy_last();
-    R s[Q];
-    static_for<Q>([&](auto K) {
-        constexpr int i = decltype(K)::value;
-        s[i] = decode<S, i>(ld_pol(fd.p[i] + c, pf));
-    });
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, cc, n, Fx, Fy, Fz);
-    const Mom<R> m = moments_of<R, FORCE>(s, Fx, Fy, Fz);
+    Mom<R> m;
+    if constexpr (MOMIN) {
+        m.rho = ld_pol(mom + c, pf);
+        m.ux = ld_pol(mom + g.slot + c, pf);
+        m.uy = ld_pol(mom + 2 * g.slot + c, pf);
+        m.uz = ld_pol(mom + 3 * g.slot + c, pf);
+    } else {
+        R s[Q];
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            s[i] = decode<S, i>(ld_pol(fd.p[i] + c, pf));
+        });
+        m = moments_of<R, FORCE>(s, Fx, Fy, Fz);
+    }
     const R usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
     // mu_i = dL/df*_i: the transpose of streaming
     R mu[Q];
@@ -769,6 +795,23 @@ __global__ void __launch_bounds__(128) k_adjoint(Geom<typename S::R> g, Dirs<con
         st_pol(gF + n + cc, ld_pol(gF + n + cc, pl) + (double)(g.kf * gy + ey * h), pl);
         st_pol(gF + 2 * n + cc, ld_pol(gF + 2 * n + cc, pl) + (double)(g.kf * gz + ez * h), pl);
     }
+}
+
+// The moments of state f (natural parity) into mom (store_mom layout): the
+// last state of an adjoint checkpoint segment, which no recompute step reads.
+template <class S, bool FORCE>
+__global__ void __launch_bounds__(128) k_adj_moments(Geom<typename S::R> g, Dirs<const typename S::T> src,
+                                                     typename S::R *__restrict__ mom)
+{
+    using R = typename S::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const int c = cell32(g, x, y, z);
+    R s[Q];
+    load_natural_d<S>(src, c, s);
+    R Fx, Fy, Fz;
+    force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
+    store_mom<R>(mom, g.slot, c, moments_of<R, FORCE>(s, Fx, Fy, Fz));
 }
 
 // lam = dL/df for L(rho, u) of state f (natural parity); gF += dL/du / (2 rho).

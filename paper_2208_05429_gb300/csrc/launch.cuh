@@ -35,12 +35,34 @@ struct Launch {
         Dirs<T> bo;  // push addresses of an interior cell, one index away
         for (int i = 0; i < Q; ++i) bo.p[i] = b.p[i] + g.noff[i];
         if (h.trt) {
-            if (force) k_two_lattice<S, true, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo);
-            else k_two_lattice<S, false, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo);
+            if (force) k_two_lattice<S, true, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo, nullptr);
+            else k_two_lattice<S, false, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo, nullptr);
         } else {
-            if (force) k_two_lattice<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo);
-            else k_two_lattice<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo);
+            if (force) k_two_lattice<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo, nullptr);
+            else k_two_lattice<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo, nullptr);
         }
+        return cudaGetLastError();
+    }
+    // the same (BGK), also storing the moments of src in mom (adjoint recompute)
+    static cudaError_t two_lattice_mom(const HostGeom &h, int64_t pitch, bool force, const void *src, void *dst,
+                                       void *mom, cudaStream_t st)
+    {
+        const Geom<R> g = make_geom<R>(h, pitch);
+        const Dirs<const T> a = make_dirs((const T *)src, slot_of(h, pitch));
+        const Dirs<T> b = make_dirs((T *)dst, slot_of(h, pitch));
+        Dirs<T> bo;
+        for (int i = 0; i < Q; ++i) bo.p[i] = b.p[i] + g.noff[i];
+        if (force) k_two_lattice<S, true, false, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo, (R *)mom);
+        else k_two_lattice<S, false, false, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo, (R *)mom);
+        return cudaGetLastError();
+    }
+    static cudaError_t adj_moments(const HostGeom &h, int64_t pitch, bool force, const void *f, void *mom,
+                                   cudaStream_t st)
+    {
+        const Geom<R> g = make_geom<R>(h, pitch);
+        const Dirs<const T> a = make_dirs((const T *)f, slot_of(h, pitch));
+        if (force) k_adj_moments<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, (R *)mom);
+        else k_adj_moments<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, (R *)mom);
         return cudaGetLastError();
     }
     // planes [z0, z1) only
@@ -288,8 +310,22 @@ struct Launch {
         const Dirs<R> lout = make_dirs((R *)lam_out, sl);
         Dirs<const R> lin;  // interior gather addresses, one index away
         for (int i = 0; i < Q; ++i) lin.p[i] = (const R *)lam_in + i * sl + g.noff[i];
-        if (force) k_adjoint<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, fd, lin, lout, gF);
-        else k_adjoint<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, fd, lin, lout, gF);
+        if (force) k_adjoint<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, fd, lin, lout, gF, nullptr);
+        else k_adjoint<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, fd, lin, lout, gF, nullptr);
+        return cudaGetLastError();
+    }
+    // the same with the moments of f^t read from mom (adj_moments layout)
+    static cudaError_t adjoint_mom(const HostGeom &h, int64_t pitch, bool force, const void *mom,
+                                   const void *lam_in, void *lam_out, double *gF, cudaStream_t st)
+    {
+        const Geom<R> g = make_geom<R>(h, pitch);
+        const int64_t sl = slot_of(h, pitch);
+        const Dirs<const T> fd{};
+        const Dirs<R> lout = make_dirs((R *)lam_out, sl);
+        Dirs<const R> lin;
+        for (int i = 0; i < Q; ++i) lin.p[i] = (const R *)lam_in + i * sl + g.noff[i];
+        if (force) k_adjoint<S, true, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, fd, lin, lout, gF, (const R *)mom);
+        else k_adjoint<S, false, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, fd, lin, lout, gF, (const R *)mom);
         return cudaGetLastError();
     }
     static cudaError_t adjoint_seed(const HostGeom &h, int64_t pitch, bool force, const void *f, const void *dLdrho,
@@ -344,6 +380,9 @@ StorageOps make_ops()
     o.merged3 = &L::merged3;
     o.zcopy = &L::zcopy;
     o.adjoint = &L::adjoint;
+    o.adjoint_mom = &L::adjoint_mom;
+    o.two_lattice_mom = &L::two_lattice_mom;
+    o.adj_moments = &L::adj_moments;
     o.adjoint_seed = &L::adjoint_seed;
     o.canon_to_pitched = &L::canon_to_pitched;
     o.pitched_to_canon = &L::pitched_to_canon;

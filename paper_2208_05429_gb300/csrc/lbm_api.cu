@@ -43,6 +43,10 @@ struct lbm_handle {
     cudaGraphExec_t gexec;
     cudaStream_t gstream;
     cudaEvent_t gev;
+    // adjoint backward: segment recomputes run on astream, overlapping the
+    // adjoint steps of the segment after them on the handle's stream
+    cudaStream_t astream;
+    cudaEvent_t aev[5];  // start, recompute done (per buffer), adjoint done (per buffer)
     struct StepState {
         int parity, g3cur;
         bool g3fresh;
@@ -89,6 +93,12 @@ static void free_graph_stream(lbm_handle *h)
     if (h->gstream) cudaStreamDestroy(h->gstream);
     h->gev = nullptr;
     h->gstream = nullptr;
+    for (cudaEvent_t &e : h->aev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
+    if (h->astream) cudaStreamDestroy(h->astream);
+    h->astream = nullptr;
 }
 
 namespace {
@@ -527,6 +537,7 @@ void lbm_destroy(lbm_handle *h)
         DeviceGuard g(h->device);
         cudaStreamSynchronize(h->stream);
         if (h->gstream) cudaStreamSynchronize(h->gstream);
+        if (h->astream) cudaStreamSynchronize(h->astream);
         free_graph_stream(h);
         if (h->owns && h->base) {
             cudaFreeAsync(h->base, h->stream);
@@ -883,19 +894,26 @@ int lbm_adjoint_seed(lbm_handle *h, const void *dLdrho, const void *dLdu, void *
 }
 
 namespace {
+// Workspace: the checkpoints f^0, f^K, f^2K, ... and f^T; two segment
+// buffers, so that one segment is recomputed while the adjoint runs through
+// the other, each with two states (the recompute's ping-pong) and the
+// moments (rho, u) of the segment's K states, which is all of f^t the
+// adjoint step reads; two adjoint buffers.  The forward pass steps through
+// the two states of segment buffer 0.
 struct AdjLayout {
-    size_t state, lam, ckpt0, nck, seg0, nseg, lam0, total;
+    size_t state, lam, mom, ckpt0, nck, seg0, segb, lam0, total;
 };
 AdjLayout adj_layout(const lbm_handle *h, int64_t T, int64_t K)
 {
     AdjLayout A;
     A.state = align_up((size_t)state_elems(h->cfg) * h->ops->elem_size);
     A.lam = align_up((size_t)state_elems(h->cfg) * h->ops->real_size);
+    A.mom = align_up((size_t)(state_elems(h->cfg) / Q) * 4 * h->ops->real_size);
     A.nck = (size_t)((T + K - 1) / K) + 1;  // checkpoints at 0, K, 2K, ... plus f^T
-    A.nseg = (size_t)(K < 2 ? 2 : K);
     A.ckpt0 = 0;
     A.seg0 = A.nck * A.state;
-    A.lam0 = A.seg0 + A.nseg * A.state;
+    A.segb = 2 * A.state + (size_t)K * A.mom;  // one segment buffer
+    A.lam0 = A.seg0 + 2 * A.segb;
     A.total = A.lam0 + 2 * A.lam;
     return A;
 }
@@ -957,21 +975,44 @@ int lbm_adjoint_backward(lbm_handle *h, const void *dLdrho, const void *dLdu, in
     const int64_t T = h->adj_T, K = h->adj_K;
     const AdjLayout A = adj_layout(h, T, K);
     char *w = (char *)work;
-    const size_t sb = (size_t)state_elems(h->cfg) * o.elem_size;
     void *la = w + A.lam0, *lb = w + A.lam0 + A.lam;
     CK(o.adjoint_seed(h->hg, h->nxp, h->force, w + (A.nck - 1) * A.state, dLdrho, dLdu, dtype, la, dLdF, h->stream));
+    if (!h->astream) {
+        if (cudaStreamCreateWithFlags(&h->astream, cudaStreamNonBlocking) != cudaSuccess) return LBM_ECUDA;
+        for (cudaEvent_t &e : h->aev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
+    }
+    // Segments from the last to the first.  Segment s recomputes its states
+    // from checkpoint s into buffer s % 2 on astream, keeping only their
+    // moments, and its adjoint steps t1-1 .. t0 run from those on the
+    // handle's stream once that is done.  The recompute of segment s-1 (the
+    // other buffer) waits only for the adjoint of segment s+1, so it overlaps
+    // the adjoint of segment s: the recompute streams at the HBM roofline
+    // while the adjoint steps leave bandwidth unused.
     const int64_t nseg = (T + K - 1) / K;
+    CK(cudaEventRecord(h->aev[0], h->stream));
+    CK(cudaStreamWaitEvent(h->astream, h->aev[0], 0));
     for (int64_t s = nseg - 1; s >= 0; --s) {
+        const int b = (int)(s & 1);
         const int64_t t0 = s * K, t1 = (t0 + K < T) ? t0 + K : T;
-        char *seg = w + A.seg0;
-        CK(cudaMemcpyAsync(seg, w + A.ckpt0 + (size_t)s * A.state, sb, cudaMemcpyDeviceToDevice, h->stream));
-        for (int64_t j = 1; j < t1 - t0; ++j)
-            CK(o.two_lattice(h->hg, h->nxp, h->force, seg + (size_t)(j - 1) * A.state, seg + (size_t)j * A.state,
-                             h->stream));
+        char *base = w + A.seg0 + (size_t)b * A.segb;
+        char *pp[2] = {base, base + A.state};
+        auto mom = [&](int64_t t) -> void * { return base + 2 * A.state + (size_t)(t - t0) * A.mom; };
+        if (s + 2 < nseg) CK(cudaStreamWaitEvent(h->astream, h->aev[3 + b], 0));
+        const void *cur = w + A.ckpt0 + (size_t)s * A.state;
+        for (int64_t t = t0; t + 1 < t1; ++t) {
+            void *nxt = pp[(t - t0) & 1];
+            CK(o.two_lattice_mom(h->hg, h->nxp, h->force, cur, nxt, mom(t), h->astream));
+            cur = nxt;
+        }
+        CK(o.adj_moments(h->hg, h->nxp, h->force, cur, mom(t1 - 1), h->astream));
+        CK(cudaEventRecord(h->aev[1 + b], h->astream));
+        CK(cudaStreamWaitEvent(h->stream, h->aev[1 + b], 0));
         for (int64_t t = t1 - 1; t >= t0; --t) {
-            CK(o.adjoint(h->hg, h->nxp, h->force, seg + (size_t)(t - t0) * A.state, la, lb, dLdF, h->stream));
+            CK(o.adjoint_mom(h->hg, h->nxp, h->force, mom(t), la, lb, dLdF, h->stream));
             void *tmp = la; la = lb; lb = tmp;
         }
+        CK(cudaEventRecord(h->aev[3 + b], h->stream));
     }
     if (dLdf0) CK(o.pitched_to_canon(h->hg, h->nxp, la, dLdf0, dtype, Q, h->stream));
     return LBM_OK;

@@ -89,6 +89,15 @@ struct StorageOps {
     // lam_* are arrays of the compute type with the given pitch
     cudaError_t (*adjoint)(const HostGeom &, int64_t pitch, bool force, const void *f, const void *lam_in,
                            void *lam_out, double *gF, cudaStream_t);
+    // The adjoint's checkpoint segments: mom holds the moments (rho, ux, uy,
+    // uz) of one state, 4 * pitch * ny * nz compute-type elements; the
+    // recompute step stores those of its input, adj_moments those of f, and
+    // adjoint_mom runs the adjoint step from them instead of from f^t.
+    cudaError_t (*two_lattice_mom)(const HostGeom &, int64_t pitch, bool force, const void *src, void *dst,
+                                   void *mom, cudaStream_t);
+    cudaError_t (*adj_moments)(const HostGeom &, int64_t pitch, bool force, const void *f, void *mom, cudaStream_t);
+    cudaError_t (*adjoint_mom)(const HostGeom &, int64_t pitch, bool force, const void *mom, const void *lam_in,
+                               void *lam_out, double *gF, cudaStream_t);
     cudaError_t (*adjoint_seed)(const HostGeom &, int64_t pitch, bool force, const void *f, const void *dLdrho,
                                 const void *dLdu, int dtype, void *lam, double *gF, cudaStream_t);
     cudaError_t (*canon_to_pitched)(const HostGeom &, int64_t pitch, const void *in, int dtype, void *out, int ncomp,
