@@ -34,7 +34,7 @@ import numpy as np
 Q = 19
 BC_PERIODIC, BC_WALL, BC_LID = 0, 1, 2
 FORCE_NONE, FORCE_UNIFORM, FORCE_FIELD = 0, 1, 2
-COLL_BGK, COLL_TRT = 0, 1
+COLL_BGK, COLL_TRT, COLL_REG = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
@@ -88,6 +88,7 @@ def _load():
                 "orc_equilibrium": [ctypes.c_double, _D, _D],
                 "orc_collide_cell": [ctypes.c_double, _D, _D, _D],
                 "orc_collide_cell_trt": [ctypes.c_double, ctypes.c_double, _D, _D, _D],
+                "orc_collide_cell_reg": [ctypes.c_double, _D, _D, _D],
                 "orc_init_equilibrium": [P, _D, _D, _D],
                 "orc_step": [P, _D, _D],
                 "orc_run": [P, _D, ctypes.c_int64, _D],
@@ -132,7 +133,7 @@ class Config:
     force_mode: int = FORCE_NONE
     force_uniform: Sequence[float] = (0.0, 0.0, 0.0)
     force_field: Optional[np.ndarray] = field(default=None, repr=False)
-    collision: int = 0            # COLL_BGK or COLL_TRT
+    collision: int = 0            # COLL_BGK, COLL_TRT or COLL_REG
     trt_lambda: float = 3.0 / 16.0
 
     @property
@@ -186,6 +187,15 @@ def equilibrium(rho: float, u) -> np.ndarray:
     uu = np.ascontiguousarray(u, dtype=np.float64)
     out = np.zeros(Q, np.float64)
     lib.orc_equilibrium(float(rho), _ptr(uu), _ptr(out))
+    return out
+
+
+def collide_cell_reg(tau: float, f, F=(0.0, 0.0, 0.0)) -> np.ndarray:
+    lib = _load()
+    ff = np.ascontiguousarray(f, dtype=np.float64)
+    FF = np.ascontiguousarray(F, dtype=np.float64)
+    out = np.zeros(Q, np.float64)
+    lib.orc_collide_cell_reg(float(tau), _ptr(ff), _ptr(FF), _ptr(out))
     return out
 
 

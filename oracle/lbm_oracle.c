@@ -33,7 +33,13 @@
  *              the "magic" product Lambda = (1/omega+ - 1/2)(1/omega- - 1/2),
  *                f*_i  = f_i - omega+ (f+_i - feq+_i) - omega- (f-_i - feq-_i)
  *                        + (1 - omega+/2) S+_i + (1 - omega-/2) S-_i
- *              (omega- = omega+ gives back BGK).
+ *              (omega- = omega+ gives back BGK), or the regularised BGK form:
+ *              f - feq replaced by its projection on the Hermite
+ *              polynomials up to second order before relaxing,
+ *                f*_i  = feq_i + (1 - omega) w_i (3 c_i . J + (9/2) Q_i : Pi)
+ *                        + (1 - omega/2) S_i
+ *              with J = sum_i (f_i - feq_i) c_i, Pi = sum_i (f_i - feq_i) c_i c_i
+ *              and Q_i = c_i c_i - I/3.
  *   streaming  f_i(x + c_i, t+1) = f*_i(x); periodic axes wrap; a link that
  *              leaves the box across a non-periodic face is a wall link
  *              (half-way bounce-back):
@@ -63,7 +69,7 @@
 
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_LID = 2 };
 enum { FORCE_NONE = 0, FORCE_UNIFORM = 1, FORCE_FIELD = 2 };
-enum { COLL_BGK = 0, COLL_TRT = 1 };
+enum { COLL_BGK = 0, COLL_TRT = 1, COLL_REG = 2 };
 
 /* The D3Q19 velocity set in the half-neighbour order described above. */
 static const int C[Q][3] = {
@@ -93,7 +99,7 @@ typedef struct {
     int32_t force_mode;
     double force_uniform[3];
     const double *force_field; /* [3][N] canonical, used when FORCE_FIELD */
-    int32_t collision;         /* COLL_BGK or COLL_TRT */
+    int32_t collision;         /* COLL_BGK, COLL_TRT or COLL_REG */
     double trt_lambda;         /* Lambda of the TRT form */
 } orc_cfg;
 
@@ -226,10 +232,52 @@ void orc_collide_cell_trt(double tau, double lambda, const double *f, const doub
     }
 }
 
+/* Regularised BGK collision of one cell: the non-equilibrium part f - feq is
+ * replaced by its projection on the Hermite polynomials up to second order,
+ * which keeps its momentum (-F/2 with a body force, zero without) and its
+ * stress and drops every higher ("ghost") moment, and then relaxed:
+ *   J_a   = sum_i (f_i - feq_i) c_ia,   Pi_ab = sum_i (f_i - feq_i) c_ia c_ib
+ *   f1_i  = w_i (3 c_ia J_a + (9/2) (c_ia c_ib - delta_ab / 3) Pi_ab)
+ *   f*_i  = feq_i + (1 - omega) f1_i + (1 - omega/2) S_i
+ * with feq, S and u as in the BGK collision above. */
+void orc_collide_cell_reg(double tau, const double *f, const double *F, double *fstar)
+{
+    double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < Q; ++i) {
+        rho += f[i];
+        for (int a = 0; a < 3; ++a) m[a] += f[i] * C[i][a];
+    }
+    double u[3];
+    for (int a = 0; a < 3; ++a) u[a] = (m[a] + 0.5 * F[a]) / rho;
+    const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+    const double omega = 1.0 / tau;
+    double feq[Q], S[Q], J[3] = {0.0, 0.0, 0.0}, Pi[3][3] = {{0.0}};
+    for (int i = 0; i < Q; ++i) {
+        const double cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
+        const double cF = C[i][0] * F[0] + C[i][1] * F[1] + C[i][2] * F[2];
+        feq[i] = W[i] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+        S[i] = W[i] * (3.0 * (cF - uF) + 9.0 * cu * cF);
+        for (int a = 0; a < 3; ++a) {
+            J[a] += (f[i] - feq[i]) * C[i][a];
+            for (int b = 0; b < 3; ++b) Pi[a][b] += (f[i] - feq[i]) * C[i][a] * C[i][b];
+        }
+    }
+    for (int i = 0; i < Q; ++i) {
+        double q = 0.0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) q += (C[i][a] * C[i][b] - (a == b ? 1.0 / 3.0 : 0.0)) * Pi[a][b];
+        const double cJ = C[i][0] * J[0] + C[i][1] * J[1] + C[i][2] * J[2];
+        const double f1 = W[i] * (3.0 * cJ + 4.5 * q);
+        fstar[i] = feq[i] + (1.0 - omega) * f1 + (1.0 - 0.5 * omega) * S[i];
+    }
+}
+
 /* The collision the configuration selects. */
 static void collide_cfg(const orc_cfg *g, const double *f, const double *F, double *fstar)
 {
     if (g->collision == COLL_TRT) orc_collide_cell_trt(g->tau, g->trt_lambda, f, F, fstar);
+    else if (g->collision == COLL_REG) orc_collide_cell_reg(g->tau, f, F, fstar);
     else orc_collide_cell(g->tau, f, F, fstar);
 }
 
