@@ -679,12 +679,12 @@ def main():
                              ("f32", "merged", "shadow"), ("f32s", "merged", None),
                              ("f16s", "merged", None), ("f16s", "aa", None), ("bf16s", "merged", None),
                              ("bf16s", "aa", None), ("f64", "aa", None), ("f32", "aa", "trt"),
-                             ("f16s", "aa", "trt")):
+                             ("f16s", "aa", "trt"), ("f32", "aa", "reg"), ("f16s", "aa", "reg")):
             if (st, var, env) == (args.storage, args.variant, None):
                 continue
             k = min(args.steps, 300)
-            coll = "trt" if env == "trt" else "bgk"
-            vms, vprof, vl = time_variant(n, st, var, k, 5, sweep_env=None if env == "trt" else env,
+            coll = env if env in ("trt", "reg") else "bgk"
+            vms, vprof, vl = time_variant(n, st, var, k, 5, sweep_env=None if coll != "bgk" else env,
                                           collision=coll)
             del vl
             dk = {"merged": "merged", "aa": "aa_odd"}.get(var, "two_lattice")

@@ -107,12 +107,16 @@ enum { LBM_FORCE_NONE = 0, LBM_FORCE_UNIFORM = 1, LBM_FORCE_FIELD = 2 };
 
 /* Collision operator.  BGK: one relaxation rate 1/tau.  TRT: the parts of
  * the populations that are symmetric / antisymmetric under c -> -c relax
- * with 1/tau and with omega-, where (tau - 1/2)(1/omega- - 1/2) = trt_lambda
- * (the paper's solver builds on "collision models" without naming one,
- * Sec. 1; the schedules of Sec. 3-4 are independent of the model).  TRT runs
- * on the AA and TWO_LATTICE schedules; with the others, and for the
- * adjoint, lbm_validate / the adjoint calls return LBM_EUNSUPPORTED. */
-enum { LBM_COLLISION_BGK = 0, LBM_COLLISION_TRT = 1 };
+ * with 1/tau and with omega-, where (tau - 1/2)(1/omega- - 1/2) = trt_lambda.
+ * REG (regularised BGK): before relaxing with 1/tau, f - feq is replaced by
+ * its projection on the Hermite polynomials up to second order,
+ * w_i (3 c_i.J + 4.5 (c_i c_i - I/3) : Pi) with J, Pi its first and second
+ * moments, which removes the higher ("ghost") moments.  (The paper's solver
+ * builds on "collision models" without naming one, Sec. 1; the schedules of
+ * Sec. 3-4 are independent of the model.)  TRT and REG run on the AA and
+ * TWO_LATTICE schedules; with MERGED, and for the adjoint, lbm_validate / the
+ * adjoint calls return LBM_EUNSUPPORTED. */
+enum { LBM_COLLISION_BGK = 0, LBM_COLLISION_TRT = 1, LBM_COLLISION_REG = 2 };
 
 /* Element type of caller-provided field buffers. */
 enum { LBM_DTYPE_F32 = 0, LBM_DTYPE_F64 = 1 };
@@ -140,8 +144,8 @@ void lbm_config_default(lbm_config *cfg);
  * one periodic and one non-periodic face, |u_lid| >= 0.3, rho_wall <= 0,
  * unknown storage/variant/force mode or collision, or a trt_lambda that is
  * not positive and finite.
- * LBM_EUNSUPPORTED for the TRT collision with a schedule other than AA and
- * TWO_LATTICE. */
+ * LBM_EUNSUPPORTED for the TRT or REG collision with a schedule other than AA
+ * and TWO_LATTICE. */
 int lbm_validate(const lbm_config *cfg);
 
 /* Device bytes a handle of this configuration uses (populations, second

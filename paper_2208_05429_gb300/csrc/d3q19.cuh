@@ -23,6 +23,10 @@ namespace lbm {
 
 constexpr int Q = 19;
 
+// Collision operators (kernel template argument): BGK, two relaxation times,
+// regularised BGK.
+enum { COLL_BGK = 0, COLL_TRT = 1, COLL_REG = 2 };
+
 // ---------------------------------------------------------------------------
 // D3Q19 velocity set.  Directions 1..9 have -1 as their first non-zero
 // component (the half of the neighbours that the swap scheme streams to,
@@ -446,6 +450,100 @@ __device__ __forceinline__ void trt_collide(R (&s)[Q], R omega, R kf, R om, R kf
     });
 }
 
+// Regularised BGK on shifted values s_i = f_i - w_i.  The non-equilibrium
+// part n_i = s_i - seq_i (seq_i = feq_i - w_i) is replaced by its projection
+// on the Hermite polynomials up to second order before relaxing:
+//   J = sum_i n_i c_i,  Pi = sum_i n_i c_i c_i,
+//   f1_i = w_i (3 c_i . J + 4.5 (c_i . Pi . c_i - tr Pi / 3)),
+//   s_i <- seq_i + (1 - omega) f1_i + kf S_i.
+// J is -F/2 with a body force (zero without); dropping it would lose part of
+// the Guo momentum gain.  Per pair {i, i+9}: seq and S split into the parts
+// even and odd in c as in trt_collide; c.Pi.c is even, c.J odd.
+template <class R, bool FORCE>
+__device__ __forceinline__ void reg_collide(R (&s)[Q], R omega, R kf, R Fx, R Fy, R Fz)
+{
+    R dif[10];
+    R drho = s[0];
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        drho = radd(drho, radd(s[i], s[i + 9]));
+        dif[i] = rsub(s[i], s[i + 9]);
+    });
+    R jx = R(0), jy = R(0), jz = R(0);
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        if constexpr (cx(i) != 0) jx = cx(i) > 0 ? radd(jx, dif[i]) : rsub(jx, dif[i]);
+        if constexpr (cy(i) != 0) jy = cy(i) > 0 ? radd(jy, dif[i]) : rsub(jy, dif[i]);
+        if constexpr (cz(i) != 0) jz = cz(i) > 0 ? radd(jz, dif[i]) : rsub(jz, dif[i]);
+    });
+    const R rho = radd(R(1), drho);
+    if constexpr (FORCE) {
+        jx = rfma(R(0.5), Fx, jx);
+        jy = rfma(R(0.5), Fy, jy);
+        jz = rfma(R(0.5), Fz, jz);
+    }
+    const R inv = rrcp(rho);
+    const R ux = rmul(jx, inv), uy = rmul(jy, inv), uz = rmul(jz, inv);
+    const R m15 = rmul(R(-1.5), radd(radd(rmul(ux, ux), rmul(uy, uy)), rmul(uz, uz)));
+    R uF = R(0);
+    if constexpr (FORCE) uF = rfma(ux, Fx, rfma(uy, Fy, rmul(uz, Fz)));
+    // pass 1: the non-equilibrium moments J and Pi (the rest population has
+    // c = 0 and adds to neither)
+    R Jx = R(0), Jy = R(0), Jz = R(0);
+    R Pxx = R(0), Pyy = R(0), Pzz = R(0), Pxy = R(0), Pxz = R(0), Pyz = R(0);
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        constexpr double w = wgt(i);
+        const R cu = cdot<i, R>(ux, uy, uz);
+        const R A = rmul(R(w), rho);
+        const R sym = rfma(rmul(R(4.5), A), rmul(cu, cu), rfma(A, m15, rmul(R(w), drho)));
+        const R anti = rmul(rmul(R(3), A), cu);
+        const R ne = rsub(radd(s[i], s[i + 9]), rmul(R(2), sym));  // n_i + n_i+9
+        const R no = rsub(dif[i], rmul(R(2), anti));               // n_i - n_i+9
+        if constexpr (cx(i) != 0) { Jx = cx(i) > 0 ? radd(Jx, no) : rsub(Jx, no); Pxx = radd(Pxx, ne); }
+        if constexpr (cy(i) != 0) { Jy = cy(i) > 0 ? radd(Jy, no) : rsub(Jy, no); Pyy = radd(Pyy, ne); }
+        if constexpr (cz(i) != 0) { Jz = cz(i) > 0 ? radd(Jz, no) : rsub(Jz, no); Pzz = radd(Pzz, ne); }
+        if constexpr (cx(i) * cy(i) != 0) Pxy = cx(i) * cy(i) > 0 ? radd(Pxy, ne) : rsub(Pxy, ne);
+        if constexpr (cx(i) * cz(i) != 0) Pxz = cx(i) * cz(i) > 0 ? radd(Pxz, ne) : rsub(Pxz, ne);
+        if constexpr (cy(i) * cz(i) != 0) Pyz = cy(i) * cz(i) > 0 ? radd(Pyz, ne) : rsub(Pyz, ne);
+    });
+    const R tr3 = rmul(R(1.0 / 3.0), radd(radd(Pxx, Pyy), Pzz));
+    const R om1 = rsub(R(1), omega);
+    // rest: seq_0 = w_0 (rho (-1.5 u.u) + drho), f1_0 = -4.5 w_0 tr/3, w_0 S_0 = -u.F
+    const R C0 = rfma(rmul(R(1.0 / 3.0), rho), m15, rmul(R(1.0 / 3.0), drho));
+    s[0] = rfma(om1, rmul(R(-1.5), tr3), C0);
+    if constexpr (FORCE) s[0] = rfma(kf, -uF, s[0]);
+    // pass 2: rebuild each pair from seq, the projected f1 and the source
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        constexpr double w = wgt(i);
+        const R cu = cdot<i, R>(ux, uy, uz);
+        const R A = rmul(R(w), rho);
+        const R sym = rfma(rmul(R(4.5), A), rmul(cu, cu), rfma(A, m15, rmul(R(w), drho)));
+        const R anti = rmul(rmul(R(3), A), cu);
+        R cpc = R(0);
+        if constexpr (cx(i) != 0) cpc = radd(cpc, Pxx);
+        if constexpr (cy(i) != 0) cpc = radd(cpc, Pyy);
+        if constexpr (cz(i) != 0) cpc = radd(cpc, Pzz);
+        if constexpr (cx(i) * cy(i) != 0) cpc = cx(i) * cy(i) > 0 ? radd(cpc, rmul(R(2), Pxy)) : rsub(cpc, rmul(R(2), Pxy));
+        if constexpr (cx(i) * cz(i) != 0) cpc = cx(i) * cz(i) > 0 ? radd(cpc, rmul(R(2), Pxz)) : rsub(cpc, rmul(R(2), Pxz));
+        if constexpr (cy(i) * cz(i) != 0) cpc = cy(i) * cz(i) > 0 ? radd(cpc, rmul(R(2), Pyz)) : rsub(cpc, rmul(R(2), Pyz));
+        const R f1s = rmul(R(4.5 * w), rsub(cpc, tr3));
+        const R f1a = rmul(R(3 * w), cdot<i, R>(Jx, Jy, Jz));
+        R a = rfma(om1, radd(f1s, f1a), radd(sym, anti));
+        R b = rfma(om1, rsub(f1s, f1a), rsub(sym, anti));
+        if constexpr (FORCE) {
+            const R cF = cdot<i, R>(Fx, Fy, Fz);
+            const R ssym = rfma(rmul(R(9 * w), cu), cF, rmul(R(-3 * w), uF));
+            const R santi = rmul(R(3 * w), cF);
+            a = rfma(kf, radd(ssym, santi), a);
+            b = rfma(kf, rsub(ssym, santi), b);
+        }
+        s[i] = a;
+        s[i + 9] = b;
+    });
+}
+
 // ---------------------------------------------------------------------------
 // Geometry and boundary description passed by value to every kernel.
 // ---------------------------------------------------------------------------
@@ -458,7 +556,7 @@ struct Geom {
     int64_t plane;       // nxp * ny
     int64_t slot;        // plane * nz: elements per direction
     R omega, kf;         // 1/tau, 1 - omega/2
-    int trt;             // TRT collision (AA and two-lattice kernels)
+    int coll;            // collision (COLL_*; AA and two-lattice kernels)
     R om, kfm;           // TRT: omega-, 1 - omega-/2
     R L[Q];              // 6 w_k rho_w (c_k . u_lid): added to incoming slot k of a lid link
     R Fu[3];             // uniform force
@@ -602,11 +700,13 @@ __device__ __forceinline__ void force_at(const Geom<R> &g, int64_t c, int64_t n,
 }
 
 // The collision a kernel of the AA or two-lattice schedule applies: BGK, or
-// TRT (a separate kernel instantiation; the other schedules are BGK only).
-template <class R, bool FORCE, bool TRT>
+// TRT or regularised (a separate kernel instantiation each; the other
+// schedules are BGK only).
+template <class R, bool FORCE, int COLL>
 __device__ __forceinline__ void collide_sel(const Geom<R> &g, R (&s)[Q], R Fx, R Fy, R Fz)
 {
-    if constexpr (TRT) trt_collide<R, FORCE>(s, g.omega, g.kf, g.om, g.kfm, Fx, Fy, Fz);
+    if constexpr (COLL == COLL_TRT) trt_collide<R, FORCE>(s, g.omega, g.kf, g.om, g.kfm, Fx, Fy, Fz);
+    else if constexpr (COLL == COLL_REG) reg_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
     else bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
 }
 

@@ -108,7 +108,7 @@ inline Geom<R> make_geom(const HostGeom &h, int64_t pitch)
     g.slot = g.plane * h.nz;
     g.omega = R(h.omega);
     g.kf = R(h.kf);
-    g.trt = h.trt;
+    g.coll = h.coll;
     g.om = R(h.omega_m);
     g.kfm = R(h.kf_m);
     for (int i = 0; i < Q; ++i) g.L[i] = R(h.L[i]);
@@ -324,7 +324,7 @@ __device__ __forceinline__ void store_mom(R *__restrict__ mom, int64_t slot, int
 // dout.p[i] = dst.p[i] + noff[i]: the push address of an interior cell.
 // MOM: also store the moments of the input state in mom (the recompute of
 // the adjoint's checkpoint segments).
-template <class S, bool FORCE, bool TRT = false, bool MOM = false>
+template <class S, bool FORCE, int COLL = COLL_BGK, bool MOM = false>
 __global__ void __launch_bounds__(128) k_two_lattice(Geom<typename S::R> g, Dirs<const typename S::T> src,
                                                      Dirs<typename S::T> dst, Dirs<typename S::T> dout,
                                                      typename S::R *__restrict__ mom)
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(128) k_two_lattice(Geom<typename S::R> g, Dirs
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
     if constexpr (MOM) store_mom<R>(mom, g.slot, c, moments_of<R, FORCE>(s, Fx, Fy, Fz));
-    collide_sel<R, FORCE, TRT>(g, s, Fx, Fy, Fz);
+    collide_sel<R, FORCE, COLL>(g, s, Fx, Fy, Fz);
     if (interior(g, x, y, z)) {
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;
@@ -369,7 +369,7 @@ __device__ __forceinline__ void even_outputs(const Geom<typename S::R> &g, int x
     });
 }
 
-template <class S, bool FORCE, bool TRT>
+template <class S, bool FORCE, int COLL>
 __device__ __forceinline__ void aa_even_cell(const Geom<typename S::R> &g, const Dirs<typename S::T> &f, int x, int y,
                                              int z, int c)
 {
@@ -381,7 +381,7 @@ __device__ __forceinline__ void aa_even_cell(const Geom<typename S::R> &g, const
     });
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
-    collide_sel<R, FORCE, TRT>(g, s, Fx, Fy, Fz);
+    collide_sel<R, FORCE, COLL>(g, s, Fx, Fy, Fz);
     even_outputs<S>(g, x, y, z, s);
     static_for<Q>([&](auto K) {
         constexpr int i = decltype(K)::value;
@@ -389,12 +389,12 @@ __device__ __forceinline__ void aa_even_cell(const Geom<typename S::R> &g, const
     });
 }
 
-template <class S, bool FORCE, bool TRT = false>
+template <class S, bool FORCE, int COLL = COLL_BGK>
 __global__ void __launch_bounds__(128) k_aa_even(Geom<typename S::R> g, Dirs<typename S::T> f, int z0)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z + z0;
     if (x >= g.nx) return;
-    aa_even_cell<S, FORCE, TRT>(g, f, x, y, z, cell32(g, x, y, z));
+    aa_even_cell<S, FORCE, COLL>(g, f, x, y, z, cell32(g, x, y, z));
 }
 
 // The even step for 2-byte storage, two neighbouring cells (x, x+1), x even,
@@ -427,7 +427,7 @@ struct Pair2 {
     }
 };
 
-template <class S, bool FORCE, bool TRT = false>
+template <class S, bool FORCE, int COLL = COLL_BGK>
 __global__ void __launch_bounds__(128) k_aa_even_pair(Geom<typename S::R> g, Dirs<typename S::T> f, int z0)
 {
     static_assert(sizeof(typename S::T) == 2 && S::shifted, "2-byte shifted storage");
@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(128) k_aa_even_pair(Geom<typename S::R> g, Dir
     if (x >= g.nx) return;
     const int c = cell32(g, x, y, z);
     if (x + 1 >= g.nx) {  // odd nx: the last cell alone
-        aa_even_cell<S, FORCE, TRT>(g, f, x, y, z, c);
+        aa_even_cell<S, FORCE, COLL>(g, f, x, y, z, c);
         return;
     }
     R a[Q], b[Q];
@@ -446,9 +446,9 @@ __global__ void __launch_bounds__(128) k_aa_even_pair(Geom<typename S::R> g, Dir
     });
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
-    collide_sel<R, FORCE, TRT>(g, a, Fx, Fy, Fz);
+    collide_sel<R, FORCE, COLL>(g, a, Fx, Fy, Fz);
     force_at<R, FORCE>(g, canon(g, x + 1, y, z), ncanon(g), Fx, Fy, Fz);
-    collide_sel<R, FORCE, TRT>(g, b, Fx, Fy, Fz);
+    collide_sel<R, FORCE, COLL>(g, b, Fx, Fy, Fz);
     even_outputs<S>(g, x, y, z, a);
     even_outputs<S>(g, x + 1, y, z, b);
     static_for<Q>([&](auto K) {
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(128) k_aa_even_pair(Geom<typename S::R> g, Dir
 // locations in this sweep, so the update is race-free in place.  Planes
 // z0 .. z0 + gridDim.z - 1.
 // ---------------------------------------------------------------------------
-template <class S, bool FORCE, bool TRT = false>
+template <class S, bool FORCE, int COLL = COLL_BGK>
 __global__ void __launch_bounds__(128) k_aa_odd(Geom<typename S::R> g, Dirs<typename S::T> f, Dirs<typename S::T> fin,
                                                 Dirs<typename S::T> fout, int z0)
 {
@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(128) k_aa_odd(Geom<typename S::R> g, Dirs<type
     }
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
-    collide_sel<R, FORCE, TRT>(g, s, Fx, Fy, Fz);
+    collide_sel<R, FORCE, COLL>(g, s, Fx, Fy, Fz);
     if (in) {
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;

@@ -8,11 +8,27 @@
 
 #include <string.h>
 
+#include <type_traits>
+
 namespace lbm {
 
 constexpr int CELL_BLOCK = 128;
 
 inline dim3 cell_grid(const HostGeom &h) { return dim3((h.nx + CELL_BLOCK - 1) / CELL_BLOCK, h.ny, h.nz); }
+
+// fn(FORCE, COLL) with the runtime force flag and collision operator as
+// compile-time constants (std::integral_constant).
+template <class Fn>
+inline void with_model(bool force, int coll, Fn &&fn)
+{
+    auto pick = [&](auto F) {
+        if (coll == COLL_TRT) fn(F, std::integral_constant<int, COLL_TRT>{});
+        else if (coll == COLL_REG) fn(F, std::integral_constant<int, COLL_REG>{});
+        else fn(F, std::integral_constant<int, COLL_BGK>{});
+    };
+    if (force) pick(std::true_type{});
+    else pick(std::false_type{});
+}
 
 template <class S>
 struct Launch {
@@ -34,13 +50,10 @@ struct Launch {
         const Dirs<T> b = make_dirs((T *)dst, slot_of(h, pitch));
         Dirs<T> bo;  // push addresses of an interior cell, one index away
         for (int i = 0; i < Q; ++i) bo.p[i] = b.p[i] + g.noff[i];
-        if (h.trt) {
-            if (force) k_two_lattice<S, true, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo, nullptr);
-            else k_two_lattice<S, false, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo, nullptr);
-        } else {
-            if (force) k_two_lattice<S, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo, nullptr);
-            else k_two_lattice<S, false><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo, nullptr);
-        }
+        with_model(force, h.coll, [&](auto F, auto C) {
+            k_two_lattice<S, decltype(F)::value, decltype(C)::value>
+                <<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo, nullptr);
+        });
         return cudaGetLastError();
     }
     // the same (BGK), also storing the moments of src in mom (adjoint recompute)
@@ -52,8 +65,8 @@ struct Launch {
         const Dirs<T> b = make_dirs((T *)dst, slot_of(h, pitch));
         Dirs<T> bo;
         for (int i = 0; i < Q; ++i) bo.p[i] = b.p[i] + g.noff[i];
-        if (force) k_two_lattice<S, true, false, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo, (R *)mom);
-        else k_two_lattice<S, false, false, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo, (R *)mom);
+        if (force) k_two_lattice<S, true, COLL_BGK, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo, (R *)mom);
+        else k_two_lattice<S, false, COLL_BGK, true><<<cell_grid(h), CELL_BLOCK, 0, st>>>(g, a, b, bo, (R *)mom);
         return cudaGetLastError();
     }
     static cudaError_t adj_moments(const HostGeom &h, int64_t pitch, bool force, const void *f, void *mom,
@@ -73,22 +86,14 @@ struct Launch {
         const Dirs<T> d = make_dirs((T *)f, slot_of(h, pitch));
         if constexpr (sizeof(T) == 2) {  // two cells per thread (packed 4-byte accesses)
             const dim3 grid((h.nx + 2 * CELL_BLOCK - 1) / (2 * CELL_BLOCK), h.ny, z1 - z0);
-            if (h.trt) {
-                if (force) k_aa_even_pair<S, true, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
-                else k_aa_even_pair<S, false, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
-            } else {
-                if (force) k_aa_even_pair<S, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
-                else k_aa_even_pair<S, false><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
-            }
+            with_model(force, h.coll, [&](auto F, auto C) {
+                k_aa_even_pair<S, decltype(F)::value, decltype(C)::value><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+            });
         } else {
             const dim3 grid((h.nx + CELL_BLOCK - 1) / CELL_BLOCK, h.ny, z1 - z0);
-            if (h.trt) {
-                if (force) k_aa_even<S, true, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
-                else k_aa_even<S, false, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
-            } else {
-                if (force) k_aa_even<S, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
-                else k_aa_even<S, false><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
-            }
+            with_model(force, h.coll, [&](auto F, auto C) {
+                k_aa_even<S, decltype(F)::value, decltype(C)::value><<<grid, CELL_BLOCK, 0, st>>>(g, d, z0);
+            });
         }
         return cudaGetLastError();
     }
@@ -103,13 +108,9 @@ struct Launch {
             dout.p[i] = d.p[i] + g.noff[i];
         }
         const dim3 grid((h.nx + CELL_BLOCK - 1) / CELL_BLOCK, h.ny, z1 - z0);
-        if (h.trt) {
-            if (force) k_aa_odd<S, true, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, din, dout, z0);
-            else k_aa_odd<S, false, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, din, dout, z0);
-        } else {
-            if (force) k_aa_odd<S, true><<<grid, CELL_BLOCK, 0, st>>>(g, d, din, dout, z0);
-            else k_aa_odd<S, false><<<grid, CELL_BLOCK, 0, st>>>(g, d, din, dout, z0);
-        }
+        with_model(force, h.coll, [&](auto F, auto C) {
+            k_aa_odd<S, decltype(F)::value, decltype(C)::value><<<grid, CELL_BLOCK, 0, st>>>(g, d, din, dout, z0);
+        });
         return cudaGetLastError();
     }
     static cudaError_t aa_even(const HostGeom &h, int64_t pitch, bool force, void *f, cudaStream_t st)

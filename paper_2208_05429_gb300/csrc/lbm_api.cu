@@ -269,8 +269,8 @@ HostGeom host_geom(const lbm_config &c)
     for (int k = 0; k < 6; ++k) h.lid[k] = c.face_bc[k] == LBM_BC_LID;
     h.omega = 1.0 / c.tau;
     h.kf = 1.0 - 0.5 * h.omega;
-    h.trt = c.collision == LBM_COLLISION_TRT;
-    h.omega_m = h.trt ? 1.0 / (0.5 + c.trt_lambda / (c.tau - 0.5)) : h.omega;
+    h.coll = c.collision == LBM_COLLISION_TRT ? COLL_TRT : (c.collision == LBM_COLLISION_REG ? COLL_REG : COLL_BGK);
+    h.omega_m = h.coll == COLL_TRT ? 1.0 / (0.5 + c.trt_lambda / (c.tau - 0.5)) : h.omega;
     h.kf_m = 1.0 - 0.5 * h.omega_m;
     for (int k = 0; k < Q; ++k) {
         const double cu = cx(k) * c.u_lid[0] + cy(k) * c.u_lid[1] + cz(k) * c.u_lid[2];
@@ -415,9 +415,10 @@ int lbm_validate(const lbm_config *c)
     if (c->force_mode < LBM_FORCE_NONE || c->force_mode > LBM_FORCE_FIELD) return LBM_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (!isfinite(c->force_uniform[a])) return LBM_EINVAL;
-    if (c->collision != LBM_COLLISION_BGK && c->collision != LBM_COLLISION_TRT) return LBM_EINVAL;
+    if (c->collision != LBM_COLLISION_BGK && c->collision != LBM_COLLISION_TRT && c->collision != LBM_COLLISION_REG)
+        return LBM_EINVAL;
     if (!(c->trt_lambda > 0.0) || !isfinite(c->trt_lambda)) return LBM_EINVAL;
-    if (c->collision == LBM_COLLISION_TRT && c->variant != LBM_VARIANT_AA &&
+    if (c->collision != LBM_COLLISION_BGK && c->variant != LBM_VARIANT_AA &&
         c->variant != LBM_VARIANT_TWO_LATTICE)
         return LBM_EUNSUPPORTED;
     return LBM_OK;

@@ -15,7 +15,7 @@ struct HostGeom {
     int per[3];
     int lid[6];
     double omega, kf;
-    int trt;             // TRT collision
+    int coll;            // collision: 0 BGK, 1 TRT, 2 regularised BGK
     double omega_m, kf_m;
     double L[19];
     double Fu[3];

@@ -27,8 +27,8 @@ LBM_STORAGE_F64, LBM_STORAGE_F32, LBM_STORAGE_F32S, LBM_STORAGE_F16S, LBM_STORAG
 LBM_VARIANT_TWO_LATTICE, LBM_VARIANT_AA, LBM_VARIANT_MERGED = 0, 1, 2
 LBM_FORCE_NONE, LBM_FORCE_UNIFORM, LBM_FORCE_FIELD = 0, 1, 2
 LBM_DTYPE_F32, LBM_DTYPE_F64 = 0, 1
-LBM_COLLISION_BGK, LBM_COLLISION_TRT = 0, 1
-COLLISION = {"bgk": LBM_COLLISION_BGK, "trt": LBM_COLLISION_TRT}
+LBM_COLLISION_BGK, LBM_COLLISION_TRT, LBM_COLLISION_REG = 0, 1, 2
+COLLISION = {"bgk": LBM_COLLISION_BGK, "trt": LBM_COLLISION_TRT, "reg": LBM_COLLISION_REG}
 LBM_KERNEL_TWO_LATTICE, LBM_KERNEL_AA_EVEN, LBM_KERNEL_AA_ODD, LBM_KERNEL_SNAPSHOT, LBM_KERNEL_MERGED = \
     0, 1, 2, 3, 4
 KERNELS = {"two_lattice": LBM_KERNEL_TWO_LATTICE, "aa_even": LBM_KERNEL_AA_EVEN, "aa_odd": LBM_KERNEL_AA_ODD,

@@ -64,7 +64,8 @@ def make_gpu(cfg: "oracle.Config", storage: str, variant: str, device="cuda:0") 
         force = None
     return Lattice((cfg.nx, cfg.ny, cfg.nz), cfg.tau, bc=tuple(int(b) for b in cfg.bc), u_lid=tuple(cfg.u_lid),
                    rho_wall=cfg.rho_wall, storage=storage, variant=variant, force=force, device=device,
-                   collision="trt" if cfg.collision == oracle.COLL_TRT else "bgk", trt_lambda=cfg.trt_lambda)
+                   collision={oracle.COLL_TRT: "trt", oracle.COLL_REG: "reg"}.get(cfg.collision, "bgk"),
+                   trt_lambda=cfg.trt_lambda)
 
 
 def oracle_force_as_f32(cfg: "oracle.Config") -> "oracle.Config":

@@ -45,7 +45,7 @@ def test_default_config_valid(cuda_lib):
 @pytest.mark.parametrize("field,value", [
     ("nx", 0), ("ny", -3), ("nz", 70000), ("tau", 0.5), ("tau", float("nan")), ("rho_wall", 0.0),
     ("storage", 9), ("variant", 3), ("variant", 4), ("force_mode", 5),
-    ("collision", 2), ("trt_lambda", 0.0), ("trt_lambda", float("inf")),
+    ("collision", 3), ("collision", -1), ("trt_lambda", 0.0), ("trt_lambda", float("inf")),
 ])
 def test_invalid_configs_rejected(cuda_lib, field, value):
     cfg = lbm.lbm_config_default()
@@ -77,10 +77,11 @@ def test_required_bytes_scale(cuda_lib):
     assert pop // 2 <= lbm.lbm_required_bytes(h16) < pop
 
 
-def test_trt_only_on_aa_and_two_lattice(cuda_lib):
+def test_trt_and_reg_only_on_aa_and_two_lattice(cuda_lib):
     for variant, want in (("aa", lbm.LBM_OK), ("two_lattice", lbm.LBM_OK), ("merged", lbm.LBM_EUNSUPPORTED)):
-        cfg = lbm.make_config((16, 16, 16), 0.7, lbm.CAVITY_BC, storage="f32", variant=variant, collision="trt")
-        assert lbm.lbm_validate(cfg) == want, variant
+        for coll in ("trt", "reg"):
+            cfg = lbm.make_config((16, 16, 16), 0.7, lbm.CAVITY_BC, storage="f32", variant=variant, collision=coll)
+            assert lbm.lbm_validate(cfg) == want, (variant, coll)
     assert lbm.lbm_config_default().collision == lbm.LBM_COLLISION_BGK
 
 
