@@ -679,7 +679,8 @@ def main():
                              ("f32", "merged", "shadow"), ("f32s", "merged", None),
                              ("f16s", "merged", None), ("f16s", "aa", None), ("bf16s", "merged", None),
                              ("bf16s", "aa", None), ("f64", "aa", None), ("f32", "aa", "trt"),
-                             ("f16s", "aa", "trt"), ("f32", "aa", "reg"), ("f16s", "aa", "reg")):
+                             ("f16s", "aa", "trt"), ("f32", "aa", "reg"), ("f16s", "aa", "reg"),
+                             ("f32", "merged", "trt"), ("f32", "merged", "reg")):
             if (st, var, env) == (args.storage, args.variant, None):
                 continue
             k = min(args.steps, 300)

@@ -113,9 +113,10 @@ enum { LBM_FORCE_NONE = 0, LBM_FORCE_UNIFORM = 1, LBM_FORCE_FIELD = 2 };
  * w_i (3 c_i.J + 4.5 (c_i c_i - I/3) : Pi) with J, Pi its first and second
  * moments, which removes the higher ("ghost") moments.  (The paper's solver
  * builds on "collision models" without naming one, Sec. 1; the schedules of
- * Sec. 3-4 are independent of the model.)  TRT and REG run on the AA and
- * TWO_LATTICE schedules; with MERGED, and for the adjoint, lbm_validate / the
- * adjoint calls return LBM_EUNSUPPORTED. */
+ * Sec. 3-4 are independent of the model.)  Every schedule runs all three;
+ * MERGED runs TRT and REG with the neighbour-synchronised sweep where that
+ * can run and as the AA pair elsewhere (the shadow-shell sweep is BGK only).
+ * The adjoint calls return LBM_EUNSUPPORTED for a handle without BGK. */
 enum { LBM_COLLISION_BGK = 0, LBM_COLLISION_TRT = 1, LBM_COLLISION_REG = 2 };
 
 /* Element type of caller-provided field buffers. */
@@ -143,9 +144,7 @@ void lbm_config_default(lbm_config *cfg);
  * cell count beyond 2^31, tau <= 0.5, a face type out of range, an axis with
  * one periodic and one non-periodic face, |u_lid| >= 0.3, rho_wall <= 0,
  * unknown storage/variant/force mode or collision, or a trt_lambda that is
- * not positive and finite.
- * LBM_EUNSUPPORTED for the TRT or REG collision with a schedule other than AA
- * and TWO_LATTICE. */
+ * not positive and finite. */
 int lbm_validate(const lbm_config *cfg);
 
 /* Device bytes a handle of this configuration uses (populations, second

@@ -239,7 +239,7 @@ struct Launch {
     // neighbour-synchronised merged sweep: 4- and 2-byte storage, 32 x 14 tiles
     static constexpr int NS_TY = 14;
     static constexpr bool HAS_NS = sizeof(T) < 8;
-    template <bool F>
+    template <bool F, int C>
     static cudaError_t nsweep_f(const HostGeom &h, int64_t pitch, void *f, const ShellInfo &si, int *prog,
                                 const void *tmap, int *status, cudaStream_t st)
     {
@@ -251,7 +251,7 @@ struct Launch {
             constexpr size_t smem = NSM::bytes;
             static bool attr_set = false;  // once per process: not inside a stream capture
             if (!attr_set) {
-                const cudaError_t e = cudaFuncSetAttribute(k_nsweep<S, F, NS_TY>,
+                const cudaError_t e = cudaFuncSetAttribute(k_nsweep<S, F, NS_TY, C>,
                                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e != cudaSuccess) return e;
                 attr_set = true;
@@ -273,23 +273,27 @@ struct Launch {
             attr[0].val.cooperative = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            return cudaLaunchKernelEx(&cfg, k_nsweep<S, F, NS_TY>, map, g, fd, fo, si, prog, status);
+            return cudaLaunchKernelEx(&cfg, k_nsweep<S, F, NS_TY, C>, map, g, fd, fo, si, prog, status);
         }
     }
     static cudaError_t nsweep(const HostGeom &h, int64_t pitch, bool force, void *f, const ShellInfo &si, int *prog,
                               const void *tmap, int *status, cudaStream_t st)
     {
-        return force ? nsweep_f<true>(h, pitch, f, si, prog, tmap, status, st)
-                     : nsweep_f<false>(h, pitch, f, si, prog, tmap, status, st);
+        cudaError_t e = cudaSuccess;
+        with_model(force, h.coll, [&](auto F, auto C) {
+            e = nsweep_f<decltype(F)::value, decltype(C)::value>(h, pitch, f, si, prog, tmap, status, st);
+        });
+        return e;
     }
     // CTAs of the sweep one SM holds (0 where it does not exist or fit)
-    static int nsweep_ctas_per_sm(bool force)
+    static int nsweep_ctas_per_sm(bool force, int coll)
     {
         if constexpr (!HAS_NS) {
             return 0;
         } else {
             constexpr size_t smem = NSSmem<NS_TY, T, R>::bytes;
-            auto kern = force ? k_nsweep<S, true, NS_TY> : k_nsweep<S, false, NS_TY>;
+            decltype(&k_nsweep<S, false, NS_TY, COLL_BGK>) kern = nullptr;
+            with_model(force, coll, [&](auto F, auto C) { kern = k_nsweep<S, decltype(F)::value, NS_TY, decltype(C)::value>; });
             if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
                 cudaGetLastError();
                 return 0;

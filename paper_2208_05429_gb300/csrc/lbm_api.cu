@@ -145,6 +145,12 @@ int sm_count();
 // environment variable LBM_MERGED_SWEEP=shadow selects the shadow-shell
 // sweep instead, LBM_MERGED_SWEEP=neighbour this one whenever it can run
 // (any tile count up to the resident limit).
+// The kernels' collision variant (COLL_*) of a configuration.
+int coll_of(const lbm_config &c)
+{
+    return c.collision == LBM_COLLISION_TRT ? COLL_TRT : (c.collision == LBM_COLLISION_REG ? COLL_REG : COLL_BGK);
+}
+
 bool uses_ns(const lbm_config &c, const ShellInfo &si)
 {
     if (c.variant != LBM_VARIANT_MERGED) return false;
@@ -158,7 +164,7 @@ bool uses_ns(const lbm_config &c, const ShellInfo &si)
     const StorageOps *o = ops_for(c.storage);
     if (!o->nsweep || o->ns_ty != o->m3_ty) return false;
     const int64_t tiles = (int64_t)si.ntx * si.nty, sms = sm_count();
-    const int per = o->nsweep_ctas_per_sm(c.force_mode != LBM_FORCE_NONE);
+    const int per = o->nsweep_ctas_per_sm(c.force_mode != LBM_FORCE_NONE, coll_of(c));
     return per > 0 && tiles <= (int64_t)per * sms && (any_count || 2 * tiles >= sms);
 }
 
@@ -167,6 +173,8 @@ bool uses_m3(const lbm_config &c, const ShellInfo &si)
 {
     if (c.variant != LBM_VARIANT_MERGED) return false;
     if (uses_ns(c, si)) return false;
+    // the shadow-shell sweep is built for BGK only
+    if (c.collision != LBM_COLLISION_BGK) return false;
     if (c.face_bc[4] == LBM_BC_PERIODIC && c.nz < 2) return false;
     // the sweep indexes one shadow copy with 32-bit offsets
     return (double)si.gplane * (double)c.nz < 2147483647.0;
@@ -269,7 +277,7 @@ HostGeom host_geom(const lbm_config &c)
     for (int k = 0; k < 6; ++k) h.lid[k] = c.face_bc[k] == LBM_BC_LID;
     h.omega = 1.0 / c.tau;
     h.kf = 1.0 - 0.5 * h.omega;
-    h.coll = c.collision == LBM_COLLISION_TRT ? COLL_TRT : (c.collision == LBM_COLLISION_REG ? COLL_REG : COLL_BGK);
+    h.coll = coll_of(c);
     h.omega_m = h.coll == COLL_TRT ? 1.0 / (0.5 + c.trt_lambda / (c.tau - 0.5)) : h.omega;
     h.kf_m = 1.0 - 0.5 * h.omega_m;
     for (int k = 0; k < Q; ++k) {
@@ -418,9 +426,6 @@ int lbm_validate(const lbm_config *c)
     if (c->collision != LBM_COLLISION_BGK && c->collision != LBM_COLLISION_TRT && c->collision != LBM_COLLISION_REG)
         return LBM_EINVAL;
     if (!(c->trt_lambda > 0.0) || !isfinite(c->trt_lambda)) return LBM_EINVAL;
-    if (c->collision != LBM_COLLISION_BGK && c->variant != LBM_VARIANT_AA &&
-        c->variant != LBM_VARIANT_TWO_LATTICE)
-        return LBM_EUNSUPPORTED;
     return LBM_OK;
 }
 

@@ -79,7 +79,7 @@ struct NSSmem {
 constexpr int NS_POLL_LIMIT = 1 << 21;
 constexpr int NS_STATUS_BIT = 8;
 
-template <class S, bool FORCE, int TY>
+template <class S, bool FORCE, int TY, int COLL = COLL_BGK>
 struct NSCta {
     using R = typename S::R;
     using T = typename S::T;
@@ -212,7 +212,7 @@ struct NSCta {
         });
         R Fx, Fy, Fz;
         force_at<R, FORCE>(g, canon(g, x, y, p), ncanon(g), Fx, Fy, Fz);
-        bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
+        collide_sel<R, FORCE, COLL>(g, s, Fx, Fy, Fz);
         // value that leaves along c_i as the next step reads it: + L_opp(i)
         // on a wall link that ends on a lid (the lid takes precedence)
         const unsigned lm = lxy | (p == 0 && g.lid[4] ? CZM : 0u) | (p == nz - 1 && g.lid[5] ? CZP : 0u);
@@ -320,7 +320,7 @@ struct NSCta {
         }
         R Fx, Fy, Fz;
         force_at<R, FORCE>(g, canon(g, x, y, k), ncanon(g), Fx, Fy, Fz);
-        bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
+        collide_sel<R, FORCE, COLL>(g, s, Fx, Fy, Fz);
     }
 
     // Push the odd-step result of plane k: slot i of x + c_i, or (wall link)
@@ -376,12 +376,12 @@ __device__ __forceinline__ int ns_load_relaxed(const int *p)
     return v;
 }
 
-template <class S, bool FORCE, int TY>
+template <class S, bool FORCE, int TY, int COLL = COLL_BGK>
 __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
     k_nsweep(const __grid_constant__ CUtensorMap tmap, Geom<typename S::R> g, Dirs<typename S::T> fd,
              Dirs<typename S::T> fo, ShellInfo si, int *__restrict__ prog, int *__restrict__ status)
 {
-    using C = NSCta<S, FORCE, TY>;
+    using C = NSCta<S, FORCE, TY, COLL>;
     using L = typename C::L;
     using SM = typename C::SM;
     using R = typename S::R;

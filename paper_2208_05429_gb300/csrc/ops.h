@@ -84,7 +84,7 @@ struct StorageOps {
     // directions.  nsweep is null where the format has no such sweep (FP64).
     cudaError_t (*nsweep)(const HostGeom &, int64_t pitch, bool force, void *f, const ShellInfo &, int *prog,
                           const void *tmap, int *status, cudaStream_t);
-    int (*nsweep_ctas_per_sm)(bool force);
+    int (*nsweep_ctas_per_sm)(bool force, int coll);  // coll: COLL_* of the kernel variant
     int ns_ty, ns_box_w, ns_margin;
     // lam_* are arrays of the compute type with the given pitch
     cudaError_t (*adjoint)(const HostGeom &, int64_t pitch, bool force, const void *f, const void *lam_in,

@@ -75,9 +75,39 @@ def test_reg_differs_from_bgk_on_gpu(gpu):
     assert relmax(gpu_state(lat_r), gpu_state(lat_b)) > 1e-6
 
 
-def test_reg_rejected_on_merged(gpu):
-    from paper_2208_05429_gb300.lbm import LBM_EUNSUPPORTED, LbmError
-    cfg = _reg(oracle.cavity(16, 0.6))
-    with pytest.raises(LbmError) as ei:
-        make_gpu(cfg, "f32", "merged")
-    assert ei.value.status == LBM_EUNSUPPORTED
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+@pytest.mark.parametrize("name", ["cavity16", "mixed_33x40x9", "channel_37x19x23"])
+def test_reg_merged_equals_aa(gpu, monkeypatch, storage, name):
+    """MERGED with the regularised collision: the neighbour-synchronised
+    sweep where it runs (the walled cavity), else the AA pair; bit-identical
+    to AA either way, including an odd step count."""
+    import torch
+    cfg = _reg(oracle_force_as_f32(cases()[name]))
+    f0 = start_state(cfg, seed=9)
+    a = make_gpu(cfg, storage, "aa")
+    load_state(a, f0)
+    a.step(7)
+    for sweep in ("neighbour", "shadow"):
+        monkeypatch.setenv("LBM_MERGED_SWEEP", sweep)
+        m = make_gpu(cfg, storage, "merged")
+        monkeypatch.delenv("LBM_MERGED_SWEEP")
+        load_state(m, f0)
+        m.profile(True)
+        m.step(7)
+        ran = m.profile_read()
+        m.profile(False)
+        if name == "cavity16" and sweep == "neighbour":
+            assert "merged" in ran, ran
+        assert torch.equal(m.populations(torch.float64), a.populations(torch.float64)), (sweep, ran)
+
+
+def test_reg_merged_fp64_against_oracle(gpu):
+    """FP64 MERGED with the regularised collision (the AA pair: FP64 has no
+    neighbour-synchronised sweep) against the oracle, 1e-12."""
+    cfg = _reg(oracle_force_as_f32(cases()["mixed_33x40x9"]))
+    f0 = start_state(cfg, seed=11)
+    ref = oracle.run(cfg, f0, 6)
+    lat = make_gpu(cfg, "f64", "merged")
+    load_state(lat, f0)
+    lat.step(6)
+    assert relmax(gpu_state(lat), ref) <= 1e-12

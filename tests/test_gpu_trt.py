@@ -84,9 +84,27 @@ def test_trt_poiseuille_exact_on_gpu(gpu):
     assert np.max(np.abs(u[0, 0, :, 1] - exact)) / np.max(exact) < 1e-9
 
 
-def test_trt_rejected_where_not_built(gpu):
-    from paper_2208_05429_gb300.lbm import LBM_EUNSUPPORTED, LbmError
-    cfg = _trt(oracle.cavity(16, 0.6), 0.1)
-    with pytest.raises(LbmError) as ei:
-        make_gpu(cfg, "f32", "merged")
-    assert ei.value.status == LBM_EUNSUPPORTED
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+@pytest.mark.parametrize("name", ["cavity16", "mixed_33x40x9", "channel_37x19x23"])
+def test_trt_merged_equals_aa(gpu, monkeypatch, storage, name):
+    """MERGED with TRT: the neighbour-synchronised sweep where it runs (the
+    walled cavity), else the AA pair (the shadow-shell sweep is BGK only);
+    bit-identical to AA either way, including an odd step count."""
+    import torch
+    cfg = _trt(oracle_force_as_f32(cases()[name]), 0.1)
+    f0 = start_state(cfg, seed=7)
+    a = make_gpu(cfg, storage, "aa")
+    load_state(a, f0)
+    a.step(7)
+    for sweep in ("neighbour", "shadow"):
+        monkeypatch.setenv("LBM_MERGED_SWEEP", sweep)
+        m = make_gpu(cfg, storage, "merged")
+        monkeypatch.delenv("LBM_MERGED_SWEEP")
+        load_state(m, f0)
+        m.profile(True)
+        m.step(7)
+        ran = m.profile_read()
+        m.profile(False)
+        if name == "cavity16" and sweep == "neighbour":
+            assert "merged" in ran, ran
+        assert torch.equal(m.populations(torch.float64), a.populations(torch.float64)), (sweep, ran)
