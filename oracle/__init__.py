@@ -34,7 +34,7 @@ import numpy as np
 Q = 19
 BC_PERIODIC, BC_WALL, BC_LID = 0, 1, 2
 FORCE_NONE, FORCE_UNIFORM, FORCE_FIELD = 0, 1, 2
-COLL_BGK, COLL_TRT, COLL_REG = 0, 1, 2
+COLL_BGK, COLL_TRT, COLL_REG, COLL_MRT = 0, 1, 2, 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
@@ -70,6 +70,8 @@ class _Cfg(ctypes.Structure):
         ("force_field", ctypes.POINTER(ctypes.c_double)),
         ("collision", ctypes.c_int32),
         ("trt_lambda", ctypes.c_double),
+        ("mrt_s3", ctypes.c_double),
+        ("mrt_s4", ctypes.c_double),
     ]
 
 
@@ -89,6 +91,7 @@ def _load():
                 "orc_collide_cell": [ctypes.c_double, _D, _D, _D],
                 "orc_collide_cell_trt": [ctypes.c_double, ctypes.c_double, _D, _D, _D],
                 "orc_collide_cell_reg": [ctypes.c_double, _D, _D, _D],
+                "orc_collide_cell_mrt": [ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D, _D],
                 "orc_init_equilibrium": [P, _D, _D, _D],
                 "orc_step": [P, _D, _D],
                 "orc_run": [P, _D, ctypes.c_int64, _D],
@@ -133,8 +136,10 @@ class Config:
     force_mode: int = FORCE_NONE
     force_uniform: Sequence[float] = (0.0, 0.0, 0.0)
     force_field: Optional[np.ndarray] = field(default=None, repr=False)
-    collision: int = 0            # COLL_BGK, COLL_TRT or COLL_REG
+    collision: int = 0            # COLL_BGK, COLL_TRT, COLL_REG or COLL_MRT
     trt_lambda: float = 3.0 / 16.0
+    mrt_s3: float = 1.0           # MRT rates of the third- and fourth-order moments
+    mrt_s4: float = 1.0
 
     @property
     def shape(self):
@@ -157,6 +162,8 @@ class Config:
         c.force_mode = int(self.force_mode)
         c.collision = int(self.collision)
         c.trt_lambda = float(self.trt_lambda)
+        c.mrt_s3 = float(self.mrt_s3)
+        c.mrt_s4 = float(self.mrt_s4)
         if self.force_mode == FORCE_FIELD:
             ff = np.ascontiguousarray(self.force_field, dtype=np.float64).reshape(3, *self.shape)
             self._ff_keep = ff  # keep the buffer alive for the call
@@ -187,6 +194,15 @@ def equilibrium(rho: float, u) -> np.ndarray:
     uu = np.ascontiguousarray(u, dtype=np.float64)
     out = np.zeros(Q, np.float64)
     lib.orc_equilibrium(float(rho), _ptr(uu), _ptr(out))
+    return out
+
+
+def collide_cell_mrt(tau: float, s3: float, s4: float, f, F=(0.0, 0.0, 0.0)) -> np.ndarray:
+    lib = _load()
+    ff = np.ascontiguousarray(f, dtype=np.float64)
+    FF = np.ascontiguousarray(F, dtype=np.float64)
+    out = np.zeros(Q, np.float64)
+    lib.orc_collide_cell_mrt(float(tau), float(s3), float(s4), _ptr(ff), _ptr(FF), _ptr(out))
     return out
 
 

@@ -39,7 +39,9 @@
  *                f*_i  = feq_i + (1 - omega) w_i (3 c_i . J + (9/2) Q_i : Pi)
  *                        + (1 - omega/2) S_i
  *              with J = sum_i (f_i - feq_i) c_i, Pi = sum_i (f_i - feq_i) c_i c_i
- *              and Q_i = c_i c_i - I/3.
+ *              and Q_i = c_i c_i - I/3; or a multiple-relaxation-time form
+ *              that relaxes the Hermite moments of f - feq of order three
+ *              and four with rates s3 and s4 (orc_collide_cell_mrt).
  *   streaming  f_i(x + c_i, t+1) = f*_i(x); periodic axes wrap; a link that
  *              leaves the box across a non-periodic face is a wall link
  *              (half-way bounce-back):
@@ -69,7 +71,7 @@
 
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_LID = 2 };
 enum { FORCE_NONE = 0, FORCE_UNIFORM = 1, FORCE_FIELD = 2 };
-enum { COLL_BGK = 0, COLL_TRT = 1, COLL_REG = 2 };
+enum { COLL_BGK = 0, COLL_TRT = 1, COLL_REG = 2, COLL_MRT = 3 };
 
 /* The D3Q19 velocity set in the half-neighbour order described above. */
 static const int C[Q][3] = {
@@ -99,8 +101,9 @@ typedef struct {
     int32_t force_mode;
     double force_uniform[3];
     const double *force_field; /* [3][N] canonical, used when FORCE_FIELD */
-    int32_t collision;         /* COLL_BGK, COLL_TRT or COLL_REG */
+    int32_t collision;         /* COLL_BGK, COLL_TRT, COLL_REG or COLL_MRT */
     double trt_lambda;         /* Lambda of the TRT form */
+    double mrt_s3, mrt_s4;     /* MRT: rates of the third- and fourth-order moments */
 } orc_cfg;
 
 static int64_t ncells(const orc_cfg *g) { return g->nx * g->ny * g->nz; }
@@ -273,11 +276,91 @@ void orc_collide_cell_reg(double tau, const double *f, const double *F, double *
     }
 }
 
+/* Multiple-relaxation-time collision of one cell in Hermite moments.  The
+ * 19 functions of c
+ *   1;  x, y, z;  xx-1/3, yy-1/3, zz-1/3, xy, xz, yz;
+ *   xxy-y/3, xxz-z/3, xyy-x/3, yyz-z/3, xzz-x/3, yzz-y/3;
+ *   (xx-1/3)(yy-1/3), (xx-1/3)(zz-1/3), (yy-1/3)(zz-1/3)
+ * are made orthogonal in sum_i w_i a(c_i) b(c_i) by Gram-Schmidt in this
+ * order (on D3Q19 the fourth-order ones are not orthogonal to the second-order
+ * ones, nor the third-order ones to each other), giving H_p with norms N_p and
+ * orders 0 .. 4.  The non-equilibrium part n = f - feq is expanded as
+ * n_i = w_i sum_p (sum_j H_p(c_j) n_j) H_p(c_i) / N_p, the part of order k is
+ * relaxed with rate s_k (omega = 1/tau up to second order, s3, s4 above it):
+ *   f*_i = feq_i + sum_p (1 - s_order(p)) w_i b_p H_p(c_i) / N_p + (1 - omega/2) S_i.
+ * s3 = s4 = omega gives BGK, s3 = s4 = 1 the regularised form, and (without a
+ * force) s3 = omega-, s4 = omega the TRT form. */
+static double mrt_H[Q][Q], mrt_N[Q];  /* basis H_p(c_i) and norms */
+static int mrt_order[Q];
+static int mrt_ready;
+
+static void mrt_basis(void)
+{
+    if (mrt_ready) return;
+    for (int i = 0; i < Q; ++i) {
+        const double x = C[i][0], y = C[i][1], z = C[i][2], t = 1.0 / 3.0;
+        const double v[Q] = {1.0, x, y, z, x * x - t, y * y - t, z * z - t, x * y, x * z, y * z,
+                             x * x * y - y * t, x * x * z - z * t, x * y * y - x * t, y * y * z - z * t,
+                             x * z * z - x * t, y * z * z - y * t, (x * x - t) * (y * y - t),
+                             (x * x - t) * (z * z - t), (y * y - t) * (z * z - t)};
+        for (int p = 0; p < Q; ++p) mrt_H[p][i] = v[p];
+    }
+    static const int order[Q] = {0, 1, 1, 1, 2, 2, 2, 2, 2, 2, 3, 3, 3, 3, 3, 3, 4, 4, 4};
+    for (int p = 0; p < Q; ++p) {
+        mrt_order[p] = order[p];
+        for (int q = 0; q < p; ++q) {
+            double d = 0.0;
+            for (int i = 0; i < Q; ++i) d += W[i] * mrt_H[p][i] * mrt_H[q][i];
+            for (int i = 0; i < Q; ++i) mrt_H[p][i] -= d / mrt_N[q] * mrt_H[q][i];
+        }
+        double nn = 0.0;
+        for (int i = 0; i < Q; ++i) nn += W[i] * mrt_H[p][i] * mrt_H[p][i];
+        mrt_N[p] = nn;
+    }
+    mrt_ready = 1;
+}
+
+void orc_collide_cell_mrt(double tau, double s3, double s4, const double *f, const double *F, double *fstar)
+{
+    mrt_basis();
+    double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < Q; ++i) {
+        rho += f[i];
+        for (int a = 0; a < 3; ++a) m[a] += f[i] * C[i][a];
+    }
+    double u[3];
+    for (int a = 0; a < 3; ++a) u[a] = (m[a] + 0.5 * F[a]) / rho;
+    const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+    const double omega = 1.0 / tau;
+    double feq[Q], S[Q], n[Q], b[Q];
+    for (int i = 0; i < Q; ++i) {
+        const double cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
+        const double cF = C[i][0] * F[0] + C[i][1] * F[1] + C[i][2] * F[2];
+        feq[i] = W[i] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+        S[i] = W[i] * (3.0 * (cF - uF) + 9.0 * cu * cF);
+        n[i] = f[i] - feq[i];
+    }
+    for (int p = 0; p < Q; ++p) {
+        b[p] = 0.0;
+        for (int i = 0; i < Q; ++i) b[p] += mrt_H[p][i] * n[i];
+    }
+    for (int i = 0; i < Q; ++i) {
+        double r = 0.0;
+        for (int p = 0; p < Q; ++p) {
+            const double sp = mrt_order[p] <= 2 ? omega : (mrt_order[p] == 3 ? s3 : s4);
+            r += (1.0 - sp) * W[i] * b[p] * mrt_H[p][i] / mrt_N[p];
+        }
+        fstar[i] = feq[i] + r + (1.0 - 0.5 * omega) * S[i];
+    }
+}
+
 /* The collision the configuration selects. */
 static void collide_cfg(const orc_cfg *g, const double *f, const double *F, double *fstar)
 {
     if (g->collision == COLL_TRT) orc_collide_cell_trt(g->tau, g->trt_lambda, f, F, fstar);
     else if (g->collision == COLL_REG) orc_collide_cell_reg(g->tau, f, F, fstar);
+    else if (g->collision == COLL_MRT) orc_collide_cell_mrt(g->tau, g->mrt_s3, g->mrt_s4, f, F, fstar);
     else orc_collide_cell(g->tau, f, F, fstar);
 }
 
@@ -303,6 +386,7 @@ void orc_init_equilibrium(const orc_cfg *g, const double *rho, const double *u, 
 /* One time step, f_in -> f_out (two lattices, f_out fully overwritten). */
 void orc_step(const orc_cfg *g, const double *f_in, double *f_out)
 {
+    if (g->collision == COLL_MRT) mrt_basis();  /* once, before the threads read it */
     const int64_t n = ncells(g);
 #pragma omp parallel for schedule(static)
     for (int64_t z = 0; z < g->nz; ++z)
@@ -331,6 +415,7 @@ void orc_step(const orc_cfg *g, const double *f_in, double *f_out)
  * cells of a large lattice can be checked without stepping all of it. */
 void orc_step_cells(const orc_cfg *g, const double *f_in, const int64_t *xyz, int64_t count, double *out)
 {
+    if (g->collision == COLL_MRT) mrt_basis();
     const int64_t n = ncells(g);
     for (int64_t k = 0; k < count; ++k) {
         const int64_t x = xyz[3 * k], y = xyz[3 * k + 1], z = xyz[3 * k + 2];
