@@ -680,11 +680,12 @@ def main():
                              ("f16s", "merged", None), ("f16s", "aa", None), ("bf16s", "merged", None),
                              ("bf16s", "aa", None), ("f64", "aa", None), ("f32", "aa", "trt"),
                              ("f16s", "aa", "trt"), ("f32", "aa", "reg"), ("f16s", "aa", "reg"),
-                             ("f32", "merged", "trt"), ("f32", "merged", "reg")):
+                             ("f32", "merged", "trt"), ("f32", "merged", "reg"), ("f32", "aa", "mrt"),
+                             ("f32", "merged", "mrt")):
             if (st, var, env) == (args.storage, args.variant, None):
                 continue
             k = min(args.steps, 300)
-            coll = env if env in ("trt", "reg") else "bgk"
+            coll = env if env in ("trt", "reg", "mrt") else "bgk"
             vms, vprof, vl = time_variant(n, st, var, k, 5, sweep_env=None if coll != "bgk" else env,
                                           collision=coll)
             del vl

@@ -111,13 +111,16 @@ enum { LBM_FORCE_NONE = 0, LBM_FORCE_UNIFORM = 1, LBM_FORCE_FIELD = 2 };
  * REG (regularised BGK): before relaxing with 1/tau, f - feq is replaced by
  * its projection on the Hermite polynomials up to second order,
  * w_i (3 c_i.J + 4.5 (c_i c_i - I/3) : Pi) with J, Pi its first and second
- * moments, which removes the higher ("ghost") moments.  (The paper's solver
+ * moments, which removes the higher ("ghost") moments.  MRT: f - feq is split
+ * into its parts of Hermite order up to two, three and four (orthogonal in
+ * sum_i w_i a_i b_i on D3Q19), relaxed with 1/tau, mrt_s3 and mrt_s4
+ * (mrt_s3 = mrt_s4 = 1/tau is BGK, = 1 is REG).  (The paper's solver
  * builds on "collision models" without naming one, Sec. 1; the schedules of
  * Sec. 3-4 are independent of the model.)  Every schedule runs all three;
  * MERGED runs TRT and REG with the neighbour-synchronised sweep where that
  * can run and as the AA pair elsewhere (the shadow-shell sweep is BGK only).
  * The adjoint calls return LBM_EUNSUPPORTED for a handle without BGK. */
-enum { LBM_COLLISION_BGK = 0, LBM_COLLISION_TRT = 1, LBM_COLLISION_REG = 2 };
+enum { LBM_COLLISION_BGK = 0, LBM_COLLISION_TRT = 1, LBM_COLLISION_REG = 2, LBM_COLLISION_MRT = 3 };
 
 /* Element type of caller-provided field buffers. */
 enum { LBM_DTYPE_F32 = 0, LBM_DTYPE_F64 = 1 };
@@ -134,17 +137,20 @@ typedef struct lbm_config {
     double force_uniform[3];  /* the force of LBM_FORCE_UNIFORM                */
     int32_t collision;        /* LBM_COLLISION_* (default BGK)                  */
     double trt_lambda;        /* TRT magic product, > 0 (default 3/16)          */
+    double mrt_s3, mrt_s4;    /* MRT rates of the third- and fourth-order
+                                 moments, in (0, 2) (default 1)                 */
 } lbm_config;
 
 /* Fill cfg with a 32^3 fully periodic FP32 AA lattice, tau = 0.6, BGK
- * (trt_lambda = 3/16 for a later switch to TRT). */
+ * (trt_lambda = 3/16 and mrt_s3 = mrt_s4 = 1 for a later switch to TRT or
+ * MRT). */
 void lbm_config_default(lbm_config *cfg);
 
 /* Check a configuration without allocating.  LBM_EINVAL on: a dimension < 1,
  * cell count beyond 2^31, tau <= 0.5, a face type out of range, an axis with
  * one periodic and one non-periodic face, |u_lid| >= 0.3, rho_wall <= 0,
- * unknown storage/variant/force mode or collision, or a trt_lambda that is
- * not positive and finite. */
+ * unknown storage/variant/force mode or collision, a trt_lambda that is not
+ * positive and finite, or an MRT rate outside (0, 2). */
 int lbm_validate(const lbm_config *cfg);
 
 /* Device bytes a handle of this configuration uses (populations, second

@@ -24,8 +24,8 @@ namespace lbm {
 constexpr int Q = 19;
 
 // Collision operators (kernel template argument): BGK, two relaxation times,
-// regularised BGK.
-enum { COLL_BGK = 0, COLL_TRT = 1, COLL_REG = 2 };
+// regularised BGK, multiple relaxation times in Hermite moments.
+enum { COLL_BGK = 0, COLL_TRT = 1, COLL_REG = 2, COLL_MRT = 3 };
 
 // ---------------------------------------------------------------------------
 // D3Q19 velocity set.  Directions 1..9 have -1 as their first non-zero
@@ -544,6 +544,139 @@ __device__ __forceinline__ void reg_collide(R (&s)[Q], R omega, R kf, R Fx, R Fy
     });
 }
 
+// Multiple relaxation times in Hermite moments, on shifted values.  The
+// non-equilibrium part n_i = s_i - seq_i splits into orthogonal parts (in
+// sum_i w_i a_i b_i) by Hermite order: f1 (orders 1 and 2, as in
+// reg_collide), P3 (order 3) and P4 = n - f1 - P3 (order 4; order 0 is zero),
+// relaxed with omega, s3 and s4:
+//   s_i <- seq_i + (1 - omega) f1_i + (1 - s3) P3_i + (1 - s4) P4_i + kf S_i.
+// On D3Q19 the third-order space is spanned by three orthogonal pairs of odd
+// functions (u, v) = (a + b, a - b) of the Hermite polynomials
+// a = xxy - y/3, b = yzz - y/3 and their permutations,
+//   u1 = y (x^2 + z^2 - 2/3), v1 = y (x^2 - z^2),
+//   u2 = z (x^2 + y^2 - 2/3), v2 = z (x^2 - y^2),
+//   u3 = x (y^2 + z^2 - 2/3), v3 = x (y^2 - z^2),
+// with norms sum_i w_i u^2 = 2/27 and sum_i w_i v^2 = 2/9, so that
+// P3_i = w_i sum (b_u u(c_i) 27/2 + b_v v(c_i) 9/2), b_u = sum_j u(c_j) n_j.
+template <int I>
+__host__ __device__ constexpr double mrt_u(int k)
+{
+    return k == 1 ? cy(I) * (cx(I) * cx(I) + cz(I) * cz(I) - 2.0 / 3.0)
+         : k == 2 ? cz(I) * (cx(I) * cx(I) + cy(I) * cy(I) - 2.0 / 3.0)
+                  : cx(I) * (cy(I) * cy(I) + cz(I) * cz(I) - 2.0 / 3.0);
+}
+template <int I>
+__host__ __device__ constexpr double mrt_v(int k)
+{
+    return k == 1 ? cy(I) * (cx(I) * cx(I) - cz(I) * cz(I))
+         : k == 2 ? cz(I) * (cx(I) * cx(I) - cy(I) * cy(I))
+                  : cx(I) * (cy(I) * cy(I) - cz(I) * cz(I));
+}
+template <class R, bool FORCE>
+__device__ __forceinline__ void mrt_collide(R (&s)[Q], R omega, R kf, R s3, R s4, R Fx, R Fy, R Fz)
+{
+    R dif[10];
+    R drho = s[0];
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        drho = radd(drho, radd(s[i], s[i + 9]));
+        dif[i] = rsub(s[i], s[i + 9]);
+    });
+    R jx = R(0), jy = R(0), jz = R(0);
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        if constexpr (cx(i) != 0) jx = cx(i) > 0 ? radd(jx, dif[i]) : rsub(jx, dif[i]);
+        if constexpr (cy(i) != 0) jy = cy(i) > 0 ? radd(jy, dif[i]) : rsub(jy, dif[i]);
+        if constexpr (cz(i) != 0) jz = cz(i) > 0 ? radd(jz, dif[i]) : rsub(jz, dif[i]);
+    });
+    const R rho = radd(R(1), drho);
+    if constexpr (FORCE) {
+        jx = rfma(R(0.5), Fx, jx);
+        jy = rfma(R(0.5), Fy, jy);
+        jz = rfma(R(0.5), Fz, jz);
+    }
+    const R inv = rrcp(rho);
+    const R ux = rmul(jx, inv), uy = rmul(jy, inv), uz = rmul(jz, inv);
+    const R m15 = rmul(R(-1.5), radd(radd(rmul(ux, ux), rmul(uy, uy)), rmul(uz, uz)));
+    R uF = R(0);
+    if constexpr (FORCE) uF = rfma(ux, Fx, rfma(uy, Fy, rmul(uz, Fz)));
+    // pass 1: J, Pi (orders 1, 2) and the six third-order coefficients
+    R Jx = R(0), Jy = R(0), Jz = R(0);
+    R Pxx = R(0), Pyy = R(0), Pzz = R(0), Pxy = R(0), Pxz = R(0), Pyz = R(0);
+    R bu1 = R(0), bu2 = R(0), bu3 = R(0), bv1 = R(0), bv2 = R(0), bv3 = R(0);
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        constexpr double w = wgt(i);
+        const R cu = cdot<i, R>(ux, uy, uz);
+        const R A = rmul(R(w), rho);
+        const R sym = rfma(rmul(R(4.5), A), rmul(cu, cu), rfma(A, m15, rmul(R(w), drho)));
+        const R anti = rmul(rmul(R(3), A), cu);
+        const R ne = rsub(radd(s[i], s[i + 9]), rmul(R(2), sym));  // n_i + n_i+9
+        const R no = rsub(dif[i], rmul(R(2), anti));               // n_i - n_i+9
+        if constexpr (cx(i) != 0) { Jx = cx(i) > 0 ? radd(Jx, no) : rsub(Jx, no); Pxx = radd(Pxx, ne); }
+        if constexpr (cy(i) != 0) { Jy = cy(i) > 0 ? radd(Jy, no) : rsub(Jy, no); Pyy = radd(Pyy, ne); }
+        if constexpr (cz(i) != 0) { Jz = cz(i) > 0 ? radd(Jz, no) : rsub(Jz, no); Pzz = radd(Pzz, ne); }
+        if constexpr (cx(i) * cy(i) != 0) Pxy = cx(i) * cy(i) > 0 ? radd(Pxy, ne) : rsub(Pxy, ne);
+        if constexpr (cx(i) * cz(i) != 0) Pxz = cx(i) * cz(i) > 0 ? radd(Pxz, ne) : rsub(Pxz, ne);
+        if constexpr (cy(i) * cz(i) != 0) Pyz = cy(i) * cz(i) > 0 ? radd(Pyz, ne) : rsub(Pyz, ne);
+        if constexpr (mrt_u<i>(1) != 0.0) bu1 = rfma(R(mrt_u<i>(1)), no, bu1);
+        if constexpr (mrt_u<i>(2) != 0.0) bu2 = rfma(R(mrt_u<i>(2)), no, bu2);
+        if constexpr (mrt_u<i>(3) != 0.0) bu3 = rfma(R(mrt_u<i>(3)), no, bu3);
+        if constexpr (mrt_v<i>(1) != 0.0) bv1 = rfma(R(mrt_v<i>(1)), no, bv1);
+        if constexpr (mrt_v<i>(2) != 0.0) bv2 = rfma(R(mrt_v<i>(2)), no, bv2);
+        if constexpr (mrt_v<i>(3) != 0.0) bv3 = rfma(R(mrt_v<i>(3)), no, bv3);
+    });
+    const R tr3 = rmul(R(1.0 / 3.0), radd(radd(Pxx, Pyy), Pzz));
+    const R om1 = rsub(R(1), omega), o3 = rsub(R(1), s3), o4 = rsub(R(1), s4);
+    // rest: seq_0, f1_0 = -1.5 tr/3, P3_0 = 0, P4_0 = n_0 - f1_0, w_0 S_0 = -u.F
+    {
+        const R C0 = rfma(rmul(R(1.0 / 3.0), rho), m15, rmul(R(1.0 / 3.0), drho));
+        const R f10 = rmul(R(-1.5), tr3);
+        const R n0 = rsub(s[0], C0);
+        s[0] = rfma(o4, rsub(n0, f10), rfma(om1, f10, C0));
+        if constexpr (FORCE) s[0] = rfma(kf, -uF, s[0]);
+    }
+    // pass 2: each pair from seq and the three relaxed parts
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        constexpr double w = wgt(i);
+        const R cu = cdot<i, R>(ux, uy, uz);
+        const R A = rmul(R(w), rho);
+        const R sym = rfma(rmul(R(4.5), A), rmul(cu, cu), rfma(A, m15, rmul(R(w), drho)));
+        const R anti = rmul(rmul(R(3), A), cu);
+        R cpc = R(0);
+        if constexpr (cx(i) != 0) cpc = radd(cpc, Pxx);
+        if constexpr (cy(i) != 0) cpc = radd(cpc, Pyy);
+        if constexpr (cz(i) != 0) cpc = radd(cpc, Pzz);
+        if constexpr (cx(i) * cy(i) != 0) cpc = cx(i) * cy(i) > 0 ? radd(cpc, rmul(R(2), Pxy)) : rsub(cpc, rmul(R(2), Pxy));
+        if constexpr (cx(i) * cz(i) != 0) cpc = cx(i) * cz(i) > 0 ? radd(cpc, rmul(R(2), Pxz)) : rsub(cpc, rmul(R(2), Pxz));
+        if constexpr (cy(i) * cz(i) != 0) cpc = cy(i) * cz(i) > 0 ? radd(cpc, rmul(R(2), Pyz)) : rsub(cpc, rmul(R(2), Pyz));
+        const R f1s = rmul(R(4.5 * w), rsub(cpc, tr3));
+        const R f1a = rmul(R(3 * w), cdot<i, R>(Jx, Jy, Jz));
+        R q = R(0);  // sum_p b_p H_p(c_i) / N_p over the third-order pairs
+        if constexpr (mrt_u<i>(1) != 0.0) q = rfma(R(13.5 * mrt_u<i>(1)), bu1, q);
+        if constexpr (mrt_u<i>(2) != 0.0) q = rfma(R(13.5 * mrt_u<i>(2)), bu2, q);
+        if constexpr (mrt_u<i>(3) != 0.0) q = rfma(R(13.5 * mrt_u<i>(3)), bu3, q);
+        if constexpr (mrt_v<i>(1) != 0.0) q = rfma(R(4.5 * mrt_v<i>(1)), bv1, q);
+        if constexpr (mrt_v<i>(2) != 0.0) q = rfma(R(4.5 * mrt_v<i>(2)), bv2, q);
+        if constexpr (mrt_v<i>(3) != 0.0) q = rfma(R(4.5 * mrt_v<i>(3)), bv3, q);
+        const R p3 = rmul(R(w), q);
+        const R na = rsub(s[i], radd(sym, anti)), nb = rsub(s[i + 9], rsub(sym, anti));
+        const R f1p = radd(f1s, f1a), f1m = rsub(f1s, f1a);
+        R a = rfma(o4, rsub(rsub(na, f1p), p3), rfma(o3, p3, rfma(om1, f1p, radd(sym, anti))));
+        R b = rfma(o4, radd(rsub(nb, f1m), p3), rfma(o3, -p3, rfma(om1, f1m, rsub(sym, anti))));
+        if constexpr (FORCE) {
+            const R cF = cdot<i, R>(Fx, Fy, Fz);
+            const R ssym = rfma(rmul(R(9 * w), cu), cF, rmul(R(-3 * w), uF));
+            const R santi = rmul(R(3 * w), cF);
+            a = rfma(kf, radd(ssym, santi), a);
+            b = rfma(kf, rsub(ssym, santi), b);
+        }
+        s[i] = a;
+        s[i + 9] = b;
+    });
+}
+
 // ---------------------------------------------------------------------------
 // Geometry and boundary description passed by value to every kernel.
 // ---------------------------------------------------------------------------
@@ -558,6 +691,7 @@ struct Geom {
     R omega, kf;         // 1/tau, 1 - omega/2
     int coll;            // collision (COLL_*; AA and two-lattice kernels)
     R om, kfm;           // TRT: omega-, 1 - omega-/2
+    R s3, s4;            // MRT: rates of the third- and fourth-order moments
     R L[Q];              // 6 w_k rho_w (c_k . u_lid): added to incoming slot k of a lid link
     R Fu[3];             // uniform force
     const float *Ff;     // per-cell force field [3][N] canonical, or nullptr
@@ -700,13 +834,13 @@ __device__ __forceinline__ void force_at(const Geom<R> &g, int64_t c, int64_t n,
 }
 
 // The collision a kernel of the AA or two-lattice schedule applies: BGK, or
-// TRT or regularised (a separate kernel instantiation each; the other
-// schedules are BGK only).
+// TRT, regularised or MRT (a separate kernel instantiation each).
 template <class R, bool FORCE, int COLL>
 __device__ __forceinline__ void collide_sel(const Geom<R> &g, R (&s)[Q], R Fx, R Fy, R Fz)
 {
     if constexpr (COLL == COLL_TRT) trt_collide<R, FORCE>(s, g.omega, g.kf, g.om, g.kfm, Fx, Fy, Fz);
     else if constexpr (COLL == COLL_REG) reg_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
+    else if constexpr (COLL == COLL_MRT) mrt_collide<R, FORCE>(s, g.omega, g.kf, g.s3, g.s4, Fx, Fy, Fz);
     else bgk_collide<R, FORCE>(s, g.omega, g.kf, Fx, Fy, Fz);
 }
 

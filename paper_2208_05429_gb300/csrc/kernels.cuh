@@ -111,6 +111,8 @@ inline Geom<R> make_geom(const HostGeom &h, int64_t pitch)
     g.coll = h.coll;
     g.om = R(h.omega_m);
     g.kfm = R(h.kf_m);
+    g.s3 = R(h.mrt_s3);
+    g.s4 = R(h.mrt_s4);
     for (int i = 0; i < Q; ++i) g.L[i] = R(h.L[i]);
     for (int a = 0; a < 3; ++a) g.Fu[a] = R(h.Fu[a]);
     g.Ff = h.Ff;

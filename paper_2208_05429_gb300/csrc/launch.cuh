@@ -24,6 +24,7 @@ inline void with_model(bool force, int coll, Fn &&fn)
     auto pick = [&](auto F) {
         if (coll == COLL_TRT) fn(F, std::integral_constant<int, COLL_TRT>{});
         else if (coll == COLL_REG) fn(F, std::integral_constant<int, COLL_REG>{});
+        else if (coll == COLL_MRT) fn(F, std::integral_constant<int, COLL_MRT>{});
         else fn(F, std::integral_constant<int, COLL_BGK>{});
     };
     if (force) pick(std::true_type{});

@@ -148,7 +148,12 @@ int sm_count();
 // The kernels' collision variant (COLL_*) of a configuration.
 int coll_of(const lbm_config &c)
 {
-    return c.collision == LBM_COLLISION_TRT ? COLL_TRT : (c.collision == LBM_COLLISION_REG ? COLL_REG : COLL_BGK);
+    switch (c.collision) {
+    case LBM_COLLISION_TRT: return COLL_TRT;
+    case LBM_COLLISION_REG: return COLL_REG;
+    case LBM_COLLISION_MRT: return COLL_MRT;
+    default: return COLL_BGK;
+    }
 }
 
 bool uses_ns(const lbm_config &c, const ShellInfo &si)
@@ -280,6 +285,8 @@ HostGeom host_geom(const lbm_config &c)
     h.coll = coll_of(c);
     h.omega_m = h.coll == COLL_TRT ? 1.0 / (0.5 + c.trt_lambda / (c.tau - 0.5)) : h.omega;
     h.kf_m = 1.0 - 0.5 * h.omega_m;
+    h.mrt_s3 = c.mrt_s3;
+    h.mrt_s4 = c.mrt_s4;
     for (int k = 0; k < Q; ++k) {
         const double cu = cx(k) * c.u_lid[0] + cy(k) * c.u_lid[1] + cz(k) * c.u_lid[2];
         h.L[k] = 6.0 * wgt(k) * c.rho_wall * cu;
@@ -401,6 +408,8 @@ void lbm_config_default(lbm_config *cfg)
     cfg->force_mode = LBM_FORCE_NONE;
     cfg->collision = LBM_COLLISION_BGK;
     cfg->trt_lambda = 3.0 / 16.0;
+    cfg->mrt_s3 = 1.0;
+    cfg->mrt_s4 = 1.0;
 }
 
 int lbm_validate(const lbm_config *c)
@@ -423,8 +432,8 @@ int lbm_validate(const lbm_config *c)
     if (c->force_mode < LBM_FORCE_NONE || c->force_mode > LBM_FORCE_FIELD) return LBM_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (!isfinite(c->force_uniform[a])) return LBM_EINVAL;
-    if (c->collision != LBM_COLLISION_BGK && c->collision != LBM_COLLISION_TRT && c->collision != LBM_COLLISION_REG)
-        return LBM_EINVAL;
+    if (c->collision < LBM_COLLISION_BGK || c->collision > LBM_COLLISION_MRT) return LBM_EINVAL;
+    if (!(c->mrt_s3 > 0.0 && c->mrt_s3 < 2.0) || !(c->mrt_s4 > 0.0 && c->mrt_s4 < 2.0)) return LBM_EINVAL;
     if (!(c->trt_lambda > 0.0) || !isfinite(c->trt_lambda)) return LBM_EINVAL;
     return LBM_OK;
 }

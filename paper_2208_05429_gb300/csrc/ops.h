@@ -15,8 +15,9 @@ struct HostGeom {
     int per[3];
     int lid[6];
     double omega, kf;
-    int coll;            // collision: 0 BGK, 1 TRT, 2 regularised BGK
+    int coll;            // collision: 0 BGK, 1 TRT, 2 regularised BGK, 3 MRT
     double omega_m, kf_m;
+    double mrt_s3, mrt_s4;
     double L[19];
     double Fu[3];
     const float *Ff;

@@ -27,8 +27,8 @@ LBM_STORAGE_F64, LBM_STORAGE_F32, LBM_STORAGE_F32S, LBM_STORAGE_F16S, LBM_STORAG
 LBM_VARIANT_TWO_LATTICE, LBM_VARIANT_AA, LBM_VARIANT_MERGED = 0, 1, 2
 LBM_FORCE_NONE, LBM_FORCE_UNIFORM, LBM_FORCE_FIELD = 0, 1, 2
 LBM_DTYPE_F32, LBM_DTYPE_F64 = 0, 1
-LBM_COLLISION_BGK, LBM_COLLISION_TRT, LBM_COLLISION_REG = 0, 1, 2
-COLLISION = {"bgk": LBM_COLLISION_BGK, "trt": LBM_COLLISION_TRT, "reg": LBM_COLLISION_REG}
+LBM_COLLISION_BGK, LBM_COLLISION_TRT, LBM_COLLISION_REG, LBM_COLLISION_MRT = 0, 1, 2, 3
+COLLISION = {"bgk": LBM_COLLISION_BGK, "trt": LBM_COLLISION_TRT, "reg": LBM_COLLISION_REG, "mrt": LBM_COLLISION_MRT}
 LBM_KERNEL_TWO_LATTICE, LBM_KERNEL_AA_EVEN, LBM_KERNEL_AA_ODD, LBM_KERNEL_SNAPSHOT, LBM_KERNEL_MERGED = \
     0, 1, 2, 3, 4
 KERNELS = {"two_lattice": LBM_KERNEL_TWO_LATTICE, "aa_even": LBM_KERNEL_AA_EVEN, "aa_odd": LBM_KERNEL_AA_ODD,
@@ -63,6 +63,8 @@ class lbm_config(ctypes.Structure):
         ("force_uniform", ctypes.c_double * 3),
         ("collision", ctypes.c_int32),
         ("trt_lambda", ctypes.c_double),
+        ("mrt_s3", ctypes.c_double),
+        ("mrt_s4", ctypes.c_double),
     ]
 
 
@@ -292,7 +294,8 @@ def lbm_adjoint_backward(h, dLdrho, dLdu, dtype_code: int, dLdf0, dLdF, work, nb
 def make_config(shape: Sequence[int], tau: float, bc: Sequence[Union[str, int]] = ("periodic",) * 6,
                 u_lid=(0.0, 0.0, 0.0), rho_wall: float = 1.0, storage: str = "f32", variant: str = "aa",
                 force_mode: int = LBM_FORCE_NONE, force_uniform=(0.0, 0.0, 0.0),
-                collision: Union[str, int] = "bgk", trt_lambda: float = 3.0 / 16.0) -> lbm_config:
+                collision: Union[str, int] = "bgk", trt_lambda: float = 3.0 / 16.0,
+                mrt_s3: float = 1.0, mrt_s4: float = 1.0) -> lbm_config:
     """Build an lbm_config; shape is (nx, ny, nz), bc lists x-, x+, y-, y+, z-, z+."""
     c = lbm_config()
     c.nx, c.ny, c.nz = (int(v) for v in shape)
@@ -309,6 +312,7 @@ def make_config(shape: Sequence[int], tau: float, bc: Sequence[Union[str, int]] 
     c.force_mode = int(force_mode)
     c.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
     c.trt_lambda = float(trt_lambda)
+    c.mrt_s3, c.mrt_s4 = float(mrt_s3), float(mrt_s4)
     return c
 
 
@@ -324,7 +328,8 @@ class Lattice:
 
     def __init__(self, shape, tau: float, bc=("periodic",) * 6, u_lid=(0.0, 0.0, 0.0), rho_wall: float = 1.0,
                  storage: str = "f32", variant: str = "aa", force=None, device=None, stream=None,
-                 collision: str = "bgk", trt_lambda: float = 3.0 / 16.0):
+                 collision: str = "bgk", trt_lambda: float = 3.0 / 16.0, mrt_s3: float = 1.0,
+                 mrt_s4: float = 1.0):
         import torch
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         if force is None:
@@ -333,7 +338,8 @@ class Lattice:
             fm, fu = LBM_FORCE_FIELD, (0.0, 0.0, 0.0)
         else:
             fm, fu = LBM_FORCE_UNIFORM, tuple(float(v) for v in force)
-        self.cfg = make_config(shape, tau, bc, u_lid, rho_wall, storage, variant, fm, fu, collision, trt_lambda)
+        self.cfg = make_config(shape, tau, bc, u_lid, rho_wall, storage, variant, fm, fu, collision, trt_lambda,
+                               mrt_s3, mrt_s4)
         self.shape = tuple(int(v) for v in shape)  # (nx, ny, nz)
         self.nbytes = lbm_required_bytes(self.cfg)
         with torch.cuda.device(self.device):

@@ -64,8 +64,9 @@ def make_gpu(cfg: "oracle.Config", storage: str, variant: str, device="cuda:0") 
         force = None
     return Lattice((cfg.nx, cfg.ny, cfg.nz), cfg.tau, bc=tuple(int(b) for b in cfg.bc), u_lid=tuple(cfg.u_lid),
                    rho_wall=cfg.rho_wall, storage=storage, variant=variant, force=force, device=device,
-                   collision={oracle.COLL_TRT: "trt", oracle.COLL_REG: "reg"}.get(cfg.collision, "bgk"),
-                   trt_lambda=cfg.trt_lambda)
+                   collision={oracle.COLL_TRT: "trt", oracle.COLL_REG: "reg", oracle.COLL_MRT: "mrt"}.get(
+                       cfg.collision, "bgk"),
+                   trt_lambda=cfg.trt_lambda, mrt_s3=cfg.mrt_s3, mrt_s4=cfg.mrt_s4)
 
 
 def oracle_force_as_f32(cfg: "oracle.Config") -> "oracle.Config":

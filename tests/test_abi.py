@@ -45,7 +45,7 @@ def test_default_config_valid(cuda_lib):
 @pytest.mark.parametrize("field,value", [
     ("nx", 0), ("ny", -3), ("nz", 70000), ("tau", 0.5), ("tau", float("nan")), ("rho_wall", 0.0),
     ("storage", 9), ("variant", 3), ("variant", 4), ("force_mode", 5),
-    ("collision", 3), ("collision", -1), ("trt_lambda", 0.0), ("trt_lambda", float("inf")),
+    ("collision", 4), ("collision", -1), ("mrt_s3", 0.0), ("mrt_s4", 2.0), ("trt_lambda", 0.0), ("trt_lambda", float("inf")),
 ])
 def test_invalid_configs_rejected(cuda_lib, field, value):
     cfg = lbm.lbm_config_default()
@@ -79,7 +79,7 @@ def test_required_bytes_scale(cuda_lib):
 
 def test_every_collision_on_every_schedule(cuda_lib):
     for variant in ("aa", "two_lattice", "merged"):
-        for coll in ("bgk", "trt", "reg"):
+        for coll in ("bgk", "trt", "reg", "mrt"):
             cfg = lbm.make_config((16, 16, 16), 0.7, lbm.CAVITY_BC, storage="f32", variant=variant, collision=coll)
             assert lbm.lbm_validate(cfg) == lbm.LBM_OK, (variant, coll)
     assert lbm.lbm_config_default().collision == lbm.LBM_COLLISION_BGK
@@ -94,7 +94,7 @@ def test_strerror(cuda_lib):
 def test_config_struct_layout_matches_header(cuda_lib):
     """The ctypes mirror of lbm_config has the C layout (checked through a
     round trip: lbm_config_default writes every field)."""
-    assert ctypes.sizeof(lbm.lbm_config) == 144
+    assert ctypes.sizeof(lbm.lbm_config) == 160
     cfg = lbm.lbm_config_default()
     assert cfg.tau == 0.6 and cfg.rho_wall == 1.0 and list(cfg.face_bc) == [0] * 6
     assert cfg.storage == lbm.LBM_STORAGE_F32 and cfg.variant == lbm.LBM_VARIANT_AA
