@@ -284,17 +284,22 @@ def e2e_leg(n, storage, variant, steps, warmup):
     dev_f = torch.empty_like(host_f, device=lat.device)
     host_rho = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
     host_u = torch.empty((3, n, n, n), dtype=torch.float32).pin_memory()
+    every = 50
     for _ in range(warmup):
         lat.step(2)
+    # the call pattern of the timed region once, so that its CUDA graph is
+    # captured here and only replayed there
+    lat.step(2 * min(every, steps))
     torch.cuda.synchronize()
     st = lat.stream
-    every = 50
     reads = 0
     start = torch.cuda.Event(enable_timing=True)
+    up = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(st):
         start.record(st)
         dev_f.copy_(host_f, non_blocking=True)
+        up.record(st)
         lat.init_populations(dev_f)
         done = 0
         while done < steps:  # one step(n) call per reduction interval
@@ -310,12 +315,13 @@ def e2e_leg(n, storage, variant, steps, warmup):
         end.record(st)
     end.synchronize()
     ms = start.elapsed_time(end)
+    up_ms = start.elapsed_time(up)
     cells = n ** 3
     h2d = host_f.numel() * 4
     d2h = (host_rho.numel() + host_u.numel()) * 4 + reads * 5 * 8
     return {"value": round(cells * 2 * steps / (ms * 1e3), 1), "unit": UNIT,
             "h2d_bytes_per_step": round(h2d / steps, 1), "d2h_bytes_per_step": round(d2h / steps, 1),
-            "ms": round(ms, 3),
+            "ms": round(ms, 3), "h2d_ms": round(up_ms, 3), "h2d_GBs": round(h2d / (up_ms * 1e6), 1),
             "what": "pinned host populations -> device, steps with an FP64 reduction read every 100 time "
                     "steps, final rho and u -> pinned host; bytes per step amortised over the run"}
 
