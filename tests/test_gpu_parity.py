@@ -145,6 +145,34 @@ def test_full_lattice_two_step_sweep_at_bench_size(gpu, monkeypatch, sweep):
     assert err <= FULL_TOL
 
 
+@pytest.mark.parametrize("collision", ["trt", "reg", "mrt"])
+def test_full_lattice_sweep_other_collisions_at_bench_size(gpu, collision):
+    """The neighbour-synchronised sweep's TRT, regularised and MRT variants
+    on the whole 256^3 cavity (FP32): after 20 steps, one more two-step sweep
+    against the FP64 oracle with the same collision stepping the GPU's own
+    state twice (the FP32 bound of the BGK check; the operators differ only
+    in how f - feq is relaxed)."""
+    from paper_2208_05429_gb300.lbm import CAVITY_BC, Lattice
+    cfg = oracle.cavity(256, 0.55)
+    cfg.collision = {"trt": oracle.COLL_TRT, "reg": oracle.COLL_REG, "mrt": oracle.COLL_MRT}[collision]
+    cfg.trt_lambda, cfg.mrt_s3, cfg.mrt_s4 = 3.0 / 16.0, 1.3, 1.7
+    lat = Lattice((256, 256, 256), 0.55, bc=CAVITY_BC, u_lid=tuple(cfg.u_lid), storage="f32", variant="merged",
+                  collision=collision, trt_lambda=cfg.trt_lambda, mrt_s3=cfg.mrt_s3, mrt_s4=cfg.mrt_s4)
+    lat.init_equilibrium()
+    lat.step(20)
+    f20 = gpu_state(lat)
+    lat.profile(True)
+    lat.step(2)
+    ran = lat.profile_read()
+    lat.profile(False)
+    assert "merged" in ran, ran
+    exp = oracle.run(cfg, f20, 2)
+    del f20
+    err = relmax(gpu_state(lat), exp)
+    print(f"merged/{collision}: full-lattice relative max error after one sweep {err:.3e}")
+    assert err <= FULL_TOL
+
+
 def test_full_lattice_aa_steps_at_bench_size(gpu):
     """The two AA kernels the benchmark times, on the whole 256^3 lattice:
     the even step (k_aa_even, natural -> A parity) and then the odd step
