@@ -233,6 +233,26 @@ def collide_cell(tau: float, f, F=(0.0, 0.0, 0.0)) -> np.ndarray:
     return out
 
 
+def store_round(f: np.ndarray, storage: str) -> np.ndarray:
+    """The populations f[19, ...] as a 16-bit shifted storage format holds
+    them: s_i = f_i - w_i rounded to nearest-even, "f16s" to IEEE binary16,
+    "bf16s" to bfloat16 (of s_i rounded to binary32 first, the compute type
+    that produces it), and returned as w_i + s_i in float64; also the stored
+    s itself.  Plain numpy; the definition of the storage, not of the step."""
+    _, w, _ = lattice()
+    shp = (-1,) + (1,) * (np.ndim(f) - 1)
+    s = np.asarray(f, dtype=np.float64) - w.reshape(shp)
+    if storage == "f16s":
+        r = s.astype(np.float16).astype(np.float64)
+    elif storage == "bf16s":
+        x = s.astype(np.float32).view(np.uint32).astype(np.uint64)
+        x = (x + 0x7FFF + ((x >> 16) & 1)) & 0xFFFF0000
+        r = x.astype(np.uint32).view(np.float32).astype(np.float64)
+    else:
+        raise ValueError(storage)
+    return r + w.reshape(shp), r
+
+
 def init_equilibrium(cfg: Config, rho=None, u=None) -> np.ndarray:
     lib = _load()
     r = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64).reshape(cfg.shape)
