@@ -320,6 +320,47 @@ __device__ __forceinline__ void store_mom(R *__restrict__ mom, int64_t slot, int
     mom[3 * slot + c] = m.uz;
 }
 
+// Push of a cell in a row inside in y and z (only x faces can be crossed),
+// for all lanes of a warp alike: f*_i goes to slot i of x + c_i
+// (dout.p[i] = dst.p[i] + noff[i]), or, across an x wall, to slot opp(i) of
+// x itself (same weight, same encoding) with the lid term of a lid face;
+// across a periodic x face the target wraps by nx.  lo / hi: x is the first /
+// last cell of its row.
+template <class S>
+__device__ __forceinline__ void push_xsel(const Geom<typename S::R> &g, const Dirs<typename S::T> &dst,
+                                          const Dirs<typename S::T> &dout, int c, bool lo, bool hi,
+                                          const typename S::R (&s)[Q])
+{
+    using R = typename S::R;
+    using T = typename S::T;
+    static_for<Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        if constexpr (cx(i) == 0) {
+            dout.p[i][c] = encode<S, i>(s[i]);
+        } else {
+            const bool out = cx(i) > 0 ? hi : lo;
+            T *a = dout.p[i] + c;
+            R v = s[i];
+            if (g.per[0]) {
+                a = out ? a + (cx(i) > 0 ? -g.nx : g.nx) : a;
+            } else {
+                a = out ? dst.p[opp(i)] + c : a;
+                if (g.lid[cx(i) > 0 ? 1 : 0]) v = out ? radd(v, g.L[opp(i)]) : v;
+            }
+            *a = encode<S, i>(v);
+        }
+    });
+}
+
+// A warp whose row is inside in y and z and that holds an x-edge cell (the
+// case push_xsel and the odd step's select gather serve).
+template <class G>
+__device__ __forceinline__ bool xedge_warp(const G &g, int x, int y, int z)
+{
+    const int wx0 = x - (int)(threadIdx.x & 31);
+    return y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1 && (wx0 == 0 || wx0 + 31 >= g.nx - 1);
+}
+
 // ---------------------------------------------------------------------------
 // K1: two-lattice fused collide-and-push (natural -> natural)
 // ---------------------------------------------------------------------------
@@ -341,7 +382,11 @@ __global__ void __launch_bounds__(128) k_two_lattice(Geom<typename S::R> g, Dirs
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
     if constexpr (MOM) store_mom<R>(mom, g.slot, c, moments_of<R, FORCE>(s, Fx, Fy, Fz));
     collide_sel<R, FORCE, COLL>(g, s, Fx, Fy, Fz);
-    if (interior(g, x, y, z)) {
+    // x-edge warps of rows inside in y and z: one select path for all lanes
+    // (4- and 8-byte storage, as in the AA odd step)
+    if (sizeof(typename S::T) >= 4 && xedge_warp(g, x, y, z)) {
+        push_xsel<S>(g, dst, dout, c, x == 0, x == g.nx - 1, s);
+    } else if (interior(g, x, y, z)) {
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;
             dout.p[i][c] = encode<S, i>(s[i]);
@@ -478,8 +523,32 @@ __global__ void __launch_bounds__(128) k_aa_odd(Geom<typename S::R> g, Dirs<type
     if (x >= g.nx) return;
     const int c = cell32(g, x, y, z);
     R s[Q];
+    // Warps whose row is inside in y and z and that hold an x-edge cell take
+    // one branch-free path for all their lanes: links through an x face pick
+    // their address (and the lid term) by select, so the warp does not split
+    // into an interior and a boundary half.  For 4- and 8-byte storage only:
+    // with 2-byte storage the kernel is instruction-bound and the extra path
+    // made it slower (0.30 -> 0.34 ms at 256^3), where FP32 gained 6%.
+    constexpr bool XSEL = sizeof(T) >= 4;
+    const bool xsel = XSEL && xedge_warp(g, x, y, z);
     const bool in = interior(g, x, y, z);
-    if (in) {
+    const bool lo = x == 0, hi = x == g.nx - 1;
+    if (XSEL && xsel) {
+        static_for<Q>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            // f_k(x) sits in slot opp(k) of x - c_k, or, across an x wall, in
+            // slot k of x itself
+            if constexpr (cx(k) == 0) {
+                s[k] = decode<S, k>(fin.p[k][c]);
+            } else {
+                const bool out = cx(k) > 0 ? lo : hi;
+                const T *a = fin.p[k] + c;
+                if (g.per[0]) a = out ? a + (cx(k) > 0 ? g.nx : -g.nx) : a;
+                else a = out ? f.p[k] + c : a;
+                s[k] = decode<S, k>(*a);
+            }
+        });
+    } else if (in) {
         static_for<Q>([&](auto K) {
             constexpr int k = decltype(K)::value;
             s[k] = decode<S, k>(fin.p[k][c]);
@@ -490,7 +559,9 @@ __global__ void __launch_bounds__(128) k_aa_odd(Geom<typename S::R> g, Dirs<type
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
     collide_sel<R, FORCE, COLL>(g, s, Fx, Fy, Fz);
-    if (in) {
+    if (XSEL && xsel) {
+        push_xsel<S>(g, f, fout, c, lo, hi, s);
+    } else if (in) {
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;
             fout.p[i][c] = encode<S, i>(s[i]);
