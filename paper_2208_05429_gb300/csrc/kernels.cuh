@@ -799,7 +799,23 @@ __global__ void __launch_bounds__(128) k_adjoint(Geom<typename S::R> g, Dirs<con
     const R usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
     // mu_i = dL/df*_i: the transpose of streaming
     R mu[Q];
-    if (interior(g, x, y, z)) {
+    if (xedge_warp(g, x, y, z)) {
+        // x-edge warps of rows inside in y and z: one select path for all
+        // lanes (links through an x face only), as in the AA odd step
+        const bool lo = x == 0, hi = x == g.nx - 1;
+        static_for<Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            if constexpr (cx(i) == 0) {
+                mu[i] = ld_pol(lin.p[i] + c, pl);
+            } else {
+                const bool out = cx(i) > 0 ? hi : lo;
+                const R *a = lin.p[i] + c;
+                if (g.per[0]) a = out ? a + (cx(i) > 0 ? -g.nx : g.nx) : a;
+                else a = out ? lin.p[opp(i)] + c + g.noff[i] : a;
+                mu[i] = ld_pol(a, pl);
+            }
+        });
+    } else if (interior(g, x, y, z)) {
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;
             mu[i] = ld_pol(lin.p[i] + c, pl);
