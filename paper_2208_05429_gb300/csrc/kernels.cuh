@@ -383,8 +383,8 @@ __global__ void __launch_bounds__(128) k_two_lattice(Geom<typename S::R> g, Dirs
     if constexpr (MOM) store_mom<R>(mom, g.slot, c, moments_of<R, FORCE>(s, Fx, Fy, Fz));
     collide_sel<R, FORCE, COLL>(g, s, Fx, Fy, Fz);
     // x-edge warps of rows inside in y and z: one select path for all lanes
-    // (4- and 8-byte storage, as in the AA odd step)
-    if (sizeof(typename S::T) >= 4 && xedge_warp(g, x, y, z)) {
+    // (as the AA odd step's push)
+    if (xedge_warp(g, x, y, z)) {
         push_xsel<S>(g, dst, dout, c, x == 0, x == g.nx - 1, s);
     } else if (interior(g, x, y, z)) {
         static_for<Q>([&](auto K) {
@@ -526,11 +526,13 @@ __global__ void __launch_bounds__(128) k_aa_odd(Geom<typename S::R> g, Dirs<type
     // Warps whose row is inside in y and z and that hold an x-edge cell take
     // one branch-free path for all their lanes: links through an x face pick
     // their address (and the lid term) by select, so the warp does not split
-    // into an interior and a boundary half.  For 4- and 8-byte storage only:
-    // with 2-byte storage the kernel is instruction-bound and the extra path
-    // made it slower (0.30 -> 0.34 ms at 256^3), where FP32 gained 6%.
+    // into an interior and a boundary half.  The gather takes this path for
+    // 4- and 8-byte storage only: with 2-byte storage the kernel is
+    // instruction-bound and the select gather made it slower (0.31 -> 0.35 ms
+    // at 256^3), while the select push helps every format (FP32 +6% with
+    // both, 2-byte 0.31 -> 0.29 ms with the push alone).
     constexpr bool XSEL = sizeof(T) >= 4;
-    const bool xsel = XSEL && xedge_warp(g, x, y, z);
+    const bool xsel = xedge_warp(g, x, y, z);
     const bool in = interior(g, x, y, z);
     const bool lo = x == 0, hi = x == g.nx - 1;
     if (XSEL && xsel) {
@@ -559,7 +561,7 @@ __global__ void __launch_bounds__(128) k_aa_odd(Geom<typename S::R> g, Dirs<type
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
     collide_sel<R, FORCE, COLL>(g, s, Fx, Fy, Fz);
-    if (XSEL && xsel) {
+    if (xsel) {
         push_xsel<S>(g, f, fout, c, lo, hi, s);
     } else if (in) {
         static_for<Q>([&](auto K) {
