@@ -493,8 +493,8 @@ __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
     cta_barrier();
     if (abort_flag[ph++ & 1]) goto bail;
     // interval k: odd step of plane k and even step of plane k+2 (in either
-    // order: even and odd tile warps take them in opposite orders, so that
-    // their pushes and collisions interleave); the copy of plane k+3 goes
+    // order: tile warps that share a scheduler take them in opposite orders,
+    // so that their pushes and collisions interleave); the copy of plane k+3 goes
     // into the slot plane k+1 left in the previous interval.  The pushes
     // into planes k-1 and k need the neighbours' copies of plane k; the
     // pushes of the odd step of plane k into plane k+1 are held in registers
@@ -504,7 +504,10 @@ __global__ void __launch_bounds__(NSL<TY, typename S::T>::THREADS, 1)
     for (int k = 0; k < nz; ++k) {
         R s[Q];
         R rn = R(0), zpn = R(0), zmn = R(0);
-        const bool odd_first = (threadIdx.x & 32) == 0;
+        // warps w, w+4, w+8, ... share a scheduler (warp index mod 4): they
+        // alternate, so that each scheduler has collisions of one step and
+        // memory operations of the other in flight at once
+        const bool odd_first = ((threadIdx.x >> 7) & 1) == 0;
         const int path = (k == 0 || k == nz - 1) ? C::PATH_WALL : (warp_x || warp_y ? xy_path : C::PATH_FREE);
         if (c.role == C::SYNC) {
             if (lane == 0 && k + 3 < nz) issue(k + 3);
