@@ -60,6 +60,29 @@ struct NSL {
     static constexpr int RSM = 3, RS0 = 3, RSP = 4;
     static constexpr int NRING = RSM * NDM + RS0 * ND0 + RSP * NDP;
     static_assert(THREADS <= 1024, "one CTA");
+
+    // Logical warp (tile row 0 .. TY-1, then the halo warps, then the sync
+    // warp) of hardware warp w.  Warps w, w+4, w+8, ... share one of the SM's
+    // four schedulers; with 14 tile, 3 halo and 1 sync warp the identity puts
+    // four tile warps and a halo warp on one scheduler and three tile warps on
+    // another.  The permutation below gives the schedulers 4 tile + sync,
+    // 3 tile + 2 halo, 4 tile, and 3 tile + 1 halo warps, closer to equal
+    // work (a halo warp does about half a tile warp's).
+    __device__ __forceinline__ static int logical(int w)
+    {
+        if constexpr (TY == 14 && NWARPS == 18) {
+            switch (w) {
+            case 13: return 14;
+            case 14: return 13;
+            case 15: return 16;
+            case 16: return 17;
+            case 17: return 15;
+            default: return w;
+            }
+        } else {
+            return w;
+        }
+    }
 };
 
 template <int TY, class T, class R>
@@ -111,7 +134,7 @@ struct NSCta {
         x0 = 32 * blockIdx.x;
         tw = min(32, nx - x0);
         band_of(si, blockIdx.y, y0, th);
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int warp = L::logical(threadIdx.x >> 5), lane = threadIdx.x & 31;
         role = warp < TY ? TILE : (warp < L::SYNCW ? HALO : SYNC);
         if (role == TILE) {
             lx = lane;
