@@ -1,4 +1,4 @@
-"""Test-only FP64 oracle of the D3Q19 BGK collide-and-stream update.
+"""Test-only FP64 oracle of the D3Q19 (also D3Q15, D3Q27) BGK collide-and-stream update.
 
 This package is test infrastructure.  Only ``tests/``, ``__graft_entry__.smoke``
 and the CPU-baseline leg of ``bench.py`` import it; the product package never
@@ -7,7 +7,8 @@ does, and the two share no code.  The arithmetic lives in ``lbm_oracle.c``
 x86 and Arm hosts give the same bits); this module only compiles it on first
 use and marshals numpy arrays through ctypes.
 
-Arrays use the canonical layout: populations ``f[19, nz, ny, nx]`` in the
+Arrays use the canonical layout: populations ``f[q, nz, ny, nx]`` (q = 19, or
+``Config.q`` = 15 or 27) in the
 oracle's own direction order (see :func:`lattice`), densities ``rho[nz, ny, nx]``
 and velocities ``u[3, nz, ny, nx]``.
 
@@ -32,6 +33,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 Q = 19
+LATTICES = (15, 19, 27)
 BC_PERIODIC, BC_WALL, BC_LID = 0, 1, 2
 FORCE_NONE, FORCE_UNIFORM, FORCE_FIELD = 0, 1, 2
 COLL_BGK, COLL_TRT, COLL_REG, COLL_MRT = 0, 1, 2, 3
@@ -72,6 +74,7 @@ class _Cfg(ctypes.Structure):
         ("trt_lambda", ctypes.c_double),
         ("mrt_s3", ctypes.c_double),
         ("mrt_s4", ctypes.c_double),
+        ("q", ctypes.c_int32),
     ]
 
 
@@ -87,7 +90,10 @@ def _load():
             P = ctypes.POINTER(_Cfg)
             sigs = {
                 "orc_lattice": [_I32, _D, _I32],
+                "orc_lattice_q": [ctypes.c_int32, _I32, _D, _I32],
                 "orc_equilibrium": [ctypes.c_double, _D, _D],
+                "orc_equilibrium_q": [ctypes.c_int32, ctypes.c_double, _D, _D],
+                "orc_collide_cell_q": [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _D, _D, _D],
                 "orc_collide_cell": [ctypes.c_double, _D, _D, _D],
                 "orc_collide_cell_trt": [ctypes.c_double, ctypes.c_double, _D, _D, _D],
                 "orc_collide_cell_reg": [ctypes.c_double, _D, _D, _D],
@@ -140,6 +146,13 @@ class Config:
     trt_lambda: float = 3.0 / 16.0
     mrt_s3: float = 1.0           # MRT rates of the third- and fourth-order moments
     mrt_s4: float = 1.0
+    q: int = 19                   # lattice: D3Q15, D3Q19 or D3Q27 (MRT: D3Q19 only)
+
+    def __post_init__(self):
+        if self.q not in LATTICES:
+            raise ValueError(f"lattice q={self.q}: one of {LATTICES}")
+        if self.q != 19 and self.collision == COLL_MRT:
+            raise ValueError("the MRT collision is defined on D3Q19 only")
 
     @property
     def shape(self):
@@ -164,6 +177,7 @@ class Config:
         c.trt_lambda = float(self.trt_lambda)
         c.mrt_s3 = float(self.mrt_s3)
         c.mrt_s4 = float(self.mrt_s4)
+        c.q = int(self.q)
         if self.force_mode == FORCE_FIELD:
             ff = np.ascontiguousarray(self.force_field, dtype=np.float64).reshape(3, *self.shape)
             self._ff_keep = ff  # keep the buffer alive for the call
@@ -179,21 +193,42 @@ def cavity(n: int, tau: float, u_lid=(0.05, 0.0, 0.0), ny: int = None, nz: int =
                   bc=(BC_WALL, BC_WALL, BC_WALL, BC_WALL, BC_WALL, BC_LID), u_lid=u_lid)
 
 
-def lattice():
-    """The oracle's own D3Q19 table: (c[19,3] int, w[19], opp[19] int)."""
+def lattice(q: int = 19):
+    """The oracle's own table of lattice D3Q<q>: (c[q,3] int, w[q], opp[q] int)."""
     lib = _load()
-    c = np.zeros((Q, 3), np.int32)
-    w = np.zeros(Q, np.float64)
-    opp = np.zeros(Q, np.int32)
-    lib.orc_lattice(c.ctypes.data_as(_I32), _ptr(w), opp.ctypes.data_as(_I32))
+    c = np.zeros((q, 3), np.int32)
+    w = np.zeros(q, np.float64)
+    opp = np.zeros(q, np.int32)
+    if q == 19:
+        lib.orc_lattice(c.ctypes.data_as(_I32), _ptr(w), opp.ctypes.data_as(_I32))
+    else:
+        assert q in LATTICES, q
+        lib.orc_lattice_q(q, c.ctypes.data_as(_I32), _ptr(w), opp.ctypes.data_as(_I32))
     return c.astype(np.int64), w, opp.astype(np.int64)
 
 
-def equilibrium(rho: float, u) -> np.ndarray:
+def equilibrium(rho: float, u, q: int = 19) -> np.ndarray:
     lib = _load()
     uu = np.ascontiguousarray(u, dtype=np.float64)
-    out = np.zeros(Q, np.float64)
-    lib.orc_equilibrium(float(rho), _ptr(uu), _ptr(out))
+    out = np.zeros(q, np.float64)
+    if q == 19:
+        lib.orc_equilibrium(float(rho), _ptr(uu), _ptr(out))
+    else:
+        assert q in LATTICES, q
+        lib.orc_equilibrium_q(q, float(rho), _ptr(uu), _ptr(out))
+    return out
+
+
+def collide_cell_q(q: int, tau: float, f, F=(0.0, 0.0, 0.0), collision: int = COLL_BGK,
+                   lam: float = 3.0 / 16.0) -> np.ndarray:
+    """One cell of lattice D3Q<q>: BGK, TRT (Lambda = lam) or regularised BGK."""
+    assert q in LATTICES and collision in (COLL_BGK, COLL_TRT, COLL_REG)
+    lib = _load()
+    ff = np.ascontiguousarray(f, dtype=np.float64)
+    assert ff.shape == (q,)
+    FF = np.ascontiguousarray(F, dtype=np.float64)
+    out = np.zeros(q, np.float64)
+    lib.orc_collide_cell_q(int(q), int(collision), float(tau), float(lam), _ptr(ff), _ptr(FF), _ptr(out))
     return out
 
 
@@ -234,12 +269,12 @@ def collide_cell(tau: float, f, F=(0.0, 0.0, 0.0)) -> np.ndarray:
 
 
 def store_round(f: np.ndarray, storage: str) -> np.ndarray:
-    """The populations f[19, ...] as a 16-bit shifted storage format holds
+    """The populations f[q, ...] (q = 15, 19 or 27) as a 16-bit shifted storage format holds
     them: s_i = f_i - w_i rounded to nearest-even, "f16s" to IEEE binary16,
     "bf16s" to bfloat16 (of s_i rounded to binary32 first, the compute type
     that produces it), and returned as w_i + s_i in float64; also the stored
     s itself.  Plain numpy; the definition of the storage, not of the step."""
-    _, w, _ = lattice()
+    _, w, _ = lattice(np.shape(f)[0])
     shp = (-1,) + (1,) * (np.ndim(f) - 1)
     s = np.asarray(f, dtype=np.float64) - w.reshape(shp)
     if storage == "f16s":
@@ -257,7 +292,7 @@ def init_equilibrium(cfg: Config, rho=None, u=None) -> np.ndarray:
     lib = _load()
     r = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64).reshape(cfg.shape)
     v = None if u is None else np.ascontiguousarray(u, dtype=np.float64).reshape(3, *cfg.shape)
-    f = np.zeros((Q, *cfg.shape), np.float64)
+    f = np.zeros((cfg.q, *cfg.shape), np.float64)
     lib.orc_init_equilibrium(ctypes.byref(cfg._c()), _ptr(r), _ptr(v), _ptr(f))
     return f
 
@@ -275,7 +310,7 @@ def step_cells(cfg: Config, f: np.ndarray, cells: np.ndarray) -> np.ndarray:
     lib = _load()
     fin = np.ascontiguousarray(f, dtype=np.float64)
     xyz = np.ascontiguousarray(cells, dtype=np.int64)
-    out = np.zeros((len(xyz), Q), np.float64)
+    out = np.zeros((len(xyz), cfg.q), np.float64)
     lib.orc_step_cells(ctypes.byref(cfg._c()), _ptr(fin), xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                        len(xyz), _ptr(out))
     return out

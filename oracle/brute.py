@@ -1,10 +1,12 @@
-"""Second, separately written FP64 D3Q19 update in numpy (test infrastructure).
+"""Second, separately written FP64 D3Q15 / D3Q19 / D3Q27 update in numpy (test
+infrastructure).
 
 This is a brute-force cross-check of ``lbm_oracle.c`` on tiny grids.  It is
 written differently on purpose:
 
-* the velocity set is generated (all vectors of {-1,0,1}^3 with |c|^2 <= 2) and
-  the weights come from |c|^2, instead of a typed-in table;
+* the velocity set is generated (the vectors of {-1,0,1}^3 whose |c|^2 the
+  lattice admits: {0,1,2} for D3Q19, {0,1,3} for D3Q15, all for D3Q27) and the
+  weights come from |c|^2, instead of a typed-in table;
 * collision runs on the whole field at once, then streaming moves each
   population plane with explicit target-index arithmetic, then the links that
   leave a non-periodic face are bounced back -- three separate passes, where the
@@ -24,20 +26,29 @@ import itertools
 import numpy as np
 
 
-def velocity_set():
-    """D3Q19 vectors and weights built from |c|^2 (order: sorted tuples)."""
-    cs = [c for c in itertools.product((-1, 0, 1), repeat=3) if sum(a * a for a in c) <= 2]
+# weight of a vector by its squared length, per lattice
+WEIGHTS = {
+    15: {0: 2.0 / 9.0, 1: 1.0 / 9.0, 3: 1.0 / 72.0},
+    19: {0: 1.0 / 3.0, 1: 1.0 / 18.0, 2: 1.0 / 36.0},
+    27: {0: 8.0 / 27.0, 1: 2.0 / 27.0, 2: 1.0 / 54.0, 3: 1.0 / 216.0},
+}
+
+
+def velocity_set(q=19):
+    """D3Q<q> vectors and weights built from |c|^2 (order: sorted tuples)."""
+    weight_of = WEIGHTS[q]
+    cs = [c for c in itertools.product((-1, 0, 1), repeat=3) if sum(a * a for a in c) in weight_of]
     cs.sort()
-    weight_of = {0: 1.0 / 3.0, 1: 1.0 / 18.0, 2: 1.0 / 36.0}
     c = np.array(cs, dtype=np.int64)
     w = np.array([weight_of[int((v * v).sum())] for v in c])
+    assert len(c) == q
     return c, w
 
 
 def collide(f, tau, F):
     """Post-collision populations for a whole field f[q, nz, ny, nx].
     F is [3, nz, ny, nx] (zeros for no force)."""
-    c, w = velocity_set()
+    c, w = velocity_set(f.shape[0])
     rho = f.sum(axis=0)
     mom = np.einsum("qa,qzyx->azyx", c.astype(np.float64), f)
     u = (mom + 0.5 * F) / rho
@@ -57,8 +68,8 @@ def stream(fs, periodic, face_lid, u_lid, rho_wall=1.0):
 
     periodic: (px, py, pz) booleans; face_lid: dict face-> bool for the six
     faces (0:x-,1:x+,2:y-,3:y+,4:z-,5:z+)."""
-    c, w = velocity_set()
     q, nz, ny, nx = fs.shape
+    c, w = velocity_set(q)
     dims = (nx, ny, nz)
     out = np.full_like(fs, np.nan)
     zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")

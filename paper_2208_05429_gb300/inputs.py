@@ -71,12 +71,12 @@ def random_density_velocity(nx: int, ny: int, nz: int, seed: int, drho: float = 
     return rho, u
 
 
-def population_noise(nx: int, ny: int, nz: int, seed: int, amp: float = 0.02) -> np.ndarray:
-    """noise[19, nz, ny, nx] = U(-amp, amp); entry k belongs to the k-th D3Q19
-    velocity in sorted (cx, cy, cz) order, so both implementations can map it
-    onto their own direction numbering."""
+def population_noise(nx: int, ny: int, nz: int, seed: int, amp: float = 0.02, q: int = 19) -> np.ndarray:
+    """noise[q, nz, ny, nx] = U(-amp, amp); entry k belongs to the k-th
+    velocity of D3Q<q> in sorted (cx, cy, cz) order, so both implementations
+    can map it onto their own direction numbering."""
     rng = np.random.default_rng(seed)
-    return rng.uniform(-amp, amp, size=(19, nz, ny, nx))
+    return rng.uniform(-amp, amp, size=(q, nz, ny, nx))
 
 
 def sample_cells(nx: int, ny: int, nz: int, k: int, seed: int = SEED_CELLS) -> np.ndarray:

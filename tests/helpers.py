@@ -1,4 +1,4 @@
-"""Test helpers: direction mapping between the two D3Q19 numberings and
+"""Test helpers: direction mapping between the two numberings of a lattice and
 conversions between the oracle's numpy arrays and the GPU's canonical
 tensors.  No lattice Boltzmann arithmetic lives here."""
 from __future__ import annotations
@@ -9,8 +9,8 @@ import oracle
 
 
 def perm_oracle_to(c_other: np.ndarray) -> np.ndarray:
-    """p with c_other[p[k]] == c_oracle[k] (both [19, 3])."""
-    c_o, _, _ = oracle.lattice()
+    """p with c_other[p[k]] == c_oracle[k] (both [q, 3], q = 15, 19 or 27)."""
+    c_o, _, _ = oracle.lattice(len(c_other))
     index = {tuple(int(v) for v in c): i for i, c in enumerate(c_other)}
     return np.array([index[tuple(int(v) for v in c)] for c in c_o], dtype=np.int64)
 
@@ -27,8 +27,8 @@ def noisy_equilibrium(cfg: "oracle.Config", seed: int, amp: float = 0.02, drho: 
     from paper_2208_05429_gb300 import inputs
     rho, u = inputs.random_density_velocity(cfg.nx, cfg.ny, cfg.nz, seed, drho=drho, umax=umax)
     f = oracle.init_equilibrium(cfg, rho, u)
-    noise = inputs.population_noise(cfg.nx, cfg.ny, cfg.nz, seed + 1, amp=amp)
-    c_o, _, _ = oracle.lattice()
+    noise = inputs.population_noise(cfg.nx, cfg.ny, cfg.nz, seed + 1, amp=amp, q=cfg.q)
+    c_o, _, _ = oracle.lattice(cfg.q)
     order = sorted_order(c_o)          # noise[k] belongs to the k-th sorted vector
     f_noise = np.empty_like(noise)
     f_noise[order] = noise
