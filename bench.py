@@ -213,19 +213,19 @@ def sync_all(dist_on):
 
 # ------------------------------------------------------------------ GPU legs
 
-def make_cavity(n, storage, variant, collision="bgk"):
+def make_cavity(n, storage, variant, collision="bgk", lattice=19):
     from paper_2208_05429_gb300.lbm import CAVITY_BC, Lattice
     return Lattice((n, n, n), TAU, bc=CAVITY_BC, u_lid=U_LID, storage=storage, variant=variant,
-                   collision=collision)
+                   collision=collision, lattice=lattice)
 
 
-def alg_bytes_per_launch(kernel: str, storage: str, cells: int) -> float:
+def alg_bytes_per_launch(kernel: str, storage: str, cells: int, q: int = Q) -> float:
     """Algorithmic DRAM bytes of one launch: every population read and written
     once per round trip (a merged sweep is one round trip for two steps)."""
-    return 2.0 * Q * ELEM[storage] * cells
+    return 2.0 * q * ELEM[storage] * cells
 
 
-def time_variant(n, storage, variant, steps, warmup, dist_on=False, sweep_env=None, collision="bgk"):
+def time_variant(n, storage, variant, steps, warmup, dist_on=False, sweep_env=None, collision="bgk", lattice=19):
     """(elapsed ms over `steps` calls of step(2), per-kernel records, lattice).
     sweep_env: value of LBM_MERGED_SWEEP while the lattice is created (None:
     the library's own choice)."""
@@ -234,7 +234,7 @@ def time_variant(n, storage, variant, steps, warmup, dist_on=False, sweep_env=No
     if sweep_env is not None:
         os.environ["LBM_MERGED_SWEEP"] = sweep_env
     try:
-        lat = make_cavity(n, storage, variant, collision)
+        lat = make_cavity(n, storage, variant, collision, lattice)
     finally:
         if sweep_env is not None:
             if old is None:
@@ -259,12 +259,12 @@ def time_variant(n, storage, variant, steps, warmup, dist_on=False, sweep_env=No
     return start.elapsed_time(end), lat.profile_read(), lat
 
 
-def roofline_of(prof, kernel, storage, cells, peak, peak_kind):
+def roofline_of(prof, kernel, storage, cells, peak, peak_kind, q=Q):
     if kernel not in prof:
         return None
     launches, ms = prof[kernel]
     avg = ms / launches
-    byts = alg_bytes_per_launch(kernel, storage, cells)
+    byts = alg_bytes_per_launch(kernel, storage, cells, q)
     achieved = byts / (avg * 1e-3) / 1e9
     traffic = recorded_traffic(f"{kernel}_{storage}_{round(cells ** (1 / 3))}")
     return {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
@@ -687,16 +687,18 @@ def main():
                              ("bf16s", "aa", None), ("f64", "aa", None), ("f32", "aa", "trt"),
                              ("f16s", "aa", "trt"), ("f32", "aa", "reg"), ("f16s", "aa", "reg"),
                              ("f32", "merged", "trt"), ("f32", "merged", "reg"), ("f32", "aa", "mrt"),
-                             ("f32", "merged", "mrt")):
+                             ("f32", "merged", "mrt"), ("f32", "aa", "d3q15"), ("f32", "aa", "d3q27"),
+                             ("f16s", "aa", "d3q27"), ("f32", "two_lattice", "d3q27")):
             if (st, var, env) == (args.storage, args.variant, None):
                 continue
             k = min(args.steps, 300)
             coll = env if env in ("trt", "reg", "mrt") else "bgk"
-            vms, vprof, vl = time_variant(n, st, var, k, 5, sweep_env=None if coll != "bgk" else env,
-                                          collision=coll)
+            q = int(env[3:]) if env and env.startswith("d3q") else Q
+            vms, vprof, vl = time_variant(n, st, var, k, 5, sweep_env=env if env == "shadow" else None,
+                                          collision=coll, lattice=q)
             del vl
             dk = {"merged": "merged", "aa": "aa_odd"}.get(var, "two_lattice")
-            r = roofline_of(vprof, dk, st, cells, peak, peak_kind)
+            r = roofline_of(vprof, dk, st, cells, peak, peak_kind, q)
             name = f"{var}_{env}_{st}" if env else f"{var}_{st}"
             variants[name] = {"MLUPS": round(cells * 2 * k / (vms * 1e3), 1),
                               "kernel_frac_of_peak": r["frac"] if r else None,

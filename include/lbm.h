@@ -22,8 +22,10 @@
  *  - Canonical field layout (inputs and outputs): x fastest, then y, then z:
  *      scalar field  a[z][y][x]              (N = nx*ny*nz elements)
  *      vector field  a[3][z][y][x]           (component-major)
- *      populations   f[19][z][y][x]          (direction-major, directions
- *                                             in the order lbm_lattice() reports)
+ *      populations   f[q][z][y][x]           (direction-major, q = 19, or
+ *                                             15 / 27 for those lattices,
+ *                                             directions in the order
+ *                                             lbm_lattice_q() reports)
  *  - Every launch is asynchronous on the stream given at creation.  Only
  *    lbm_reduce() and lbm_adjoint_* with host outputs synchronise it.
  *  - A handle is not thread-safe; use one handle per host thread.
@@ -122,6 +124,16 @@ enum { LBM_FORCE_NONE = 0, LBM_FORCE_UNIFORM = 1, LBM_FORCE_FIELD = 2 };
  * The adjoint calls return LBM_EUNSUPPORTED for a handle without BGK. */
 enum { LBM_COLLISION_BGK = 0, LBM_COLLISION_TRT = 1, LBM_COLLISION_REG = 2, LBM_COLLISION_MRT = 3 };
 
+/* Velocity set (lbm_config.lattice): D3Q19, the paper's lattice, or the two
+ * other cubic sets for which its dependency guard holds (Sec. 4.1): D3Q15
+ * (rest, 6 faces, 8 corners; w = 2/9, 1/9, 1/72) and D3Q27 (every vector of
+ * {-1, 0, 1}^3; w = 8/27, 2/27, 1/54, 1/216).  c_s^2 = 1/3 on all three.
+ * D3Q15 and D3Q27 run the single-step schedules (TWO_LATTICE, AA; MERGED
+ * runs the AA pair) with every storage format and the BGK, TRT and REG
+ * collisions; MRT and the adjoint calls return LBM_EUNSUPPORTED for them.
+ * 0 means D3Q19. */
+enum { LBM_LATTICE_D3Q15 = 15, LBM_LATTICE_D3Q19 = 19, LBM_LATTICE_D3Q27 = 27 };
+
 /* Element type of caller-provided field buffers. */
 enum { LBM_DTYPE_F32 = 0, LBM_DTYPE_F64 = 1 };
 
@@ -139,9 +151,10 @@ typedef struct lbm_config {
     double trt_lambda;        /* TRT magic product, > 0 (default 3/16)          */
     double mrt_s3, mrt_s4;    /* MRT rates of the third- and fourth-order
                                  moments, in (0, 2) (default 1)                 */
+    int32_t lattice;          /* LBM_LATTICE_* (default D3Q19; 0 = D3Q19)       */
 } lbm_config;
 
-/* Fill cfg with a 32^3 fully periodic FP32 AA lattice, tau = 0.6, BGK
+/* Fill cfg with a 32^3 fully periodic FP32 AA D3Q19 lattice, tau = 0.6, BGK
  * (trt_lambda = 3/16 and mrt_s3 = mrt_s4 = 1 for a later switch to TRT or
  * MRT). */
 void lbm_config_default(lbm_config *cfg);
@@ -149,8 +162,9 @@ void lbm_config_default(lbm_config *cfg);
 /* Check a configuration without allocating.  LBM_EINVAL on: a dimension < 1,
  * cell count beyond 2^31, tau <= 0.5, a face type out of range, an axis with
  * one periodic and one non-periodic face, |u_lid| >= 0.3, rho_wall <= 0,
- * unknown storage/variant/force mode or collision, a trt_lambda that is not
- * positive and finite, or an MRT rate outside (0, 2). */
+ * unknown storage/variant/force mode, collision or lattice, a trt_lambda that
+ * is not positive and finite, or an MRT rate outside (0, 2).
+ * LBM_EUNSUPPORTED for MRT on D3Q15 or D3Q27. */
 int lbm_validate(const lbm_config *cfg);
 
 /* Device bytes a handle of this configuration uses (populations, second
@@ -190,6 +204,13 @@ const char *lbm_strerror(int status);
  * Sec. 3 streams to), direction i+9 is the opposite of i, 0 is rest. */
 int lbm_lattice(int32_t *c, double *w);
 
+/* The table of lattice q (LBM_LATTICE_*, 0 = D3Q19): c[q][3] and w[q] (host
+ * outputs, either may be NULL), ordered by the same rule: 0 is rest,
+ * directions 1 .. (q-1)/2 have -1 as first non-zero component (in
+ * lexicographic (cx, cy, cz) order for D3Q15 and D3Q27), direction
+ * i + (q-1)/2 is the opposite of i.  LBM_EINVAL for another q. */
+int lbm_lattice_q(int32_t q, int32_t *c, double *w);
+
 /* Populations of every cell := equilibrium feq(rho, u) (second-order BGK
  * equilibrium) and the time counter := 0.  rho: device [z][y][x] or NULL
  * (rho = 1); u: device [3][z][y][x] or NULL (u = 0); both of element type
@@ -219,7 +240,8 @@ int lbm_time(const lbm_handle *h, int64_t *t);
 int lbm_moments(lbm_handle *h, void *rho, void *u, int32_t dtype);
 
 /* Copy out the post-stream populations f^n in canonical layout
- * f[19][z][y][x] (device, element type `dtype`, directions as lbm_lattice()). */
+ * f[q][z][y][x] (device, element type `dtype`, directions as lbm_lattice_q()
+ * of the handle's lattice). */
 int lbm_populations(lbm_handle *h, void *f_out, int32_t dtype);
 
 /* Replace the state with caller populations f_in (device, canonical layout,
@@ -250,7 +272,8 @@ int lbm_reduce(lbm_handle *h, double *out);
  *   cfg    lattice sizes and body force (force_mode, force_uniform); the
  *          whole config must pass lbm_validate(), so lattices beyond
  *          2^31 - 1 cells are rejected with LBM_EINVAL; storage, variant
- *          and collision are ignored
+ *          and collision are ignored; the lattice must be D3Q19
+ *          (LBM_EUNSUPPORTED otherwise)
  *   f      device, canonical natural-parity populations f[19][z][y][x] of
  *          element type `dtype` (LBM_DTYPE_F32 or _F64), directions as
  *          lbm_lattice() -- what lbm_populations() writes

@@ -1,0 +1,10 @@
+// inst_dq_bf16s.cu -- D3Q15 and D3Q27 kernels and launchers of the BF16S storage format.
+#include "dqn.cuh"
+
+namespace lbm {
+const StorageOps *ops_dq_bf16s(int q)
+{
+    static const StorageOps q15 = make_ops_q<15, StoreBF16S>(), q27 = make_ops_q<27, StoreBF16S>();
+    return q == 15 ? &q15 : (q == 27 ? &q27 : nullptr);
+}
+}  // namespace lbm

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "d3q19.cuh"
+#include "lattice.cuh"
 #include "lbm.h"
 #include "ops.h"
 
@@ -118,10 +119,29 @@ const StorageOps *ops_for(int storage)
     }
 }
 
+// Velocities of the configuration's lattice (lattice 0 is D3Q19).
+inline int lat_q(const lbm_config &c) { return c.lattice == 0 ? 19 : c.lattice; }
+
+// The launch table of a configuration: the D3Q19 kernels of its storage
+// format, or the single-step D3Q15 / D3Q27 kernels.
+const StorageOps *ops_for_cfg(const lbm_config &c)
+{
+    const int q = lat_q(c);
+    if (q == 19) return ops_for(c.storage);
+    switch (c.storage) {
+    case LBM_STORAGE_F64: return ops_dq_f64(q);
+    case LBM_STORAGE_F32: return ops_dq_f32(q);
+    case LBM_STORAGE_F32S: return ops_dq_f32s(q);
+    case LBM_STORAGE_F16S: return ops_dq_f16s(q);
+    case LBM_STORAGE_BF16S: return ops_dq_bf16s(q);
+    default: return nullptr;
+    }
+}
+
 // Row pitch: nx rounded up to 16 elements.
 inline int64_t pitch_of(const lbm_config &c) { return (c.nx + 15) / 16 * 16; }
 
-inline int64_t state_elems(const lbm_config &c) { return (int64_t)Q * c.nz * c.ny * pitch_of(c); }
+inline int64_t state_elems(const lbm_config &c) { return (int64_t)lat_q(c) * c.nz * c.ny * pitch_of(c); }
 
 size_t elem_size_of(int storage)
 {
@@ -158,7 +178,7 @@ int coll_of(const lbm_config &c)
 
 bool uses_ns(const lbm_config &c, const ShellInfo &si)
 {
-    if (c.variant != LBM_VARIANT_MERGED) return false;
+    if (c.variant != LBM_VARIANT_MERGED || lat_q(c) != 19) return false;
     bool any_count = false;
     if (const char *e = getenv("LBM_MERGED_SWEEP")) {
         if (strcmp(e, "shadow") == 0) return false;
@@ -176,7 +196,7 @@ bool uses_ns(const lbm_config &c, const ShellInfo &si)
 // si: the tiles of c (shell_info), computed once per query or creation.
 bool uses_m3(const lbm_config &c, const ShellInfo &si)
 {
-    if (c.variant != LBM_VARIANT_MERGED) return false;
+    if (c.variant != LBM_VARIANT_MERGED || lat_q(c) != 19) return false;
     if (uses_ns(c, si)) return false;
     // the shadow-shell sweep is built for BGK only
     if (c.collision != LBM_COLLISION_BGK) return false;
@@ -287,10 +307,16 @@ HostGeom host_geom(const lbm_config &c)
     h.kf_m = 1.0 - 0.5 * h.omega_m;
     h.mrt_s3 = c.mrt_s3;
     h.mrt_s4 = c.mrt_s4;
-    for (int k = 0; k < Q; ++k) {
-        const double cu = cx(k) * c.u_lid[0] + cy(k) * c.u_lid[1] + cz(k) * c.u_lid[2];
-        h.L[k] = 6.0 * wgt(k) * c.rho_wall * cu;
-    }
+    h.q = lat_q(c);
+    auto lid_terms = [&](auto cxf, auto cyf, auto czf, auto wf) {
+        for (int k = 0; k < h.q; ++k) {
+            const double cu = cxf(k) * c.u_lid[0] + cyf(k) * c.u_lid[1] + czf(k) * c.u_lid[2];
+            h.L[k] = 6.0 * wf(k) * c.rho_wall * cu;
+        }
+    };
+    if (h.q == 15) lid_terms(DQ<15>::cx, DQ<15>::cy, DQ<15>::cz, DQ<15>::wgt);
+    else if (h.q == 27) lid_terms(DQ<27>::cx, DQ<27>::cy, DQ<27>::cz, DQ<27>::wgt);
+    else lid_terms(cx, cy, cz, wgt);
     if (c.force_mode == LBM_FORCE_UNIFORM)
         for (int a = 0; a < 3; ++a) h.Fu[a] = c.force_uniform[a];
     h.Ff = nullptr;
@@ -410,6 +436,7 @@ void lbm_config_default(lbm_config *cfg)
     cfg->trt_lambda = 3.0 / 16.0;
     cfg->mrt_s3 = 1.0;
     cfg->mrt_s4 = 1.0;
+    cfg->lattice = LBM_LATTICE_D3Q19;
 }
 
 int lbm_validate(const lbm_config *c)
@@ -435,6 +462,10 @@ int lbm_validate(const lbm_config *c)
     if (c->collision < LBM_COLLISION_BGK || c->collision > LBM_COLLISION_MRT) return LBM_EINVAL;
     if (!(c->mrt_s3 > 0.0 && c->mrt_s3 < 2.0) || !(c->mrt_s4 > 0.0 && c->mrt_s4 < 2.0)) return LBM_EINVAL;
     if (!(c->trt_lambda > 0.0) || !isfinite(c->trt_lambda)) return LBM_EINVAL;
+    if (c->lattice != 0 && c->lattice != LBM_LATTICE_D3Q15 && c->lattice != LBM_LATTICE_D3Q19 &&
+        c->lattice != LBM_LATTICE_D3Q27)
+        return LBM_EINVAL;
+    if (lat_q(*c) != 19 && c->collision == LBM_COLLISION_MRT) return LBM_EUNSUPPORTED;
     return LBM_OK;
 }
 
@@ -463,7 +494,7 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
     h->cfg = *cfg;
     h->stream = (cudaStream_t)stream;
     if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return LBM_ECUDA; }
-    h->ops = ops_for(cfg->storage);
+    h->ops = ops_for_cfg(*cfg);
     h->hg = host_geom(*cfg);
     h->nxp = pitch_of(*cfg);
     h->force = cfg->force_mode != LBM_FORCE_NONE;
@@ -587,6 +618,21 @@ int lbm_lattice(int32_t *c, double *w)
         if (c) { c[3 * i] = cx(i); c[3 * i + 1] = cy(i); c[3 * i + 2] = cz(i); }
         if (w) w[i] = wgt(i);
     }
+    return LBM_OK;
+}
+
+int lbm_lattice_q(int32_t q, int32_t *c, double *w)
+{
+    auto fill = [&](int n, auto cxf, auto cyf, auto czf, auto wf) {
+        for (int i = 0; i < n; ++i) {
+            if (c) { c[3 * i] = cxf(i); c[3 * i + 1] = cyf(i); c[3 * i + 2] = czf(i); }
+            if (w) w[i] = wf(i);
+        }
+    };
+    if (q == 0 || q == LBM_LATTICE_D3Q19) return lbm_lattice(c, w);
+    if (q == LBM_LATTICE_D3Q15) fill(15, DQ<15>::cx, DQ<15>::cy, DQ<15>::cz, DQ<15>::wgt);
+    else if (q == LBM_LATTICE_D3Q27) fill(27, DQ<27>::cx, DQ<27>::cy, DQ<27>::cz, DQ<27>::wgt);
+    else return LBM_EINVAL;
     return LBM_OK;
 }
 
@@ -884,7 +930,7 @@ int lbm_profile_read(lbm_handle *h, int32_t kernel, int64_t *launches, double *t
 int lbm_adjoint_step(lbm_handle *h, const void *f_t, const void *lambda_in, void *lambda_out, int32_t dtype,
                      double *dLdF)
 {
-    if (h && h->cfg.collision != LBM_COLLISION_BGK) return LBM_EUNSUPPORTED;
+    if (h && (h->cfg.collision != LBM_COLLISION_BGK || lat_q(h->cfg) != 19)) return LBM_EUNSUPPORTED;
     if (!h || !f_t || !lambda_in || !lambda_out || lambda_in == lambda_out || check_dtype(dtype)) return LBM_EINVAL;
     if (!h->force_set) return LBM_ESTATE;
     DeviceGuard g(h->device);
@@ -895,7 +941,7 @@ int lbm_adjoint_step(lbm_handle *h, const void *f_t, const void *lambda_in, void
 
 int lbm_adjoint_seed(lbm_handle *h, const void *dLdrho, const void *dLdu, void *lambda, int32_t dtype, double *dLdF)
 {
-    if (h && h->cfg.collision != LBM_COLLISION_BGK) return LBM_EUNSUPPORTED;
+    if (h && (h->cfg.collision != LBM_COLLISION_BGK || lat_q(h->cfg) != 19)) return LBM_EUNSUPPORTED;
     if (!h || !dLdu || !lambda || check_dtype(dtype)) return LBM_EINVAL;
     if (!h->force_set) return LBM_ESTATE;
     DeviceGuard g(h->device);
@@ -937,13 +983,14 @@ AdjLayout adj_layout(const lbm_handle *h, int64_t T, int64_t K)
 int lbm_adjoint_workspace_bytes(const lbm_handle *h, int64_t T, int64_t K, size_t *bytes)
 {
     if (!h || !bytes || T < 1 || K < 1) return LBM_EINVAL;
+    if (lat_q(h->cfg) != 19) return LBM_EUNSUPPORTED;
     *bytes = adj_layout(h, T, K).total;
     return LBM_OK;
 }
 
 int lbm_adjoint_forward(lbm_handle *h, int64_t T, int64_t K, void *work, size_t work_bytes)
 {
-    if (h && h->cfg.collision != LBM_COLLISION_BGK) return LBM_EUNSUPPORTED;
+    if (h && (h->cfg.collision != LBM_COLLISION_BGK || lat_q(h->cfg) != 19)) return LBM_EUNSUPPORTED;
     if (!h || !work || T < 1 || K < 1 || ((uintptr_t)work % ALIGN) != 0) return LBM_EINVAL;
     if (!h->force_set) return LBM_ESTATE;
     const AdjLayout A = adj_layout(h, T, K);

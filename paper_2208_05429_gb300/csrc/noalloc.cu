@@ -78,6 +78,7 @@ extern "C" int lbm_reduce_populations(const lbm_config *cfg, const void *f, int3
     // never need more than RED_BLOCKS_MAX blocks whatever the size.
     if (!cfg || !f || !out) return LBM_EINVAL;
     if (lbm_validate(cfg) != LBM_OK) return LBM_EINVAL;
+    if (cfg->lattice != 0 && cfg->lattice != LBM_LATTICE_D3Q19) return LBM_EUNSUPPORTED;
     if (dtype != LBM_DTYPE_F32 && dtype != LBM_DTYPE_F64) return LBM_EINVAL;
     if (cfg->force_mode == LBM_FORCE_FIELD && !F) return LBM_EINVAL;
     double *scratch = nullptr;

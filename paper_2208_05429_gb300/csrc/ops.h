@@ -18,7 +18,8 @@ struct HostGeom {
     int coll;            // collision: 0 BGK, 1 TRT, 2 regularised BGK, 3 MRT
     double omega_m, kf_m;
     double mrt_s3, mrt_s4;
-    double L[19];
+    int q;               // lattice: 15, 19 or 27 velocities
+    double L[27];        // 6 w_k rho_w (c_k . u_lid), k < q
     double Fu[3];
     const float *Ff;
 };
@@ -112,6 +113,13 @@ const StorageOps &ops_f32();
 const StorageOps &ops_f32s();
 const StorageOps &ops_f16s();
 const StorageOps &ops_bf16s();
+// the D3Q15 / D3Q27 single-step kernels of one storage format (q = 15 or
+// 27; null otherwise)
+const StorageOps *ops_dq_f64(int q);
+const StorageOps *ops_dq_f32(int q);
+const StorageOps *ops_dq_f32s(int q);
+const StorageOps *ops_dq_f16s(int q);
+const StorageOps *ops_dq_bf16s(int q);
 
 constexpr int RED_BLOCKS_MAX = 1024;
 // ints per tile of the neighbour-synchronised sweep's progress words (one

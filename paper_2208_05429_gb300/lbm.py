@@ -27,6 +27,7 @@ LBM_STORAGE_F64, LBM_STORAGE_F32, LBM_STORAGE_F32S, LBM_STORAGE_F16S, LBM_STORAG
 LBM_VARIANT_TWO_LATTICE, LBM_VARIANT_AA, LBM_VARIANT_MERGED = 0, 1, 2
 LBM_FORCE_NONE, LBM_FORCE_UNIFORM, LBM_FORCE_FIELD = 0, 1, 2
 LBM_DTYPE_F32, LBM_DTYPE_F64 = 0, 1
+LBM_LATTICE_D3Q15, LBM_LATTICE_D3Q19, LBM_LATTICE_D3Q27 = 15, 19, 27
 LBM_COLLISION_BGK, LBM_COLLISION_TRT, LBM_COLLISION_REG, LBM_COLLISION_MRT = 0, 1, 2, 3
 COLLISION = {"bgk": LBM_COLLISION_BGK, "trt": LBM_COLLISION_TRT, "reg": LBM_COLLISION_REG, "mrt": LBM_COLLISION_MRT}
 LBM_KERNEL_TWO_LATTICE, LBM_KERNEL_AA_EVEN, LBM_KERNEL_AA_ODD, LBM_KERNEL_SNAPSHOT, LBM_KERNEL_MERGED = \
@@ -65,6 +66,7 @@ class lbm_config(ctypes.Structure):
         ("trt_lambda", ctypes.c_double),
         ("mrt_s3", ctypes.c_double),
         ("mrt_s4", ctypes.c_double),
+        ("lattice", ctypes.c_int32),
     ]
 
 
@@ -80,6 +82,7 @@ _SIGNATURES = {
     "lbm_destroy": (None, [_H]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "lbm_lattice": (ctypes.c_int, [_VP, _VP]),
+    "lbm_lattice_q": (ctypes.c_int, [ctypes.c_int32, _VP, _VP]),
     "lbm_init_equilibrium": (ctypes.c_int, [_H, _VP, _VP, ctypes.c_int32]),
     "lbm_set_force": (ctypes.c_int, [_H, _VP]),
     "lbm_step": (ctypes.c_int, [_H, ctypes.c_int64]),
@@ -198,6 +201,14 @@ def lbm_lattice() -> Tuple[np.ndarray, np.ndarray]:
     return c.astype(np.int64), w
 
 
+def lbm_lattice_q(q: int) -> Tuple[np.ndarray, np.ndarray]:
+    """c[q, 3], w[q] of lattice D3Q<q> (15, 19 or 27) in the library's order."""
+    c = np.zeros((q, 3), np.int32)
+    w = np.zeros(q, np.float64)
+    _check(library().lbm_lattice_q(int(q), c.ctypes.data, w.ctypes.data), "lbm_lattice_q")
+    return c.astype(np.int64), w
+
+
 def lbm_init_equilibrium(h, rho=None, u=None, dtype_code: int = LBM_DTYPE_F32):
     _check(library().lbm_init_equilibrium(h, _ptr(rho), _ptr(u), dtype_code), "lbm_init_equilibrium")
 
@@ -295,8 +306,9 @@ def make_config(shape: Sequence[int], tau: float, bc: Sequence[Union[str, int]] 
                 u_lid=(0.0, 0.0, 0.0), rho_wall: float = 1.0, storage: str = "f32", variant: str = "aa",
                 force_mode: int = LBM_FORCE_NONE, force_uniform=(0.0, 0.0, 0.0),
                 collision: Union[str, int] = "bgk", trt_lambda: float = 3.0 / 16.0,
-                mrt_s3: float = 1.0, mrt_s4: float = 1.0) -> lbm_config:
-    """Build an lbm_config; shape is (nx, ny, nz), bc lists x-, x+, y-, y+, z-, z+."""
+                mrt_s3: float = 1.0, mrt_s4: float = 1.0, lattice: int = 19) -> lbm_config:
+    """Build an lbm_config; shape is (nx, ny, nz), bc lists x-, x+, y-, y+, z-, z+;
+    lattice is 15, 19 or 27 (D3Q15, D3Q19, D3Q27)."""
     c = lbm_config()
     c.nx, c.ny, c.nz = (int(v) for v in shape)
     c.tau = float(tau)
@@ -313,6 +325,7 @@ def make_config(shape: Sequence[int], tau: float, bc: Sequence[Union[str, int]] 
     c.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
     c.trt_lambda = float(trt_lambda)
     c.mrt_s3, c.mrt_s4 = float(mrt_s3), float(mrt_s4)
+    c.lattice = int(lattice)
     return c
 
 
@@ -320,7 +333,8 @@ CAVITY_BC = ("wall", "wall", "wall", "wall", "wall", "lid")
 
 
 class Lattice:
-    """One D3Q19 lattice on a GPU, memory owned by a torch tensor.
+    """One D3Q19 (or D3Q15 / D3Q27: ``lattice=15`` / ``27``) lattice on a GPU,
+    memory owned by a torch tensor.
 
     force: None (no force), a 3-sequence (uniform force), or a float32 CUDA
     tensor [3, nz, ny, nx] (per-cell force field, kept alive here).
@@ -329,7 +343,7 @@ class Lattice:
     def __init__(self, shape, tau: float, bc=("periodic",) * 6, u_lid=(0.0, 0.0, 0.0), rho_wall: float = 1.0,
                  storage: str = "f32", variant: str = "aa", force=None, device=None, stream=None,
                  collision: str = "bgk", trt_lambda: float = 3.0 / 16.0, mrt_s3: float = 1.0,
-                 mrt_s4: float = 1.0):
+                 mrt_s4: float = 1.0, lattice: int = 19):
         import torch
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         if force is None:
@@ -339,7 +353,8 @@ class Lattice:
         else:
             fm, fu = LBM_FORCE_UNIFORM, tuple(float(v) for v in force)
         self.cfg = make_config(shape, tau, bc, u_lid, rho_wall, storage, variant, fm, fu, collision, trt_lambda,
-                               mrt_s3, mrt_s4)
+                               mrt_s3, mrt_s4, lattice)
+        self.q = int(lattice) or Q
         self.shape = tuple(int(v) for v in shape)  # (nx, ny, nz)
         self.nbytes = lbm_required_bytes(self.cfg)
         with torch.cuda.device(self.device):
@@ -406,11 +421,13 @@ class Lattice:
     def populations(self, dtype=None):
         import torch
         dtype = dtype or torch.float32
-        f = self._empty((Q,), dtype)
+        f = self._empty((self.q,), dtype)
         lbm_populations(self.h, f, _dtype_code(dtype))
         return f
 
     def init_populations(self, f):
+        if tuple(f.shape) != (self.q,) + self.field_shape:
+            raise ValueError(f"populations of shape {tuple(f.shape)}: expected {(self.q,) + self.field_shape}")
         f = f.to(self.device).contiguous()
         lbm_init_populations(self.h, f, _dtype_code(f.dtype))
         self._keep = f

@@ -8,7 +8,7 @@ import numpy as np
 import oracle
 from oracle import BC_LID, BC_PERIODIC, BC_WALL, FORCE_FIELD, FORCE_NONE, FORCE_UNIFORM
 from paper_2208_05429_gb300 import inputs
-from paper_2208_05429_gb300.lbm import Lattice, lbm_lattice
+from paper_2208_05429_gb300.lbm import Lattice, lbm_lattice, lbm_lattice_q
 from helpers import noisy_equilibrium, perm_oracle_to
 
 P, W, L = BC_PERIODIC, BC_WALL, BC_LID
@@ -36,8 +36,8 @@ def cases():
     return c
 
 
-def gpu_perm():
-    c_gpu, _ = lbm_lattice()
+def gpu_perm(q: int = 19):
+    c_gpu, _ = lbm_lattice() if q == 19 else lbm_lattice_q(q)
     p = perm_oracle_to(c_gpu)          # c_gpu[p[k]] == c_oracle[k]
     inv = np.empty_like(p)
     inv[p] = np.arange(len(p))
@@ -45,12 +45,12 @@ def gpu_perm():
 
 
 def to_gpu_order(f_oracle: np.ndarray) -> np.ndarray:
-    _, inv = gpu_perm()
+    _, inv = gpu_perm(len(f_oracle))
     return f_oracle[inv]
 
 
 def to_oracle_order(f_gpu: np.ndarray) -> np.ndarray:
-    p, _ = gpu_perm()
+    p, _ = gpu_perm(len(f_gpu))
     return f_gpu[p]
 
 
@@ -66,7 +66,7 @@ def make_gpu(cfg: "oracle.Config", storage: str, variant: str, device="cuda:0") 
                    rho_wall=cfg.rho_wall, storage=storage, variant=variant, force=force, device=device,
                    collision={oracle.COLL_TRT: "trt", oracle.COLL_REG: "reg", oracle.COLL_MRT: "mrt"}.get(
                        cfg.collision, "bgk"),
-                   trt_lambda=cfg.trt_lambda, mrt_s3=cfg.mrt_s3, mrt_s4=cfg.mrt_s4)
+                   trt_lambda=cfg.trt_lambda, mrt_s3=cfg.mrt_s3, mrt_s4=cfg.mrt_s4, lattice=cfg.q)
 
 
 def oracle_force_as_f32(cfg: "oracle.Config") -> "oracle.Config":

@@ -29,6 +29,54 @@ def test_lattice_table(cuda_lib):
     assert np.allclose(np.einsum("q,qa,qb->ab", w, c, c), np.eye(3) / 3, atol=1e-16)
 
 
+@pytest.mark.parametrize("q", [15, 27])
+def test_other_lattice_tables(cuda_lib, q):
+    """D3Q15 / D3Q27: the admitted vectors, the half-neighbour order, and the
+    weights from the moment identities (up to fourth order; for D3Q27 the
+    D1Q3 product rule sum w cx^2 cy^2 cz^2 = 1/27)."""
+    import itertools
+    c, w = lbm.lbm_lattice_q(q)
+    norms = {15: {0, 1, 3}, 27: {0, 1, 2, 3}}[q]
+    vecs = [tuple(int(a) for a in v) for v in c]
+    assert set(vecs) == {v for v in itertools.product((-1, 0, 1), repeat=3) if sum(a * a for a in v) in norms}
+    h = (q - 1) // 2
+    assert vecs[0] == (0, 0, 0)
+    for i in range(1, h + 1):
+        assert next(a for a in vecs[i] if a != 0) == -1
+        assert np.array_equal(c[i + h], -c[i])
+    assert vecs[1:h + 1] == sorted(vecs[1:h + 1])       # lexicographic within the half
+    cf = c.astype(np.float64)
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.allclose(np.einsum("q,qa,qb->ab", w, cf, cf), np.eye(3) / 3, atol=1e-16)
+    assert abs(np.sum(w * cf[:, 0] ** 2 * cf[:, 1] ** 2) - 1.0 / 9.0) < 1e-16
+    if q == 27:
+        assert abs(np.sum(w * cf[:, 0] ** 2 * cf[:, 1] ** 2 * cf[:, 2] ** 2) - 1.0 / 27.0) < 1e-16
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_lattice_q(21)
+    # the 19-velocity query is lbm_lattice's table
+    assert np.array_equal(lbm.lbm_lattice_q(19)[0], lbm.lbm_lattice()[0])
+
+
+@pytest.mark.parametrize("q", [15, 27])
+def test_other_lattices_validate(cuda_lib, q):
+    for variant in ("aa", "two_lattice", "merged"):
+        for storage in ("f64", "f32", "f32s", "f16s", "bf16s"):
+            for coll in ("bgk", "trt", "reg"):
+                cfg = lbm.make_config((16, 16, 16), 0.7, lbm.CAVITY_BC, storage=storage, variant=variant,
+                                      collision=coll, lattice=q)
+                assert lbm.lbm_validate(cfg) == lbm.LBM_OK, (variant, storage, coll)
+    cfg = lbm.make_config((16, 16, 16), 0.7, collision="mrt", lattice=q)
+    assert lbm.lbm_validate(cfg) == lbm.LBM_EUNSUPPORTED
+    pop = q * 64 ** 3 * 4
+    aa = lbm.make_config((64, 64, 64), 0.6, storage="f32", variant="aa", lattice=q)
+    mg = lbm.make_config((64, 64, 64), 0.6, lbm.CAVITY_BC, storage="f32", variant="merged", lattice=q)
+    assert pop <= lbm.lbm_required_bytes(aa) < pop * 1.01
+    assert pop <= lbm.lbm_required_bytes(mg) < pop * 1.01      # MERGED runs the AA pair: no shadow
+    for bad in (21, 9, -1):
+        cfg = lbm.make_config((16, 16, 16), 0.7, lattice=bad)
+        assert lbm.lbm_validate(cfg) == lbm.LBM_EINVAL
+
+
 def test_lattice_table_is_the_one_the_schedule_tests_restate(cuda_lib):
     from test_merged_schedule import GPU_C
     c, _ = lbm.lbm_lattice()
@@ -94,11 +142,12 @@ def test_strerror(cuda_lib):
 def test_config_struct_layout_matches_header(cuda_lib):
     """The ctypes mirror of lbm_config has the C layout (checked through a
     round trip: lbm_config_default writes every field)."""
-    assert ctypes.sizeof(lbm.lbm_config) == 160
+    assert ctypes.sizeof(lbm.lbm_config) == 168
     cfg = lbm.lbm_config_default()
     assert cfg.tau == 0.6 and cfg.rho_wall == 1.0 and list(cfg.face_bc) == [0] * 6
     assert cfg.storage == lbm.LBM_STORAGE_F32 and cfg.variant == lbm.LBM_VARIANT_AA
     assert cfg.collision == lbm.LBM_COLLISION_BGK and cfg.trt_lambda == 3.0 / 16.0
+    assert cfg.lattice == lbm.LBM_LATTICE_D3Q19
 
 
 def test_create_without_gpu_fails_cleanly(cuda_lib):
