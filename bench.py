@@ -65,8 +65,8 @@ ELEM = {"f64": 8, "f32": 4, "f32s": 4, "f16s": 2, "bf16s": 2}
 DTYPE_NAME = {"f64": "f64", "f32": "f32", "f32s": "f32", "f16s": "f32 (f16 storage)", "bf16s": "f32 (bf16 storage)"}
 
 
-def workload_name(n: int) -> str:
-    return (f"lid-driven cavity {n}^3, D3Q19 BGK, tau={TAU}, lid u=(0.05,0,0) on z+, half-way bounce-back "
+def workload_name(n: int, q: int = Q) -> str:
+    return (f"lid-driven cavity {n}^3, D3Q{q} BGK, tau={TAU}, lid u=(0.05,0,0) on z+, half-way bounce-back "
             f"on the other faces, initial rest state")
 
 
@@ -79,6 +79,8 @@ def parse():
     p.add_argument("--size", type=int, default=256)
     p.add_argument("--storage", default="f32", choices=sorted(ELEM))
     p.add_argument("--variant", default="merged", choices=["merged", "aa", "two_lattice"])
+    p.add_argument("--lattice", type=int, default=Q, choices=[15, 19, 27],
+                   help="velocity set of the timed leg (D3Q15 and D3Q27: single-step schedules)")
     p.add_argument("--no-extras", action="store_true", help="skip the per-variant, adjoint and CPU legs")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle baseline")
     p.add_argument("--sweep", action="store_true", help="cavity size sweep (prints its own JSON line)")
@@ -266,7 +268,7 @@ def roofline_of(prof, kernel, storage, cells, peak, peak_kind, q=Q):
     avg = ms / launches
     byts = alg_bytes_per_launch(kernel, storage, cells, q)
     achieved = byts / (avg * 1e-3) / 1e9
-    traffic = recorded_traffic(f"{kernel}_{storage}_{round(cells ** (1 / 3))}")
+    traffic = recorded_traffic(f"{kernel}_{storage}_{round(cells ** (1 / 3))}" + ("" if q == Q else f"_d3q{q}"))
     return {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
             "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
             "alg_bytes_per_launch": byts, "avg_launch_ms": round(avg, 5), "launches": launches}
@@ -644,7 +646,8 @@ def main():
 
     sampler = ClockSampler(local)
     sampler.start()
-    ms, prof, lat = time_variant(n, args.storage, args.variant, args.steps, args.warmup, dist_on)
+    ms, prof, lat = time_variant(n, args.storage, args.variant, args.steps, args.warmup, dist_on,
+                                 lattice=args.lattice)
     clocks = sampler.stop()
     ms = slowest_rank_ms(ms, dist_on, "cuda")
     # mass check of the timed state: a broken kernel shows up here
@@ -654,7 +657,9 @@ def main():
 
     value = whole_job_mlups(world, cells, args.steps, ms)
     dominant = {"merged": "merged", "aa": "aa_odd"}.get(args.variant, "two_lattice")
-    roof = roofline_of(prof, dominant, args.storage, cells, peak, peak_kind)
+    if args.lattice != Q and dominant == "merged":
+        dominant = "aa_odd"   # MERGED runs the AA pair on D3Q15 / D3Q27
+    roof = roofline_of(prof, dominant, args.storage, cells, peak, peak_kind, args.lattice)
     launches = sum(v[0] for v in prof.values())
     if "snapshot" in prof and roof is not None:
         sn, sms = prof["snapshot"]
@@ -667,10 +672,10 @@ def main():
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[args.storage], "data": "synthetic",
-        "config": {"workload": workload_name(n), "cells": cells, "time_steps_per_step": 2,
+        "config": {"workload": workload_name(n, args.lattice), "cells": cells, "time_steps_per_step": 2,
                    "storage": args.storage, "variant": args.variant,
                    "l2": "no flush: the populations (%.2f GB) are larger than the 129 MB L2" %
-                         (Q * ELEM[args.storage] * cells / 1e9),
+                         (args.lattice * ELEM[args.storage] * cells / 1e9),
                    "parallelism": "independent replicas, one per GPU" if dist_on else "single GPU"},
         "roofline": roof, "gpu_launches": launches, "clocks": clocks, "mass_conserved": bool(ok),
     }

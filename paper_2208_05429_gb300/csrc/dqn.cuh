@@ -231,36 +231,6 @@ __device__ __forceinline__ void dq_load_aparity(const Geom<typename S::R> &g, co
     });
 }
 
-// Two-lattice push rule: f*_i to slot i of x + c_i, or (wall link) to slot
-// opp(i) of x with the lid term of a lid face.
-template <class L, class S>
-__device__ __forceinline__ void dq_push(const Geom<typename S::R> &g, const LidQ<typename S::R, L::Q> &lq,
-                                        typename S::T *__restrict__ dst, int x, int y, int z, int64_t c,
-                                        const typename S::R (&s)[L::Q])
-{
-    using R = typename S::R;
-    if (interior(g, x, y, z)) {
-        static_for<L::Q>([&](auto K) {
-            constexpr int i = decltype(K)::value;
-            const int64_t off = (int64_t)L::cz(i) * g.plane + (int64_t)L::cy(i) * g.nxp + L::cx(i);
-            dst[i * g.slot + c + off] = dq_encode<S>(s[i], R(L::wgt(i)));
-        });
-    } else {
-        static_for<L::Q>([&](auto K) {
-            constexpr int i = decltype(K)::value;
-            int tx, ty, tz;
-            bool lid;
-            if (link(g, x, y, z, L::cx(i), L::cy(i), L::cz(i), tx, ty, tz, lid)) {
-                dst[i * g.slot + cell_of(g, tx, ty, tz)] = dq_encode<S>(s[i], R(L::wgt(i)));
-            } else {
-                R v = s[i];
-                if (lid) v = radd(v, lq.L[L::opp(i)]);
-                dst[L::opp(i) * g.slot + c] = dq_encode<S>(v, R(L::wgt(i)));
-            }
-        });
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
@@ -291,35 +261,162 @@ __global__ void k_q_init_eq(Geom<typename S::R> g, typename S::T *__restrict__ f
     });
 }
 
+// Base pointer of every direction slot of lattice QN (kernel parameters, so
+// that each access is one 32-bit cell index away from a parameter).
+template <class T, int QN>
+struct DirsQ {
+    T *p[QN];
+};
+
+// Cell-index offset of x + c_i from x (no wrap).
+template <class L, int I>
+inline int64_t dq_noff(int64_t plane, int64_t pitch)
+{
+    return (int64_t)L::cz(I) * plane + (int64_t)L::cy(I) * pitch + L::cx(I);
+}
+
+// Natural-parity loads of cell c from per-direction base pointers.
+template <class L, class S>
+__device__ __forceinline__ void dq_load_natural_d(const DirsQ<const typename S::T, L::Q> &f, int c,
+                                                  typename S::R (&s)[L::Q])
+{
+    using R = typename S::R;
+    static_for<L::Q>([&](auto K) {
+        constexpr int i = decltype(K)::value;
+        s[i] = dq_decode<S>(f.p[i][c], R(L::wgt(i)));
+    });
+}
+
+// A-parity gather: f_k(x) from slot opp(k) of x - c_k, or (wall link) from
+// slot k of x.  fin.p[k] = slot opp(k) - noff(k): the gather address of an
+// interior cell, one index away.  One branch per cell: interior cells take
+// a straight run of loads.
+template <class L, class S>
+__device__ __forceinline__ void dq_gather_aparity_d(const Geom<typename S::R> &g,
+                                                    const DirsQ<const typename S::T, L::Q> &f,
+                                                    const DirsQ<const typename S::T, L::Q> &fin, int x, int y, int z,
+                                                    int c, typename S::R (&s)[L::Q])
+{
+    using R = typename S::R;
+    using T = typename S::T;
+    if (interior(g, x, y, z)) {
+        static_for<L::Q>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            s[k] = dq_decode<S>(fin.p[k][c], R(L::wgt(k)));
+        });
+    } else if (sizeof(T) >= 4 && xedge_warp(g, x, y, z)) {
+        // a warp of a row inside in y and z holding an x-edge cell: one
+        // path for all its lanes, the links through an x face selecting
+        // their address (the wrapped one, or slot k of x across a wall)
+        const bool lo = x == 0, hi = x == g.nx - 1;
+        static_for<L::Q>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            if constexpr (L::cx(k) == 0) {
+                s[k] = dq_decode<S>(fin.p[k][c], R(L::wgt(k)));
+            } else {
+                const bool out = L::cx(k) > 0 ? lo : hi;
+                const T *ad = fin.p[k] + c;
+                if (g.per[0]) ad = out ? ad + (L::cx(k) > 0 ? g.nx : -g.nx) : ad;
+                else ad = out ? f.p[k] + c : ad;
+                s[k] = dq_decode<S>(*ad, R(L::wgt(k)));
+            }
+        });
+    } else {
+        const Faces fc = faces_of(g, x, y, z);
+        static_for<L::Q>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            constexpr unsigned m = face_mask(-L::cx(k), -L::cy(k), -L::cz(k));
+            if (fc.wall & m) s[k] = dq_decode<S>(f.p[k][c], R(L::wgt(k)));
+            else s[k] = dq_decode<S>(f.p[L::opp(k)][c + step_offset<-L::cx(k), -L::cy(k), -L::cz(k)>(g, fc)],
+                                     R(L::wgt(k)));
+        });
+    }
+}
+
+// Push: f*_i to slot i of x + c_i (dout.p[i] = slot i + noff(i) for an
+// interior cell), or (wall link) to slot opp(i) of x with the lid term of a
+// lid face; across a periodic face the target wraps.
+template <class L, class S>
+__device__ __forceinline__ void dq_push_d(const Geom<typename S::R> &g, const LidQ<typename S::R, L::Q> &lq,
+                                          const DirsQ<typename S::T, L::Q> &dst,
+                                          const DirsQ<typename S::T, L::Q> &dout, int x, int y, int z, int c,
+                                          const typename S::R (&s)[L::Q])
+{
+    using R = typename S::R;
+    using T = typename S::T;
+    if (interior(g, x, y, z)) {
+        static_for<L::Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            dout.p[i][c] = dq_encode<S>(s[i], R(L::wgt(i)));
+        });
+    } else if (xedge_warp(g, x, y, z)) {
+        // x-edge warp of a row inside in y and z: the links through an x face
+        // select their target (wrapped, or slot opp(i) of x with the lid term)
+        const bool lo = x == 0, hi = x == g.nx - 1;
+        static_for<L::Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            if constexpr (L::cx(i) == 0) {
+                dout.p[i][c] = dq_encode<S>(s[i], R(L::wgt(i)));
+            } else {
+                const bool out = L::cx(i) > 0 ? hi : lo;
+                T *ad = dout.p[i] + c;
+                R v = s[i];
+                if (g.per[0]) {
+                    ad = out ? ad + (L::cx(i) > 0 ? -g.nx : g.nx) : ad;
+                } else {
+                    ad = out ? dst.p[L::opp(i)] + c : ad;
+                    if (g.lid[L::cx(i) > 0 ? 1 : 0]) v = out ? radd(v, lq.L[L::opp(i)]) : v;
+                }
+                *ad = dq_encode<S>(v, R(L::wgt(i)));
+            }
+        });
+    } else {
+        const Faces fc = faces_of(g, x, y, z);
+        static_for<L::Q>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            constexpr unsigned m = face_mask(L::cx(i), L::cy(i), L::cz(i));
+            if (fc.wall & m) {
+                R v = s[i];
+                if (fc.lid & m) v = radd(v, lq.L[L::opp(i)]);
+                dst.p[L::opp(i)][c] = dq_encode<S>(v, R(L::wgt(i)));
+            } else {
+                dst.p[i][c + step_offset<L::cx(i), L::cy(i), L::cz(i)>(g, fc)] = dq_encode<S>(s[i], R(L::wgt(i)));
+            }
+        });
+    }
+}
+
 template <class L, class S, bool FORCE, int COLL>
 __global__ void __launch_bounds__(128) k_q_two_lattice(Geom<typename S::R> g, LidQ<typename S::R, L::Q> lq,
-                                                       const typename S::T *__restrict__ src,
-                                                       typename S::T *__restrict__ dst)
+                                                       DirsQ<const typename S::T, L::Q> src,
+                                                       DirsQ<typename S::T, L::Q> dst,
+                                                       DirsQ<typename S::T, L::Q> dout)
 {
     using R = typename S::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     if (x >= g.nx) return;
-    const int64_t c = cell_of(g, x, y, z);
+    const int c = cell32(g, x, y, z);
     R s[L::Q];
-    dq_load_natural<L, S>(g, src, c, s);
+    dq_load_natural_d<L, S>(src, c, s);
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
     dq_collide<L, R, FORCE, COLL>(g, s, Fx, Fy, Fz);
-    dq_push<L, S>(g, lq, dst, x, y, z, c, s);
+    dq_push_d<L, S>(g, lq, dst, dout, x, y, z, c, s);
 }
 
 // AA even step (natural -> A parity): collide, f*_i into slot opp(i) of the
 // same cell (+ L_opp(i) across a lid).
 template <class L, class S, bool FORCE, int COLL>
 __global__ void __launch_bounds__(128) k_q_aa_even(Geom<typename S::R> g, LidQ<typename S::R, L::Q> lq,
-                                                   typename S::T *__restrict__ f)
+                                                   DirsQ<typename S::T, L::Q> f)
 {
     using R = typename S::R;
+    using T = typename S::T;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     if (x >= g.nx) return;
-    const int64_t c = cell_of(g, x, y, z);
+    const int c = cell32(g, x, y, z);
     R s[L::Q];
-    dq_load_natural<L, S>(g, f, c, s);
+    dq_load_natural_d<L, S>(reinterpret_cast<const DirsQ<const T, L::Q> &>(f), c, s);
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
     dq_collide<L, R, FORCE, COLL>(g, s, Fx, Fy, Fz);
@@ -333,7 +430,7 @@ __global__ void __launch_bounds__(128) k_q_aa_even(Geom<typename S::R> g, LidQ<t
     }
     static_for<L::Q>([&](auto K) {
         constexpr int i = decltype(K)::value;
-        f[L::opp(i) * g.slot + c] = dq_encode<S>(s[i], R(L::wgt(i)));
+        f.p[L::opp(i)][c] = dq_encode<S>(s[i], R(L::wgt(i)));
     });
 }
 
@@ -342,18 +439,20 @@ __global__ void __launch_bounds__(128) k_q_aa_even(Geom<typename S::R> g, LidQ<t
 // location is read and written by the same cell only.
 template <class L, class S, bool FORCE, int COLL>
 __global__ void __launch_bounds__(128) k_q_aa_odd(Geom<typename S::R> g, LidQ<typename S::R, L::Q> lq,
-                                                  typename S::T *__restrict__ f)
+                                                  DirsQ<typename S::T, L::Q> f, DirsQ<const typename S::T, L::Q> fin,
+                                                  DirsQ<typename S::T, L::Q> fout)
 {
     using R = typename S::R;
+    using T = typename S::T;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     if (x >= g.nx) return;
-    const int64_t c = cell_of(g, x, y, z);
+    const int c = cell32(g, x, y, z);
     R s[L::Q];
-    dq_load_aparity<L, S>(g, f, x, y, z, c, s);
+    dq_gather_aparity_d<L, S>(g, reinterpret_cast<const DirsQ<const T, L::Q> &>(f), fin, x, y, z, c, s);
     R Fx, Fy, Fz;
     force_at<R, FORCE>(g, canon(g, x, y, z), ncanon(g), Fx, Fy, Fz);
     dq_collide<L, R, FORCE, COLL>(g, s, Fx, Fy, Fz);
-    dq_push<L, S>(g, lq, f, x, y, z, c, s);
+    dq_push_d<L, S>(g, lq, f, fout, x, y, z, c, s);
 }
 
 // rho and u (with half the force) of the post-stream state.
@@ -540,14 +639,31 @@ struct LaunchQ {
         k_q_init_eq<L, S><<<grid(h), 128, 0, st>>>(make_geom<R>(h, pitch), (T *)f, rho, u, dtype);
         return cudaGetLastError();
     }
+    // direction base pointers of a state at base: slot i, slot i + noff(i)
+    // (push target of an interior cell), slot opp(i) - noff(i) (A-parity
+    // gather address of an interior cell)
+    template <class P>
+    static DirsQ<P, QN> slots(P *base, const HostGeom &h, int64_t pitch, int shift)
+    {
+        DirsQ<P, QN> d;
+        const int64_t plane = pitch * h.ny, slot = plane * h.nz;
+        static_for<QN>([&](auto K) {
+            constexpr int i = decltype(K)::value;
+            if (shift == 0) d.p[i] = base + i * slot;
+            else if (shift > 0) d.p[i] = base + i * slot + dq_noff<L, i>(plane, pitch);
+            else d.p[i] = base + L::opp(i) * slot - dq_noff<L, i>(plane, pitch);
+        });
+        return d;
+    }
     static cudaError_t two_lattice(const HostGeom &h, int64_t pitch, bool force, const void *src, void *dst,
                                    cudaStream_t st)
     {
         const Geom<R> g = make_geom<R>(h, pitch);
         const LidQ<R, QN> lq = make_lidq<R, QN>(h);
+        const DirsQ<const T, QN> a = slots((const T *)src, h, pitch, 0);
+        const DirsQ<T, QN> b = slots((T *)dst, h, pitch, 0), bo = slots((T *)dst, h, pitch, 1);
         model(force, h.coll, [&](auto F, auto C) {
-            k_q_two_lattice<L, S, decltype(F)::value, decltype(C)::value>
-                <<<grid(h), 128, 0, st>>>(g, lq, (const T *)src, (T *)dst);
+            k_q_two_lattice<L, S, decltype(F)::value, decltype(C)::value><<<grid(h), 128, 0, st>>>(g, lq, a, b, bo);
         });
         return cudaGetLastError();
     }
@@ -555,8 +671,9 @@ struct LaunchQ {
     {
         const Geom<R> g = make_geom<R>(h, pitch);
         const LidQ<R, QN> lq = make_lidq<R, QN>(h);
+        const DirsQ<T, QN> d = slots((T *)f, h, pitch, 0);
         model(force, h.coll, [&](auto F, auto C) {
-            k_q_aa_even<L, S, decltype(F)::value, decltype(C)::value><<<grid(h), 128, 0, st>>>(g, lq, (T *)f);
+            k_q_aa_even<L, S, decltype(F)::value, decltype(C)::value><<<grid(h), 128, 0, st>>>(g, lq, d);
         });
         return cudaGetLastError();
     }
@@ -564,8 +681,10 @@ struct LaunchQ {
     {
         const Geom<R> g = make_geom<R>(h, pitch);
         const LidQ<R, QN> lq = make_lidq<R, QN>(h);
+        const DirsQ<T, QN> d = slots((T *)f, h, pitch, 0), dout = slots((T *)f, h, pitch, 1);
+        const DirsQ<const T, QN> din = slots((const T *)f, h, pitch, -1);
         model(force, h.coll, [&](auto F, auto C) {
-            k_q_aa_odd<L, S, decltype(F)::value, decltype(C)::value><<<grid(h), 128, 0, st>>>(g, lq, (T *)f);
+            k_q_aa_odd<L, S, decltype(F)::value, decltype(C)::value><<<grid(h), 128, 0, st>>>(g, lq, d, din, dout);
         });
         return cudaGetLastError();
     }
