@@ -223,10 +223,49 @@ __device__ __forceinline__ float2 cdot_pair(float2 A, float2 B, float2 C)
     return v;
 }
 
+// Sum of t[B .. E-1] as a balanced tree (compile-time bounds).
+template <int B, int E>
+__device__ __forceinline__ float2 pair_tree_sum(const float2 *t)
+{
+    if constexpr (E - B == 1) return t[B];
+    else return p_add(pair_tree_sum<B, (B + E) / 2>(t), pair_tree_sum<(B + E) / 2, E>(t));
+}
+
+// Component a of c_i (i = 1..9), and the number of pairs with a non-zero one.
+__host__ __device__ constexpr int ccomp(int i, int a) { return a == 0 ? cx(i) : (a == 1 ? cy(i) : cz(i)); }
+template <int A>
+__host__ __device__ constexpr int n_axis()
+{
+    int n = 0;
+    for (int i = 1; i <= 9; ++i) n += ccomp(i, A) != 0;
+    return n;
+}
+template <int A>
+__host__ __device__ constexpr int axis_slot(int i)
+{
+    int n = 0;
+    for (int k = 1; k < i; ++k) n += ccomp(k, A) != 0;
+    return n;
+}
+
+// S_A = sum_i c_iA P_i over the pairs with c_iA != 0, as a balanced tree.
+template <int A>
+__device__ __forceinline__ float2 axis_tree_sum(const float2 (&P)[10])
+{
+    float2 t[n_axis<A>()];
+    static_for<9>([&](auto K) {
+        constexpr int i = decltype(K)::value + 1;
+        constexpr int c = ccomp(i, A);
+        if constexpr (c != 0) t[axis_slot<A>(i)] = c > 0 ? P[i] : p_neg(P[i]);
+    });
+    return pair_tree_sum<0, n_axis<A>()>(t);
+}
+
 // The FP32 collision of bgk_collide() on the pairs P_i = {s_i, s_i+9} of
 // opposite directions, two lanes per instruction.
 //  * Moments: D = sum_i P_i gives delta_rho = (s_0 + D.x) + D.y, and
-//    S_a = sum_i c_ia P_i gives j_a = S_a.x - S_a.y (c_i+9 = -c_i).
+//    S_a = sum_i c_ia P_i gives j_a = S_a.x - S_a.y (c_i+9 = -c_i); both
+//    sums are balanced trees, which keeps their dependency chains short.
 //  * Relaxation: per pair the common part sym and the odd part +-anti of
 //    the equilibrium, {a, b} = P + omega ({sym + anti, sym - anti} - P)
 //    (plus the Guo source the same way), with exactly the operations, order
@@ -239,21 +278,9 @@ __device__ __forceinline__ void bgk_collide_pairs(float (&s)[Q], float omega, fl
         constexpr int i = decltype(K)::value + 1;
         P[i] = make_float2(s[i], s[i + 9]);
     });
-    float2 D = P[1];
-    static_for<8>([&](auto K) { D = p_add(D, P[decltype(K)::value + 2]); });
-    float2 Sx = make_float2(0.f, 0.f), Sy = Sx, Sz = Sx;
-    bool fx = true, fy = true, fz = true;
-    static_for<9>([&](auto K) {
-        constexpr int i = decltype(K)::value + 1;
-        auto acc = [&](float2 &S, bool &first, int c) {
-            if (c == 0) return;
-            if (first) { S = c > 0 ? P[i] : p_neg(P[i]); first = false; }
-            else S = p_add(S, c > 0 ? P[i] : p_neg(P[i]));
-        };
-        acc(Sx, fx, cx(i));
-        acc(Sy, fy, cy(i));
-        acc(Sz, fz, cz(i));
-    });
+    // balanced sums (depth 4 and 3 instead of chains of 8 and 4 additions)
+    const float2 D = pair_tree_sum<1, 10>(P);
+    const float2 Sx = axis_tree_sum<0>(P), Sy = axis_tree_sum<1>(P), Sz = axis_tree_sum<2>(P);
     const float drho = radd(radd(s[0], D.x), D.y);
     float jx = rsub(Sx.x, Sx.y), jy = rsub(Sy.x, Sy.y), jz = rsub(Sz.x, Sz.y);
     const float rho = radd(1.f, drho);
