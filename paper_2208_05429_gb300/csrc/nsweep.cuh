@@ -229,10 +229,24 @@ struct NSCta {
     {
         R s[Q];
         const T *in = stage(p) + sidx;
-        static_for<Q>([&](auto K) {
-            constexpr int i = decltype(K)::value;
-            s[i] = decode<S, i>(in[i * BPLANE]);
-        });
+        // FP32 storage of f itself: decode the opposite pairs {i, i+9}
+        // (one weight) two lanes at a time -- the same roundings as the
+        // scalar decode, half the instructions
+        constexpr bool PAIRS = std::is_same<S, StoreF32>::value;
+        if constexpr (PAIRS) {
+            s[0] = decode<S, 0>(in[0]);
+            static_for<9>([&](auto K) {
+                constexpr int i = decltype(K)::value + 1;
+                const float2 v = p_add(make_float2(in[i * BPLANE], in[(i + 9) * BPLANE]), p_dup(-float(wgt(i))));
+                s[i] = v.x;
+                s[i + 9] = v.y;
+            });
+        } else {
+            static_for<Q>([&](auto K) {
+                constexpr int i = decltype(K)::value;
+                s[i] = decode<S, i>(in[i * BPLANE]);
+            });
+        }
         R Fx, Fy, Fz;
         force_at<R, FORCE>(g, canon(g, x, y, p), ncanon(g), Fx, Fy, Fz);
         collide_sel<R, FORCE, COLL>(g, s, Fx, Fy, Fz);
@@ -245,13 +259,44 @@ struct NSCta {
                 if (lm & (1u << i)) s[i] = radd(s[i], g.L[opp(i)]);
             });
         }
+        // the values as the storage holds them (the AA pair stores them
+        // between its two steps): the pairs of FP32 storage two lanes at a time
+        if constexpr (PAIRS) {
+            s[0] = roundtrip<S, 0>(s[0]);
+            static_for<9>([&](auto K) {
+                constexpr int i = decltype(K)::value + 1;
+                const float2 w = p_dup(float(wgt(i)));
+                const float2 v = p_add(p_add(make_float2(s[i], s[i + 9]), w), p_neg(w));
+                s[i] = v.x;
+                s[i + 9] = v.y;
+            });
+        } else if constexpr (std::is_same<S, StoreF16S>::value || std::is_same<S, StoreBF16S>::value) {
+            // 16-bit storage: both lanes of a pair converted down (round to
+            // nearest even, as the scalar conversion) and back in one go
+            s[0] = roundtrip<S, 0>(s[0]);
+            static_for<9>([&](auto K) {
+                constexpr int i = decltype(K)::value + 1;
+                float2 v;
+                if constexpr (std::is_same<S, StoreF16S>::value)
+                    v = __half22float2(__float22half2_rn(make_float2(s[i], s[i + 9])));
+                else
+                    v = __bfloat1622float2(__float22bfloat162_rn(make_float2(s[i], s[i + 9])));
+                s[i] = v.x;
+                s[i + 9] = v.y;
+            });
+        } else {
+            static_for<Q>([&](auto K) {
+                constexpr int i = decltype(K)::value;
+                s[i] = roundtrip<S, i>(s[i]);
+            });
+        }
         R *const wm_ = ringm + (p % L::RSM) * (NDM * NPOS) + pos;
         R *const w0_ = ring0 + (p % L::RS0) * (ND0 * NPOS) + pos;
         R *const wp_ = ringp + (p % L::RSP) * (NDP * NPOS) + pos;
         static_for<Q>([&](auto K) {
             constexpr int i = decltype(K)::value;
             constexpr int gg = grp(i);
-            const R v = roundtrip<S, i>(s[i]);
+            const R v = s[i];
             if constexpr (gg == GRP_M) wm_[gidx(i) * NPOS] = v;
             else if constexpr (gg == GRP_0) w0_[gidx(i) * NPOS] = v;
             else if constexpr (gg == GRP_P) wp_[gidx(i) * NPOS] = v;
@@ -356,10 +401,27 @@ struct NSCta {
     {
         const int c = cxy + k * (int)g.plane;
         if (path == PATH_FREE) {
-            static_for<Q>([&](auto K) {
-                constexpr int i = decltype(K)::value;
-                if constexpr ((cz(i) == 1) == ZP) st_no_l1(&fo.p[i][c], encode<S, i>(s[i]));
-            });
+            if constexpr (std::is_same<S, StoreF32>::value && !ZP) {
+                // FP32 storage: the opposite pairs in the plane (c_z = 0, one
+                // weight) encoded two lanes at a time, the rest one by one
+                static_for<9>([&](auto K) {
+                    constexpr int i = decltype(K)::value + 1;
+                    if constexpr (cz(i) == 0) {
+                        const float2 e = p_add(make_float2(s[i], s[i + 9]), p_dup(float(wgt(i))));
+                        st_no_l1(&fo.p[i][c], e.x);
+                        st_no_l1(&fo.p[i + 9][c], e.y);
+                    }
+                });
+                static_for<Q>([&](auto K) {
+                    constexpr int i = decltype(K)::value;
+                    if constexpr (i == 0 || cz(i) == -1) st_no_l1(&fo.p[i][c], encode<S, i>(s[i]));
+                });
+            } else {
+                static_for<Q>([&](auto K) {
+                    constexpr int i = decltype(K)::value;
+                    if constexpr ((cz(i) == 1) == ZP) st_no_l1(&fo.p[i][c], encode<S, i>(s[i]));
+                });
+            }
         } else if (path == PATH_XYWALL) {
             // a wall link through an x or y face stores into the cell's own
             // slot opp(i) (same weight, so the same encoding), with the lid
