@@ -1,5 +1,6 @@
 """The oracle's hand-derived discrete adjoint against central finite
-differences of the oracle's own forward map (FP64)."""
+differences of the oracle's own forward map (FP64), on D3Q19 and on the
+D3Q15 and D3Q27 lattices the same formulas serve."""
 import numpy as np
 import pytest
 
@@ -9,9 +10,9 @@ from paper_2208_05429_gb300 import inputs
 from helpers import noisy_equilibrium
 
 
-def _channel(nx=6, ny=5, nz=4, tau=0.6, lid=False):
+def _channel(nx=6, ny=5, nz=4, tau=0.6, lid=False, q=19):
     bc = (BC_PERIODIC, BC_PERIODIC, BC_WALL, BC_WALL, BC_WALL, BC_LID if lid else BC_WALL)
-    cfg = oracle.Config(nx=nx, ny=ny, nz=nz, tau=tau, bc=bc, u_lid=(0.03, 0.0, 0.0), force_mode=FORCE_FIELD)
+    cfg = oracle.Config(nx=nx, ny=ny, nz=nz, tau=tau, bc=bc, u_lid=(0.03, 0.0, 0.0), force_mode=FORCE_FIELD, q=q)
     cfg.force_field = inputs.channel_force(nx, ny, nz, seed=2208, sigma=1e-4, bias_x=1e-4).astype(np.float64)
     return cfg
 
@@ -32,9 +33,10 @@ def _loss_parts(cfg, target, weights_rho):
     return loss, dLdu, dLdrho
 
 
+@pytest.mark.parametrize("q", [19, 15, 27])
 @pytest.mark.parametrize("lid", [False, True])
-def test_adjoint_matches_central_differences(lid):
-    cfg = _channel(lid=lid)
+def test_adjoint_matches_central_differences(lid, q):
+    cfg = _channel(lid=lid, q=q)
     T = 6
     f0 = noisy_equilibrium(cfg, seed=17, amp=0.01)
     target = inputs.parabolic_target(cfg.ny, cfg.nz, Ut=1e-2)
@@ -43,7 +45,7 @@ def test_adjoint_matches_central_differences(lid):
     lam0, gF = oracle.adjoint_run(cfg, f0, T, dLdu, dLdrho)
 
     def L_of(f_init, Ffield):
-        c2 = _channel(lid=lid)
+        c2 = _channel(lid=lid, q=q)
         c2.force_field = Ffield
         return loss(oracle.run(c2, f_init, T))
 
@@ -58,19 +60,20 @@ def test_adjoint_matches_central_differences(lid):
         fd = (L_of(f0, Fp) - L_of(f0, Fm)) / (2 * h)
         assert abs(gF[a, z, y, x] - fd) <= 1e-6 * max(abs(fd), 1e-3), (a, z, y, x, gF[a, z, y, x], fd)
     for _ in range(8):
-        q, z, y, x = rng.integers(19), rng.integers(cfg.nz), rng.integers(cfg.ny), rng.integers(cfg.nx)
+        i, z, y, x = rng.integers(q), rng.integers(cfg.nz), rng.integers(cfg.ny), rng.integers(cfg.nx)
         h = 1e-6
         fp, fm = f0.copy(), f0.copy()
-        fp[q, z, y, x] += h
-        fm[q, z, y, x] -= h
+        fp[i, z, y, x] += h
+        fm[i, z, y, x] -= h
         fd = (L_of(fp, F0) - L_of(fm, F0)) / (2 * h)
-        assert abs(lam0[q, z, y, x] - fd) <= 1e-6 * max(abs(fd), 1e-3), (q, z, y, x, lam0[q, z, y, x], fd)
+        assert abs(lam0[i, z, y, x] - fd) <= 1e-6 * max(abs(fd), 1e-3), (i, z, y, x, lam0[i, z, y, x], fd)
 
 
-def test_adjoint_step_is_transpose():
+@pytest.mark.parametrize("q", [19, 15, 27])
+def test_adjoint_step_is_transpose(q):
     """<lam, J v> = <J^T lam, v> for the one-step Jacobian J (J v by central
     differences of the step, which is quadratic-free enough for h = 1e-6)."""
-    cfg = _channel(nx=5, ny=4, nz=4, lid=True)
+    cfg = _channel(nx=5, ny=4, nz=4, lid=True, q=q)
     f = noisy_equilibrium(cfg, seed=8, amp=0.02)
     rng = np.random.default_rng(9)
     lam = rng.normal(size=f.shape)
