@@ -6,8 +6,10 @@ tau = 0.55, lid u = (0.05, 0, 0) on the z+ face, half-way bounce-back on the
 other five faces, fluid at rest at t = 0; FP32 storage and arithmetic; the
 two-step merged sweep by default (on this lattice the neighbour-synchronised
 kernel; --variant selects the single-copy AA pair or two lattices; the
-other schedules and storage formats are reported under
-"variants", the shadow-shell merged sweep as merged_shadow).  One benchmark step = two lattice
+other schedules, storage formats, collision models and the D3Q15 / D3Q27
+lattices are reported under "variants", the shadow-shell merged sweep as
+merged_shadow; --lattice 15 or 27 times one of those lattices instead, with
+the single-step schedules).  One benchmark step = two lattice
 time steps over all 16.8 M cells (one merged sweep, or an AA even/odd pair).
 MLUPS counts every cell as a fluid node (million lattice-node updates per
 second).
