@@ -46,6 +46,7 @@ import argparse
 import glob
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -107,11 +108,34 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_digest() -> str:
+CSRC = os.path.join(ROOT, "paper_2208_05429_gb300", "csrc")
+
+
+def source_closure(unit: str, read=None) -> list:
+    """The csrc files a translation unit is compiled from: the unit and every
+    header it includes with #include "...", transitively (sorted names).
+    read(name) returns a file's text (default: the working tree)."""
+    read = read or (lambda name: open(os.path.join(CSRC, name)).read())
+    seen, todo = set(), [unit]
+    while todo:
+        name = todo.pop()
+        if name in seen:
+            continue
+        seen.add(name)
+        for inc in re.findall(r'^\s*#\s*include\s+"([^"]+)"', read(name), re.M):
+            if os.path.exists(os.path.join(CSRC, inc)):
+                todo.append(inc)
+    return sorted(seen)
+
+
+def kernel_digest(unit: str, read=None) -> str:
+    """Digest of the sources of one translation unit (names and contents):
+    a kernel's recorded counters stay valid while these are unchanged."""
+    read = read or (lambda name: open(os.path.join(CSRC, name)).read())
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2208_05429_gb300", "csrc", "*"))):
-        with open(p, "rb") as fh:
-            h.update(fh.read())
+    for name in source_closure(unit, read):
+        h.update(name.encode())
+        h.update(read(name).encode())
     return h.hexdigest()[:16]
 
 
@@ -123,7 +147,7 @@ def recorded_traffic(key: str):
         with open(path) as fh:
             d = json.load(fh)
         ent = d.get(key)
-        if ent and ent.get("kernel_digest") == kernel_digest():
+        if ent and ent.get("kernel_digest") == kernel_digest(ent["unit"]):
             return float(ent["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -261,6 +285,30 @@ def time_variant(n, storage, variant, steps, warmup, dist_on=False, sweep_env=No
     lat.profile(False)
     sync_all(dist_on)
     return start.elapsed_time(end), lat.profile_read(), lat
+
+
+def time_kstep(n, storage, K, sweeps, warmup):
+    """(elapsed ms over `sweeps` calls of step(K), per-kernel records) of the
+    K-step sweep on the cavity: one K-step sweep per call."""
+    import torch
+    from paper_2208_05429_gb300.lbm import CAVITY_BC, Lattice
+    lat = Lattice((n, n, n), TAU, bc=CAVITY_BC, u_lid=U_LID, storage=storage, variant="kstep", sweep_steps=K)
+    lat.init_equilibrium()
+    for _ in range(warmup):
+        lat.step(K)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    lat.profile(True)
+    start.record(lat.stream)
+    for _ in range(sweeps):
+        lat.step(K)
+    end.record(lat.stream)
+    end.synchronize()
+    lat.profile(False)
+    prof = lat.profile_read()
+    del lat
+    return start.elapsed_time(end), prof
 
 
 def roofline_of(prof, kernel, storage, cells, peak, peak_kind, q=Q):
@@ -710,6 +758,12 @@ def main():
             variants[name] = {"MLUPS": round(cells * 2 * k / (vms * 1e3), 1),
                               "kernel_frac_of_peak": r["frac"] if r else None,
                               "kernel": dk}
+        for st, K in (("f32", 3), ("f32", 4), ("f16s", 3)):
+            k = min(args.steps, 100)
+            vms, vprof = time_kstep(n, st, K, k, 3)
+            r = roofline_of(vprof, "kstep", st, cells, peak, peak_kind)
+            variants[f"kstep{K}_{st}"] = {"MLUPS": round(cells * K * k / (vms * 1e3), 1),
+                                          "kernel_frac_of_peak": r["frac"] if r else None, "kernel": "kstep"}
         line["variants"] = variants
         try:
             line["adjoint"] = adjoint_leg()

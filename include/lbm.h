@@ -100,8 +100,18 @@ enum { LBM_STORAGE_F64 = 0, LBM_STORAGE_F32 = 1, LBM_STORAGE_F32S = 2,
  *                shadow-shell sweep, =neighbour the neighbour-synchronised
  *                one for any tile count it can hold resident.  Where
  *                neither sweep can run (a periodic z with nz = 1, or a
- *                shadow beyond 2^31 elements) MERGED runs the AA pair. */
-enum { LBM_VARIANT_TWO_LATTICE = 0, LBM_VARIANT_AA = 1, LBM_VARIANT_MERGED = 2 };
+ *                shadow beyond 2^31 elements) MERGED runs the AA pair.
+ *   KSTEP        K = sweep_steps (3 or 4) time steps per sweep on two
+ *                lattices, the merge of more than two steps the paper
+ *                leaves as future work (Sec. 6): each 16 x 8 (K = 3) or
+ *                16 x 4 (K = 4) column tile marches z with K levels of
+ *                post-collision planes in shared memory, the level-s values
+ *                on the tile widened by K - s cells (halos recomputed by
+ *                every tile that reads them, no tile waits on another).
+ *                4- and 2-byte storage, D3Q19, BGK (LBM_EUNSUPPORTED
+ *                otherwise); step counts not divisible by K end with
+ *                two-lattice steps. */
+enum { LBM_VARIANT_TWO_LATTICE = 0, LBM_VARIANT_AA = 1, LBM_VARIANT_MERGED = 2, LBM_VARIANT_KSTEP = 3 };
 
 /* Body force (Guo forcing): none, one vector for every cell, or a per-cell
  * FP32 field [3][z][y][x] set with lbm_set_force(). */
@@ -152,6 +162,7 @@ typedef struct lbm_config {
     double mrt_s3, mrt_s4;    /* MRT rates of the third- and fourth-order
                                  moments, in (0, 2) (default 1)                 */
     int32_t lattice;          /* LBM_LATTICE_* (default D3Q19; 0 = D3Q19)       */
+    int32_t sweep_steps;      /* time steps per KSTEP sweep: 3 or 4 (0 = 3)     */
 } lbm_config;
 
 /* Fill cfg with a 32^3 fully periodic FP32 AA D3Q19 lattice, tau = 0.6, BGK
@@ -164,7 +175,9 @@ void lbm_config_default(lbm_config *cfg);
  * one periodic and one non-periodic face, |u_lid| >= 0.3, rho_wall <= 0,
  * unknown storage/variant/force mode, collision or lattice, a trt_lambda that
  * is not positive and finite, or an MRT rate outside (0, 2).
- * LBM_EUNSUPPORTED for MRT on D3Q15 or D3Q27. */
+ * LBM_EUNSUPPORTED for MRT on D3Q15 or D3Q27, and for KSTEP with FP64
+ * storage, another lattice or another collision; LBM_EINVAL for a
+ * sweep_steps other than 0, 3 or 4. */
 int lbm_validate(const lbm_config *cfg);
 
 /* Device bytes a handle of this configuration uses (populations, second
@@ -300,7 +313,7 @@ int lbm_reduce_populations(const lbm_config *cfg, const void *f, int32_t dtype, 
 /* ---------------- per-kernel timing ----------------
  * Kernel classes launched by lbm_step(). */
 enum { LBM_KERNEL_TWO_LATTICE = 0, LBM_KERNEL_AA_EVEN = 1, LBM_KERNEL_AA_ODD = 2,
-       LBM_KERNEL_SNAPSHOT = 3, LBM_KERNEL_MERGED = 4, LBM_KERNEL_COUNT = 5 };
+       LBM_KERNEL_SNAPSHOT = 3, LBM_KERNEL_MERGED = 4, LBM_KERNEL_KSTEP = 5, LBM_KERNEL_COUNT = 6 };
 /* LBM_KERNEL_SNAPSHOT: the shadow-shell sweep's copies made before a sweep
  * (the tile shells after a single step, the planes at z-chunk boundaries);
  * LBM_KERNEL_MERGED: either two-step sweep. */

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "d3q19.cuh"
+#include "ksweep_api.h"
 #include "lattice.cuh"
 #include "lbm.h"
 #include "ops.h"
@@ -275,7 +276,7 @@ Layout layout_of(const lbm_config &c, const ShellInfo &si)
     const size_t pop = align_up((size_t)state_elems(c) * es);
     size_t off = 0;
     L.f = off; off += pop;
-    L.f2 = off; if (c.variant == LBM_VARIANT_TWO_LATTICE) off += pop;
+    L.f2 = off; if (c.variant == LBM_VARIANT_TWO_LATTICE || c.variant == LBM_VARIANT_KSTEP) off += pop;
     L.G3 = off;
     if (uses_m3(c, si)) off += 2 * align_up((size_t)(si.gplane * c.nz) * es);
     L.Z3 = off;
@@ -454,7 +455,7 @@ int lbm_validate(const lbm_config *c)
     if (!(ul < 0.3)) return LBM_EINVAL;
     if (!(c->rho_wall > 0.0) || !isfinite(c->rho_wall)) return LBM_EINVAL;
     if (c->storage < LBM_STORAGE_F64 || c->storage > LBM_STORAGE_BF16S) return LBM_EINVAL;
-    if (c->variant < LBM_VARIANT_TWO_LATTICE || c->variant > LBM_VARIANT_MERGED) return LBM_EINVAL;
+    if (c->variant < LBM_VARIANT_TWO_LATTICE || c->variant > LBM_VARIANT_KSTEP) return LBM_EINVAL;
     if ((double)((c->nx + 15) / 16 * 16) * (double)c->ny * (double)c->nz > 2147483647.0) return LBM_EINVAL;
     if (c->force_mode < LBM_FORCE_NONE || c->force_mode > LBM_FORCE_FIELD) return LBM_EINVAL;
     for (int a = 0; a < 3; ++a)
@@ -466,6 +467,10 @@ int lbm_validate(const lbm_config *c)
         c->lattice != LBM_LATTICE_D3Q27)
         return LBM_EINVAL;
     if (lat_q(*c) != 19 && c->collision == LBM_COLLISION_MRT) return LBM_EUNSUPPORTED;
+    if (c->sweep_steps != 0 && c->sweep_steps != 3 && c->sweep_steps != 4) return LBM_EINVAL;
+    if (c->variant == LBM_VARIANT_KSTEP &&
+        (c->storage == LBM_STORAGE_F64 || lat_q(*c) != 19 || c->collision != LBM_COLLISION_BGK))
+        return LBM_EUNSUPPORTED;
     return LBM_OK;
 }
 
@@ -524,7 +529,7 @@ static int create_impl(const lbm_config *cfg, void *stream, void *buf, size_t by
     h->bytes = bytes;
     char *b = (char *)buf;
     h->f = b + L.f;
-    h->f2 = cfg->variant == LBM_VARIANT_TWO_LATTICE ? b + L.f2 : nullptr;
+    h->f2 = cfg->variant == LBM_VARIANT_TWO_LATTICE || cfg->variant == LBM_VARIANT_KSTEP ? b + L.f2 : nullptr;
     h->m3 = uses_m3(*cfg, si);
     h->ns = uses_ns(*cfg, si);
     if (h->ns) {
@@ -669,6 +674,20 @@ static int step_units(lbm_handle *h, int64_t n)
             CK(timed(h, LBM_KERNEL_TWO_LATTICE, [&] { return o.two_lattice(h->hg, h->nxp, h->force, h->f, h->f2, h->stream); }));
             void *t = h->f; h->f = h->f2; h->f2 = t;
             n -= 1; h->t += 1;
+            break;
+        }
+        case LBM_VARIANT_KSTEP: {
+            const int K = h->cfg.sweep_steps ? h->cfg.sweep_steps : 3;
+            if (n >= K) {
+                CK(timed(h, LBM_KERNEL_KSTEP, [&] {
+                    return ksweep_launch(h->cfg.storage, h->hg, h->nxp, h->force, K, h->f, h->f2, h->stream);
+                }));
+                n -= K; h->t += K;
+            } else {
+                CK(timed(h, LBM_KERNEL_TWO_LATTICE, [&] { return o.two_lattice(h->hg, h->nxp, h->force, h->f, h->f2, h->stream); }));
+                n -= 1; h->t += 1;
+            }
+            void *t = h->f; h->f = h->f2; h->f2 = t;
             break;
         }
         case LBM_VARIANT_AA:

@@ -24,20 +24,21 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ESTATE, LBM_ENONFINITE, LBM_ETIME
     0, -1, -2, -3, -4, -5, -6, -7
 LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_LID = 0, 1, 2
 LBM_STORAGE_F64, LBM_STORAGE_F32, LBM_STORAGE_F32S, LBM_STORAGE_F16S, LBM_STORAGE_BF16S = 0, 1, 2, 3, 4
-LBM_VARIANT_TWO_LATTICE, LBM_VARIANT_AA, LBM_VARIANT_MERGED = 0, 1, 2
+LBM_VARIANT_TWO_LATTICE, LBM_VARIANT_AA, LBM_VARIANT_MERGED, LBM_VARIANT_KSTEP = 0, 1, 2, 3
 LBM_FORCE_NONE, LBM_FORCE_UNIFORM, LBM_FORCE_FIELD = 0, 1, 2
 LBM_DTYPE_F32, LBM_DTYPE_F64 = 0, 1
 LBM_LATTICE_D3Q15, LBM_LATTICE_D3Q19, LBM_LATTICE_D3Q27 = 15, 19, 27
 LBM_COLLISION_BGK, LBM_COLLISION_TRT, LBM_COLLISION_REG, LBM_COLLISION_MRT = 0, 1, 2, 3
 COLLISION = {"bgk": LBM_COLLISION_BGK, "trt": LBM_COLLISION_TRT, "reg": LBM_COLLISION_REG, "mrt": LBM_COLLISION_MRT}
-LBM_KERNEL_TWO_LATTICE, LBM_KERNEL_AA_EVEN, LBM_KERNEL_AA_ODD, LBM_KERNEL_SNAPSHOT, LBM_KERNEL_MERGED = \
-    0, 1, 2, 3, 4
+LBM_KERNEL_TWO_LATTICE, LBM_KERNEL_AA_EVEN, LBM_KERNEL_AA_ODD, LBM_KERNEL_SNAPSHOT, LBM_KERNEL_MERGED, \
+    LBM_KERNEL_KSTEP = 0, 1, 2, 3, 4, 5
 KERNELS = {"two_lattice": LBM_KERNEL_TWO_LATTICE, "aa_even": LBM_KERNEL_AA_EVEN, "aa_odd": LBM_KERNEL_AA_ODD,
-           "snapshot": LBM_KERNEL_SNAPSHOT, "merged": LBM_KERNEL_MERGED}
+           "snapshot": LBM_KERNEL_SNAPSHOT, "merged": LBM_KERNEL_MERGED, "kstep": LBM_KERNEL_KSTEP}
 
 STORAGE = {"f64": LBM_STORAGE_F64, "f32": LBM_STORAGE_F32, "f32s": LBM_STORAGE_F32S,
            "f16s": LBM_STORAGE_F16S, "bf16s": LBM_STORAGE_BF16S}
-VARIANT = {"two_lattice": LBM_VARIANT_TWO_LATTICE, "aa": LBM_VARIANT_AA, "merged": LBM_VARIANT_MERGED}
+VARIANT = {"two_lattice": LBM_VARIANT_TWO_LATTICE, "aa": LBM_VARIANT_AA, "merged": LBM_VARIANT_MERGED,
+           "kstep": LBM_VARIANT_KSTEP}
 BC = {"periodic": LBM_BC_PERIODIC, "wall": LBM_BC_WALL, "lid": LBM_BC_LID}
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -67,6 +68,7 @@ class lbm_config(ctypes.Structure):
         ("mrt_s3", ctypes.c_double),
         ("mrt_s4", ctypes.c_double),
         ("lattice", ctypes.c_int32),
+        ("sweep_steps", ctypes.c_int32),
     ]
 
 
@@ -306,9 +308,10 @@ def make_config(shape: Sequence[int], tau: float, bc: Sequence[Union[str, int]] 
                 u_lid=(0.0, 0.0, 0.0), rho_wall: float = 1.0, storage: str = "f32", variant: str = "aa",
                 force_mode: int = LBM_FORCE_NONE, force_uniform=(0.0, 0.0, 0.0),
                 collision: Union[str, int] = "bgk", trt_lambda: float = 3.0 / 16.0,
-                mrt_s3: float = 1.0, mrt_s4: float = 1.0, lattice: int = 19) -> lbm_config:
+                mrt_s3: float = 1.0, mrt_s4: float = 1.0, lattice: int = 19, sweep_steps: int = 0) -> lbm_config:
     """Build an lbm_config; shape is (nx, ny, nz), bc lists x-, x+, y-, y+, z-, z+;
-    lattice is 15, 19 or 27 (D3Q15, D3Q19, D3Q27)."""
+    lattice is 15, 19 or 27 (D3Q15, D3Q19, D3Q27); sweep_steps the steps per
+    sweep of the "kstep" variant (3 or 4; 0 = 3)."""
     c = lbm_config()
     c.nx, c.ny, c.nz = (int(v) for v in shape)
     c.tau = float(tau)
@@ -326,6 +329,7 @@ def make_config(shape: Sequence[int], tau: float, bc: Sequence[Union[str, int]] 
     c.trt_lambda = float(trt_lambda)
     c.mrt_s3, c.mrt_s4 = float(mrt_s3), float(mrt_s4)
     c.lattice = int(lattice)
+    c.sweep_steps = int(sweep_steps)
     return c
 
 
@@ -343,7 +347,7 @@ class Lattice:
     def __init__(self, shape, tau: float, bc=("periodic",) * 6, u_lid=(0.0, 0.0, 0.0), rho_wall: float = 1.0,
                  storage: str = "f32", variant: str = "aa", force=None, device=None, stream=None,
                  collision: str = "bgk", trt_lambda: float = 3.0 / 16.0, mrt_s3: float = 1.0,
-                 mrt_s4: float = 1.0, lattice: int = 19):
+                 mrt_s4: float = 1.0, lattice: int = 19, sweep_steps: int = 0):
         import torch
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         if force is None:
@@ -353,7 +357,7 @@ class Lattice:
         else:
             fm, fu = LBM_FORCE_UNIFORM, tuple(float(v) for v in force)
         self.cfg = make_config(shape, tau, bc, u_lid, rho_wall, storage, variant, fm, fu, collision, trt_lambda,
-                               mrt_s3, mrt_s4, lattice)
+                               mrt_s3, mrt_s4, lattice, sweep_steps)
         self.q = int(lattice) or Q
         self.shape = tuple(int(v) for v in shape)  # (nx, ny, nz)
         self.nbytes = lbm_required_bytes(self.cfg)

@@ -77,6 +77,22 @@ def test_other_lattices_validate(cuda_lib, q):
         assert lbm.lbm_validate(cfg) == lbm.LBM_EINVAL
 
 
+def test_kstep_validation(cuda_lib):
+    """The K-step sweep: 3 or 4 steps, FP32-compute storage, D3Q19, BGK;
+    two lattices of memory."""
+    for st in ("f32", "f32s", "f16s", "bf16s"):
+        for k in (0, 3, 4):
+            cfg = lbm.make_config((24, 20, 12), 0.7, lbm.CAVITY_BC, storage=st, variant="kstep", sweep_steps=k)
+            assert lbm.lbm_validate(cfg) == lbm.LBM_OK, (st, k)
+    for kw in (dict(storage="f64"), dict(lattice=27), dict(collision="trt"), dict(collision="mrt")):
+        cfg = lbm.make_config((16, 16, 16), 0.7, variant="kstep", **kw)
+        assert lbm.lbm_validate(cfg) == lbm.LBM_EUNSUPPORTED, kw
+    pop = 19 * 64 ** 3 * 4
+    ks = lbm.make_config((64, 64, 64), 0.6, storage="f32", variant="kstep")
+    assert 2 * pop <= lbm.lbm_required_bytes(ks) < 2 * pop * 1.01
+    assert lbm.lbm_config_default().sweep_steps == 0
+
+
 def test_lattice_table_is_the_one_the_schedule_tests_restate(cuda_lib):
     from test_merged_schedule import GPU_C
     c, _ = lbm.lbm_lattice()
@@ -92,7 +108,8 @@ def test_default_config_valid(cuda_lib):
 
 @pytest.mark.parametrize("field,value", [
     ("nx", 0), ("ny", -3), ("nz", 70000), ("tau", 0.5), ("tau", float("nan")), ("rho_wall", 0.0),
-    ("storage", 9), ("variant", 3), ("variant", 4), ("force_mode", 5),
+    ("storage", 9), ("variant", 4), ("variant", 5), ("variant", -1), ("force_mode", 5), ("sweep_steps", 2),
+    ("sweep_steps", 5),
     ("collision", 4), ("collision", -1), ("mrt_s3", 0.0), ("mrt_s4", 2.0), ("trt_lambda", 0.0), ("trt_lambda", float("inf")),
 ])
 def test_invalid_configs_rejected(cuda_lib, field, value):
