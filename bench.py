@@ -759,7 +759,7 @@ def main():
                               "kernel_frac_of_peak": r["frac"] if r else None,
                               "kernel": dk}
         for st, K in (("f32", 3), ("f32", 4), ("f16s", 3)):
-            k = min(args.steps, 100)
+            k = min(args.steps, 30)
             vms, vprof = time_kstep(n, st, K, k, 3)
             r = roofline_of(vprof, "kstep", st, cells, peak, peak_kind)
             variants[f"kstep{K}_{st}"] = {"MLUPS": round(cells * K * k / (vms * 1e3), 1),

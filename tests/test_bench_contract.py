@@ -54,3 +54,24 @@ def test_reference_arm_under_torchrun_two_ranks():
     lines = _run(cmd)
     assert len(lines) == 1
     assert json.loads(lines[0])["n_gpus"] == 2
+
+
+def test_recorded_traffic_is_keyed_to_each_kernels_sources():
+    """Each recorded ncu figure names the translation unit its kernel is built
+    from; the digest covers that unit and the headers it includes (so a new
+    kernel elsewhere leaves it valid, an edit of those sources voids it)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
+        rec = json.load(fh)
+    assert rec
+    for key, ent in rec.items():
+        assert os.path.exists(os.path.join(bench.CSRC, ent["unit"])), key
+        assert bench.recorded_traffic(key) == ent["dram_bytes_per_launch"], key
+    closure = bench.source_closure("inst_f32.cu")
+    assert {"inst_f32.cu", "launch.cuh", "nsweep.cuh", "kernels.cuh", "d3q19.cuh", "ops.h"} <= set(closure)
+    assert "ksweep.cuh" not in closure and "dqn.cuh" not in closure
+    files = {n: open(os.path.join(bench.CSRC, n)).read() for n in closure}
+    base = bench.kernel_digest("inst_f32.cu", lambda n: files[n])
+    edited = dict(files, **{"nsweep.cuh": files["nsweep.cuh"] + "\n// edit\n"})
+    assert bench.kernel_digest("inst_f32.cu", lambda n: edited[n]) != base
