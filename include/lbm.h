@@ -181,7 +181,7 @@ void lbm_config_default(lbm_config *cfg);
 int lbm_validate(const lbm_config *cfg);
 
 /* Device bytes a handle of this configuration uses (populations, second
- * lattice for TWO_LATTICE, tile-shell shadow or progress words for MERGED,
+ * lattice for TWO_LATTICE and KSTEP, tile-shell shadow or progress words for MERGED,
  * reduction scratch), each region aligned to
  * 256 bytes.
  * *bytes is a host output.  For MERGED the figure depends on the current
@@ -237,7 +237,8 @@ int lbm_set_force(lbm_handle *h, const float *F);
 
 /* Advance n >= 0 time steps (one step = collide then stream, Sec. 3).  With
  * MERGED, pairs of steps run as one two-step sweep (Sec. 4) and
- * an odd remainder as one AA step.  Asynchronous on the handle's stream.
+ * an odd remainder as one AA step; with KSTEP, groups of sweep_steps steps
+ * run as one K-step sweep and a remainder as two-lattice steps.  Asynchronous on the handle's stream.
  * Calls with n >= 32 (outside profiling) capture the launches of 32 steps
  * once into a CUDA graph and replay it, on an internal stream ordered after
  * and before the handle's stream; a new force field drops the graph. */
@@ -316,7 +317,8 @@ enum { LBM_KERNEL_TWO_LATTICE = 0, LBM_KERNEL_AA_EVEN = 1, LBM_KERNEL_AA_ODD = 2
        LBM_KERNEL_SNAPSHOT = 3, LBM_KERNEL_MERGED = 4, LBM_KERNEL_KSTEP = 5, LBM_KERNEL_COUNT = 6 };
 /* LBM_KERNEL_SNAPSHOT: the shadow-shell sweep's copies made before a sweep
  * (the tile shells after a single step, the planes at z-chunk boundaries);
- * LBM_KERNEL_MERGED: either two-step sweep. */
+ * LBM_KERNEL_MERGED: either two-step sweep; LBM_KERNEL_KSTEP: the K-step
+ * sweep. */
 
 /* enable = 1: from now on every kernel lbm_step() launches is bracketed by
  * two CUDA events recorded on the handle's stream (earlier records are
